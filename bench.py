@@ -1,0 +1,346 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the SAIM hot path (one JSON line on rank 0).
+
+Workload: QKP N=300 at densities 0.25/0.5/0.75/1.0, 256 instances each (1024 instances,
+N' <= 313 spins), 128 chains per instance, 1000 sweeps with beta 0 -> 10 (Table I).  One step
+is one outer iteration of Algorithm 1 over the whole batch: one annealing run per chain
+(sais_sample), the feasible-sample bookkeeping (sais_track_best) and the multiplier step
+(sais_update_lambda), all through the C-ABI on device buffers.  Metric: p-bit spin updates
+per second (chains x sweeps x N' summed over instances, divided by the step time).
+
+--impl reference times the CPU oracle (the only reference that exists for this method) on a
+bounded sample of the same workload.  Under torchrun every rank runs its own 1024 instances
+(weak scaling, no collective on the data path); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "p-bit spin updates/s; wall-clock to 1% gap on QKP N=300 (BF16 block vs plain)"
+UNIT = "spin_updates/s"
+DENSITIES = (0.25, 0.5, 0.75, 1.0)
+SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--variant", default="auto", choices=["auto", "plain", "blocked"])
+    ap.add_argument("--per-density", type=int, default=256)
+    ap.add_argument("--chains", type=int, default=128)
+    ap.add_argument("--sweeps", type=int, default=1000)
+    ap.add_argument("--beta-max", type=float, default=10.0)
+    ap.add_argument("--eta", type=float, default=20.0)
+    ap.add_argument("--block-k", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload(per_density: int, rank: int):
+    from paper_2501_04971_gb300 import workloads as wl
+    return [wl.qkp(300, d, rank * per_density + s) for d in DENSITIES for s in range(per_density)]
+
+
+def workload_name(a) -> str:
+    return (f"QKP N=300, d in {{0.25,0.5,0.75,1}} x {a.per_density} instances, "
+            f"{a.chains} chains, {a.sweeps} sweeps (beta 0->{a.beta_max:g}) per step")
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and --impl reference)
+# ------------------------------------------------------------------------------------------
+
+def oracle_rate(insts, seconds: float, chains: int):
+    """The oracle's annealing runs (or_anneal, OpenMP over chains) on a bounded sample: the
+    first instance of each density, `chains` chains, sweep count calibrated so the run takes
+    about `seconds`.  Returns (updates/s, cores, description)."""
+    import oracle
+    sample = [insts[i * (len(insts) // len(DENSITIES))] for i in range(len(DENSITIES))]
+    probs = []
+    for inst in sample:
+        p = oracle.Problem(inst.n, inst.m, inst.W, inst.h, inst.A, inst.b, alpha=inst.alpha,
+                           density=inst.density)
+        J, hI, _ = p.ising(np.array([1.0], np.float32))
+        probs.append((p, J, hI))
+
+    def run(T):
+        t0 = time.perf_counter()
+        upd = 0
+        for p, J, hI in probs:
+            oracle.anneal(J, hI, 10.0, T, 1, 0, chains)
+            upd += chains * T * p.nprime
+        return upd, time.perf_counter() - t0
+
+    u, dt = run(2)
+    T = max(2, int(2 * seconds / max(dt, 1e-6)))
+    u, dt = run(T)
+    cores = os.cpu_count() or 1
+    desc = (f"oracle or_anneal, {len(probs)} instances (one per density), {chains} chains x "
+            f"{T} sweeps each, {u} updates in {dt:.1f} s, OpenMP over chains")
+    return u / dt, cores, desc
+
+
+def reference_arm(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    insts = workload(a.per_density, 0)
+    per = max(2.0, a.cpu_seconds / max(1, a.steps + a.warmup))
+    for _ in range(a.warmup):
+        oracle_rate(insts, per / 4, 2 * (os.cpu_count() or 1))
+    vals, cores, desc = [], 1, ""
+    for _ in range(a.steps):
+        v, cores, desc = oracle_rate(insts, per, 2 * (os.cpu_count() or 1))
+        vals.append(v)
+    v = float(statistics.median(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "sample": "bounded CPU sample"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                    rows.append(f)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v == "Active"})
+        return {"sm_mhz": float(statistics.median(sm)), "sm_max_mhz": float(rows[0][2]),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return reference_arm(a)
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2501_04971_gb300 import sais
+
+    insts = workload(a.per_density, rank)
+    prob = sais.Problem(insts, device=local)
+    nspins = np.array([s.n_spins for s in prob.scalars], dtype=np.int64)
+    upd_step = int(nspins.sum()) * a.chains * a.sweeps
+    variant = a.variant
+    if variant == "auto":
+        variant = "plain"
+        try:
+            lam_probe = torch.zeros(prob.count * prob.m_stride, device="cuda")
+            prob.sample(lam_probe, 32, 1, a.beta_max, 0, 0, variant="blocked")
+            variant = "blocked"
+        except sais.SaisError:
+            pass
+
+    stream = torch.cuda.current_stream()
+    lam = torch.zeros(prob.count * prob.m_stride, device="cuda", dtype=torch.float32)
+    out = prob.alloc_outputs(a.chains)
+    best = prob.alloc_best()
+
+    def step(k):
+        prob.sample(lam, a.chains, a.sweeps, a.beta_max, 1234, k, variant=variant,
+                    block_k=a.block_k, out=out, stream=stream)
+        prob.track_best(out, a.chains, k, best, stream=stream)
+        prob.update_lambda(out["g"], a.chains, a.eta, True, lam, stream=stream)
+
+    for k in range(a.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(a.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_start.record(stream)
+        for k in range(a.steps):
+            ev[k][0].record(stream)
+            prob.sample(lam, a.chains, a.sweeps, a.beta_max, 1234, a.warmup + k,
+                        variant=variant, block_k=a.block_k, out=out, stream=stream)
+            ev[k][1].record(stream)
+            prob.track_best(out, a.chains, a.warmup + k, best, stream=stream)
+            prob.update_lambda(out["g"], a.chains, a.eta, True, lam, stream=stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = t_start.elapsed_time(t_end)
+    kern_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = upd_step * a.steps * world / (ms / 1e3)
+
+    # roofline of the dominant kernel (the sampler), per launch
+    kmean = statistics.mean(kern_ms) / 1e3
+    if variant == "blocked":
+        npad = ((nspins + 63) // 64) * 64
+        flops = float((2 * npad * nspins).sum()) * a.chains * a.sweeps
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        peak = peaks.get("bf16_tflops", 1900.0) * 1e12
+        roof = {"bound": "tensor", "achieved": flops / kmean / 1e12, "peak": peak / 1e12,
+                "unit": "TFLOP/s", "frac": flops / kmean / peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)" if peaks else
+                "fallback 1.9 PFLOP/s"}
+    else:
+        flops = float((2 * nspins * nspins).sum()) * a.chains * a.sweeps
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6
+        roof = {"bound": "alu", "achieved": flops / kmean / 1e12, "peak": peak / 1e12,
+                "unit": "TFLOP/s", "frac": flops / kmean / peak, "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "per_update": "2 N' flops (Eq. 9 field, dense)"}
+    roof["kernel_ms"] = kmean * 1e3
+
+    # end to end through sais_solve with pinned host buffers, one iteration per step
+    e2e = None
+    if not a.no_e2e:
+        M, Wd, cnt = prob.m_stride, prob.words, prob.count
+        lam_h = torch.zeros(cnt * M, dtype=torch.float32).pin_memory()
+        pinned = {"best_cost": torch.zeros(cnt, dtype=torch.int64).pin_memory(),
+                  "best_x": torch.zeros(cnt * Wd, dtype=torch.int32).pin_memory(),
+                  "best_iter": torch.zeros(cnt, dtype=torch.int32).pin_memory(),
+                  "best_chain": torch.zeros(cnt, dtype=torch.int32).pin_memory(),
+                  "feasible_count": torch.zeros(cnt, dtype=torch.int64).pin_memory(),
+                  "lambda_final": torch.zeros(cnt * M, dtype=torch.float32).pin_memory(),
+                  "lambda_trace": torch.zeros(cnt * M, dtype=torch.float32).pin_memory()}
+        prm = sais.sais_solve_params()
+        prm.iters, prm.chains, prm.sweeps, prm.beta_max = 1, a.chains, a.sweeps, a.beta_max
+        prm.eta, prm.seed, prm.project_nonneg = a.eta, 1234, 1
+        prm.variant = sais._VARIANTS[variant]
+        prm.block_k = a.block_k
+        prm.lambda0 = sais._P(lam_h.data_ptr())
+        res = sais.sais_solve_result()
+        for k_, v_ in pinned.items():
+            setattr(res, k_, sais._P(v_.data_ptr()))
+        sp = sais._P(stream.cuda_stream)
+        prm.iter0 = 0
+        sais.sais_solve(prob.handle, prm, res, sp)     # warm
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for k in range(a.steps):
+            prm.iter0 = k
+            sais.sais_solve(prob.handle, prm, res, sp)
+            lam_h.copy_(pinned["lambda_final"])
+        dt = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        h2d = cnt * M * 4 + cnt * (8 + 4 + 4) + 4
+        d2h = cnt * (8 + Wd * 4 + 4 + 4 + 8 + M * 4 + M * 4)
+        e2e = {"value": upd_step * a.steps * world / dt, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "api": "sais_solve(iters=1), pinned host lambda0 and results"}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if world == 1 and not a.no_cpu:
+        v, cores, desc = oracle_rate(insts, a.cpu_seconds, 2 * (os.cpu_count() or 1))
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if variant == "blocked" else "fp32",
+            "data": "synthetic",
+            "config": {"workload": workload_name(a), "instances": prob.count,
+                       "chains": a.chains, "sweeps": a.sweeps, "spins_total": int(nspins.sum()),
+                       "variant": variant, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (W int16 + bf16 of 1024 instances, "
+                             f"{prob.count * 2 * 2 * 320 * 320 / 1e6:.0f} MB)"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 3 * a.steps, "clocks": clk.summary(),
+            "updates_per_step": upd_step}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

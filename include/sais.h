@@ -1,0 +1,252 @@
+/*
+ * sais.h -- C-ABI of libsais, the GB300 (sm_103a) hot path of the Self-Adaptive Ising Machine
+ * (SAIM) for constrained binary optimisation: C. Delacour, "Self-Adaptive Ising Machines for
+ * Constrained Optimization", arXiv 2501.04971.
+ *
+ * The method.  A constrained problem  min f(x) s.t. g(x) = 0,  x in {0,1}^N  (Sec. II, Eq. 2)
+ * is relaxed into the Lagrange function L = f + P ||g||^2 + lambda^T g (Eq. 3 and 5).  An Ising
+ * machine samples low-L states; after each run the multipliers take the subgradient step
+ * lambda <- lambda + eta g(x) (Algorithm 1).  The machine is a network of p-bits,
+ * I_i = sum_j J_ij m_j + h_i (Eq. 9), m_i = sign(tanh(beta I_i) + rand(-1,1)) (Eq. 10), updated
+ * one spin after the other with beta annealed linearly from 0 to beta_max (Sec. III-B).  The
+ * problems are knapsacks (Sec. IV): minimise c(x) = -x^T W x / 2 - h^T x subject to A x <= b
+ * (QKP: one constraint, W dense; MKP: several constraints, W absent).  Inequalities become
+ * equalities with binary slack spins, Q_k = floor(log2 b_k) + 1 per constraint (Sec. IV-A).
+ *
+ * Conventions used by every entry point.
+ *  - Status codes, never exceptions, cross the ABI.  On failure the thread-local message of
+ *    sais_last_error() says what was wrong.  No entry point falls back to a CPU path; a device
+ *    that is not sm_103 is SAIS_EUNSUPPORTED.
+ *  - "host" pointers are ordinary host memory; "device" pointers are CUDA device memory of the
+ *    problem's device.  The caller owns every pointer it passes.  sais_create_* copy the problem
+ *    data to the device, so host arrays may be freed when they return.  Device buffers passed to
+ *    sais_sample / sais_update_lambda are borrowed until the work queued on `stream` completes.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream.  All GPU
+ *    work of a call is queued on that stream; calls return without synchronising unless stated.
+ *  - A problem handle may hold a batch of `count` independent instances.  Per-instance device
+ *    arrays are laid out [count][chains][stride], with strides given by sais_problem_info:
+ *    words = ceil(max N'/32) for bit-packed states (spin i of a chain is bit i%32 of word i/32),
+ *    m_stride = max(1, max m) for per-constraint values.  Unused tail entries are written 0.
+ *  - Spin order: items 0..n-1, then the slack bits of constraint 0 (bit q has coefficient 2^q),
+ *    then those of constraint 1, and so on.
+ *  - Random numbers: instance j of a batch draws from Philox4x32-10 with key (seed + j, as two
+ *    32-bit words, low first) and counter (i/4, sweep t, chain c, outer iteration k); word i%4
+ *    gives rho = (2v+1)/2^24 - 1, v = word >> 8.  Equal arguments give equal results on every run.
+ *  - Scalars (sigma_f, sigma_g, P, beta_t, lambda) are FP32 values; the decision of Eq. 10 is the
+ *    one exact real arithmetic on those values gives, evaluated in FP32 with a rigorous error
+ *    bound and re-evaluated in FP64 when the bound cannot separate the two outcomes.
+ */
+#ifndef SAIS_H
+#define SAIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define SAIS_API __attribute__((visibility("default")))
+#else
+#define SAIS_API
+#endif
+
+typedef enum sais_status {
+    SAIS_OK = 0,
+    SAIS_EINVAL = 1,       /* bad argument: NULL where data is required, size out of range,
+                              W not symmetric / nonzero diagonal, b <= 0, A < 0, ...        */
+    SAIS_ENOMEM = 2,       /* a device or host allocation failed                             */
+    SAIS_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed                    */
+    SAIS_EOVERFLOW = 4,    /* an integer bound that keeps the fields exact would be broken:
+                              |h_i| + sum_j |W_ij| >= 2^24, |W_ij| > 32767, or
+                              b_k + sum_i a_ki(ext) >= 2^24                                 */
+    SAIS_ETIMEOUT = 5,     /* a bounded device wait gave up (status word set by a kernel)    */
+    SAIS_EUNSUPPORTED = 6  /* device is not sm_103, or sizes exceed what a kernel supports   */
+} sais_status;
+
+/* One knapsack instance in integer form (Sec. IV, Eq. 12 and 14):
+ *   minimise  c(x) = -x^T W x / 2 - h^T x   subject to   A x <= b,   x in {0,1}^n.
+ * All arrays are host memory, read during sais_create_* only. */
+typedef struct sais_problem_desc {
+    int32_t n;          /* items, >= 1                                                      */
+    int32_t m;          /* constraints (knapsacks), 0 <= m <= 32                            */
+    const int32_t *W;   /* n*n row-major pair values, symmetric, zero diagonal, |W_ij| <=
+                           32767; NULL for a linear objective (MKP)                          */
+    const int32_t *h;   /* n item values                                                    */
+    const int32_t *A;   /* m*n row-major weights, >= 0 (may be NULL when m == 0)            */
+    const int64_t *b;   /* m capacities, >= 1                                               */
+    float alpha;        /* penalty rule P = alpha d N' (Sec. III-A; Table I: QKP 2, MKP 5)  */
+    float density;      /* d in the penalty rule; < 0 selects the measured profit density
+                           (QKP: nonzero p_ij, i <= j, over n(n+1)/2) or 2/(N'+1) when W is
+                           NULL (Sec. IV-B)                                                   */
+    float penalty;      /* > 0: use this P instead of the alpha rule                        */
+} sais_problem_desc;
+
+/* Scalars derived from one instance on the host (no GPU involved). */
+typedef struct sais_problem_scalars {
+    int32_t n, m;
+    int32_t n_spins;         /* N' = n + sum_k Q_k                                          */
+    int32_t words;           /* ceil(N'/32)                                                 */
+    float sigma_f;           /* 1 / max(|W|, |h|)            (Sec. IV-A)                    */
+    float sigma_g;           /* 1 / max(|A|, |b|)            (Sec. IV-A)                    */
+    float penalty;           /* P                             (Sec. III-A)                  */
+    float reserved;
+    double density;          /* the d that entered P                                        */
+} sais_problem_scalars;
+
+typedef struct sais_problem sais_problem; /* opaque, owned by the library */
+
+typedef struct sais_layout {
+    int32_t count;           /* instances in the handle                                     */
+    int32_t max_spins;       /* max N' over the instances                                   */
+    int32_t words;           /* ceil(max N' / 32): stride of bit-packed states              */
+    int32_t m_stride;        /* max(1, max m): stride of per-constraint arrays              */
+    int32_t device;          /* CUDA device ordinal                                         */
+    int32_t has_quadratic;   /* 1 if any instance has W                                     */
+} sais_layout;
+
+typedef enum sais_variant {
+    SAIS_PLAIN = 0,          /* per-spin sampler: FP32 fields, rank-1 update on every flip  */
+    SAIS_BLOCKED = 1         /* k spins per block, rank-k field update on the tensor cores  */
+} sais_variant;
+
+/* One annealing run per chain (Sec. III-B): every chain starts at x = 0 and performs `sweeps`
+ * sequential sweeps, sweep t at beta_t = beta_max t / (sweeps-1) (beta_max when sweeps = 1). */
+typedef struct sais_sample_params {
+    int32_t chains;          /* chains per instance, >= 1                                   */
+    int32_t sweeps;          /* T >= 1                                                      */
+    float beta_max;          /* >= 0                                                        */
+    uint32_t iter;           /* outer-iteration index k (selects the random stream)         */
+    uint64_t seed;           /* instance j uses seed + j                                    */
+    int32_t variant;         /* sais_variant                                                */
+    int32_t block_k;         /* SAIS_BLOCKED: spins per block (16, 32 or 64); 0 = default   */
+    int32_t chains_per_cta;  /* 0 = library choice; else 32, 64 or 128                      */
+    int32_t reserved;
+} sais_sample_params;
+
+/* Algorithm 1 (Sec. III-A) on every instance of the handle. */
+typedef struct sais_solve_params {
+    int32_t iters;           /* K outer iterations, >= 1                                    */
+    int32_t chains;          /* chains per instance per iteration (the batch of samples)    */
+    int32_t sweeps;          /* sweeps per annealing run                                    */
+    float beta_max;
+    double eta;              /* step size of the multiplier update                          */
+    uint64_t seed;
+    uint32_t iter0;          /* index of the first iteration (resume: previous iter0 + K)   */
+    int32_t project_nonneg;  /* 1: lambda <- max(0, .) after each step                      */
+    int32_t variant;         /* sais_variant of the sampler                                 */
+    int32_t block_k;         /* as in sais_sample_params                                    */
+    int32_t chains_per_cta;  /* as in sais_sample_params                                    */
+    int32_t use_graph;       /* 1: replay the iteration as a captured CUDA graph            */
+    const float *lambda0;    /* host [count*m_stride] initial multipliers, or NULL for 0    */
+} sais_solve_params;
+
+/* Results of sais_solve, all caller-allocated HOST arrays (any may be NULL to skip it). */
+typedef struct sais_solve_result {
+    int64_t *best_cost;      /* [count] min c(x) over the stored feasible samples (Alg. 1,
+                                final line); INT64_MAX when none was feasible               */
+    uint32_t *best_x;        /* [count*words] the sample achieving it (first in (k, chain)
+                                order on ties)                                              */
+    int32_t *best_iter;      /* [count] its outer iteration k, -1 if none                   */
+    int32_t *best_chain;     /* [count] its chain, -1 if none                               */
+    int64_t *feasible_count; /* [count] feasible samples seen                               */
+    float *lambda_final;     /* [count*m_stride] multipliers after the last step            */
+    float *lambda_trace;     /* [iters*count*m_stride] multipliers after each step          */
+    double elapsed_ms;       /* device time of the iterations (CUDA events)                 */
+    int64_t spin_updates;    /* count * chains * sweeps * N' summed over instances and k    */
+} sais_solve_result;
+
+/* Slack extension, normalisation and penalty of one instance, computed on the host
+ * (Sec. III-A, IV-A, IV-B).  No GPU is touched.  Errors: SAIS_EINVAL, SAIS_EOVERFLOW. */
+SAIS_API sais_status sais_describe(const sais_problem_desc *desc, sais_problem_scalars *out);
+
+/* Validate one instance, build its slack-extended, normalised device form on `device` and
+ * return a handle in *out.  Errors: SAIS_EINVAL, SAIS_EOVERFLOW, SAIS_ENOMEM, SAIS_ECUDA,
+ * SAIS_EUNSUPPORTED (device not sm_103, or N' beyond the kernels' limit). */
+SAIS_API sais_status sais_create_problem(const sais_problem_desc *desc, int32_t device,
+                                         sais_problem **out);
+
+/* As sais_create_problem for `count` independent instances (descs[0..count-1]) held by one
+ * handle; instances may differ in n, m and N'. */
+SAIS_API sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count,
+                                       int32_t device, sais_problem **out);
+
+/* Free the device data of a handle (synchronises its device).  NULL is accepted. */
+SAIS_API sais_status sais_destroy_problem(sais_problem *p);
+
+SAIS_API sais_status sais_problem_info(const sais_problem *p, sais_layout *out);
+
+/* Scalars of instance `index` of a handle (as sais_describe computed them at creation). */
+SAIS_API sais_status sais_instance_scalars(const sais_problem *p, int32_t index,
+                                           sais_problem_scalars *out);
+
+/* The Ising-machine step of Algorithm 1 ("minimise L_k") as Sec. III-B runs it: one annealing
+ * run of p-bit Gibbs sweeps per chain at multipliers `lambda`, returning each chain's last
+ * sample x_k with its cost and constraint values.
+ *   lambda   device [count*m_stride] FP32 multipliers (read)
+ *   x        device [count*chains*words] bit-packed last samples (written)
+ *   cost     device [count*chains] int64 c(x) = -x^T W x / 2 - h^T x (written)
+ *   g        device [count*chains*m_stride] int64 g_k(x) = A_ext x - b, slack included
+ *   feasible device [count*chains] uint8, 1 iff A x <= b on the items (Sec. IV-A), or NULL
+ * Errors: SAIS_EINVAL (NULL buffers, chains < 1, sweeps < 1, beta_max < 0 or not finite, bad
+ * block_k / chains_per_cta), SAIS_EUNSUPPORTED, SAIS_ECUDA (launch failure). */
+SAIS_API sais_status sais_sample(sais_problem *p, const sais_sample_params *prm,
+                                 const float *lambda, uint32_t *x, int64_t *cost, int64_t *g,
+                                 uint8_t *feasible, void *stream);
+
+/* sais_sample that also records the state after every sweep:
+ *   trace  device [count*chains*sweeps*words] bit-packed states (written)
+ * Used to replay recorded sweeps decision by decision against a reference. */
+SAIS_API sais_status sais_sample_trace(sais_problem *p, const sais_sample_params *prm,
+                                       const float *lambda, uint32_t *x, int64_t *cost,
+                                       int64_t *g, uint8_t *feasible, uint32_t *trace,
+                                       void *stream);
+
+/* The multiplier step of Algorithm 1, lambda_k <- lambda_k + eta g_k(x), with the normalised
+ * constraint sigma_g g averaged over the `chains` samples of each instance and, if
+ * project_nonneg, projected on lambda >= 0.  The chain sum is exact (int64); mean and step are
+ * FP64 evaluated as mean = S/C, step = eta*(sigma_g*mean), lambda + step, rounded to FP32.
+ *   g       device [count*chains*m_stride] int64 (read), as written by sais_sample
+ *   lambda  device [count*m_stride] FP32 (read and written in place)
+ * Errors: SAIS_EINVAL, SAIS_ECUDA. */
+SAIS_API sais_status sais_update_lambda(sais_problem *p, const int64_t *g, int32_t chains,
+                                        double eta, int32_t project_nonneg, float *lambda,
+                                        void *stream);
+
+/* The "store feasible x_k" step of Algorithm 1 for one batch of samples (Sec. III-A; the
+ * feasibility test of Sec. IV-A): among the chains whose sample is feasible, the one of least
+ * cost (lowest chain index on ties) replaces the kept best of its instance when it is strictly
+ * better, so the kept sample is the first achiever in (iteration, chain) order; the number of
+ * feasible samples is added to feasible_count.
+ *   x, cost, feasible   device, as written by sais_sample for `chains` chains (read)
+ *   iter                outer iteration of the samples (stored with a new best)
+ *   best_cost       device [count] int64 (in/out; start at INT64_MAX)
+ *   best_x          device [count*words] (in/out)
+ *   best_iter, best_chain  device [count] int32 (in/out; start at -1)
+ *   feasible_count  device [count] int64 (in/out; start at 0)
+ * Errors: SAIS_EINVAL, SAIS_ECUDA. */
+SAIS_API sais_status sais_track_best(sais_problem *p, const uint32_t *x, const int64_t *cost,
+                                     const uint8_t *feasible, int32_t chains, uint32_t iter,
+                                     int64_t *best_cost, uint32_t *best_x, int32_t *best_iter,
+                                     int32_t *best_chain, int64_t *feasible_count,
+                                     void *stream);
+
+/* Algorithm 1 for `iters` iterations on every instance: per iteration one sais_sample batch,
+ * the feasible samples checked and the best kept, then sais_update_lambda.  The library owns
+ * the device scratch it needs for the call.  Synchronises `stream` before returning and fills
+ * the host arrays of `res`.  Errors: as sais_sample, plus SAIS_ENOMEM. */
+SAIS_API sais_status sais_solve(sais_problem *p, const sais_solve_params *prm,
+                                sais_solve_result *res, void *stream);
+
+/* Static text for a status code. */
+SAIS_API const char *sais_status_string(sais_status s);
+
+/* Message of the last failing call on this thread ("" if none). */
+SAIS_API const char *sais_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SAIS_H */

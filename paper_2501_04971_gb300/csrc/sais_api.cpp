@@ -1,0 +1,765 @@
+// sais_api.cpp -- host side of libsais: argument checks, the slack-extended and normalised
+// device form of each instance, and the entry points declared in include/sais.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "sais.h"
+#include "sais_internal.h"
+
+namespace sais {
+size_t plain_smem_bytes(int max_npad, int max_words, bool any_w, int cpb);
+}
+
+using namespace sais;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+sais_status fail(sais_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+#define SAIS_CUDA(expr)                                                                   \
+    do {                                                                                  \
+        cudaError_t e_ = (expr);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(e_ == cudaErrorMemoryAllocation ? SAIS_ENOMEM : SAIS_ECUDA,      \
+                        "%s: %s", #expr, cudaGetErrorString(e_));                         \
+    } while (0)
+
+constexpr int64_t kExact24 = int64_t(1) << 24;
+
+int32_t binary_digits(int64_t b) {  // Q = floor(log2 b) + 1 for b >= 1 (Sec. IV-A)
+    int32_t q = 0;
+    for (; b > 0; b >>= 1) ++q;
+    return q;
+}
+
+// One instance after validation, slack extension and normalisation (host copy).
+struct HostInst {
+    int32_t n = 0, m = 0, nprime = 0, npad = 0, words = 0;
+    bool has_w = false;
+    float sf = 1.f, sg = 1.f, P = 0.f;
+    double d = 0.0, psg2 = 0.0;
+    float kappa = 0.f;
+    bool need_lo = false;                  // some |W| > 256: BF16 hi/lo split
+    std::vector<int32_t> Q, slack_off;     // m, m+1
+    std::vector<int32_t> acol;             // nprime x m (spin-major)
+    std::vector<float> D, asum;            // nprime
+    std::vector<int32_t> b;                // m
+    std::vector<float> hF;                 // npad
+    const int32_t *W = nullptr;            // borrowed from the descriptor during creation
+};
+
+sais_status build_host(const sais_problem_desc *d, HostInst &h) {
+    if (!d) return fail(SAIS_EINVAL, "descriptor is NULL");
+    if (d->n < 1) return fail(SAIS_EINVAL, "n = %d: need at least one item", d->n);
+    if (d->m < 0 || d->m > kMaxConstraints)
+        return fail(SAIS_EINVAL, "m = %d: need 0 <= m <= %d", d->m, kMaxConstraints);
+    if (!d->h) return fail(SAIS_EINVAL, "h is NULL");
+    if (d->m > 0 && (!d->A || !d->b)) return fail(SAIS_EINVAL, "A or b is NULL with m > 0");
+    if (!std::isfinite(d->alpha) || !std::isfinite(d->density) || !std::isfinite(d->penalty))
+        return fail(SAIS_EINVAL, "alpha, density and penalty must be finite");
+    const int32_t n = d->n, m = d->m;
+    h.n = n;
+    h.m = m;
+    h.has_w = d->W != nullptr;
+    h.W = d->W;
+
+    // Integer checks: W symmetric with zero diagonal and int16 range; A >= 0; b >= 1.
+    int64_t maxabs_f = 0, nz = 0, max_w = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        int64_t row = std::llabs((int64_t)d->h[i]);
+        maxabs_f = std::max(maxabs_f, row);
+        if (d->h[i] != 0) ++nz;
+        if (h.has_w) {
+            for (int32_t j = 0; j < n; ++j) {
+                const int32_t w = d->W[(size_t)i * n + j];
+                if (w != d->W[(size_t)j * n + i])
+                    return fail(SAIS_EINVAL, "W is not symmetric at (%d,%d)", i, j);
+                if (i == j && w != 0) return fail(SAIS_EINVAL, "W has nonzero diagonal at %d", i);
+                if (w > 32767 || w < -32767)
+                    return fail(SAIS_EOVERFLOW, "|W(%d,%d)| = %d exceeds 32767", i, j, w);
+                const int64_t aw = std::llabs((int64_t)w);
+                maxabs_f = std::max(maxabs_f, aw);
+                max_w = std::max(max_w, aw);
+                row += aw;
+                if (j > i && w != 0) ++nz;
+            }
+        }
+        if (row >= kExact24)
+            return fail(SAIS_EOVERFLOW,
+                        "item %d: |h| + sum |W| = %lld >= 2^24 breaks the exact FP32 field", i,
+                        (long long)row);
+    }
+    h.need_lo = max_w > 256;
+    int64_t maxabs_g = 0;
+    h.Q.assign(m, 0);
+    h.slack_off.assign(m + 1, 0);
+    int32_t nprime = n;
+    for (int32_t k = 0; k < m; ++k) {
+        const int64_t bk = d->b[k];
+        if (bk < 1) return fail(SAIS_EINVAL, "b[%d] = %lld: capacities must be >= 1", k, (long long)bk);
+        int64_t rowsum = 0;
+        for (int32_t i = 0; i < n; ++i) {
+            const int32_t a = d->A[(size_t)k * n + i];
+            if (a < 0) return fail(SAIS_EINVAL, "A(%d,%d) = %d is negative", k, i, a);
+            rowsum += a;
+            maxabs_g = std::max(maxabs_g, (int64_t)a);
+        }
+        maxabs_g = std::max(maxabs_g, bk);
+        h.Q[k] = binary_digits(bk);
+        h.slack_off[k] = nprime;
+        nprime += h.Q[k];
+        // |g_k| <= max(b_k, sum_i a_ki + 2^Q - 1 - b_k) must stay exact in FP32 / int32
+        const int64_t span = rowsum + ((int64_t(1) << h.Q[k]) - 1) + bk;
+        if (span >= kExact24)
+            return fail(SAIS_EOVERFLOW,
+                        "constraint %d: b + sum a + slack range = %lld >= 2^24", k,
+                        (long long)span);
+    }
+    h.slack_off[m] = nprime;
+    h.nprime = nprime;
+    h.npad = (nprime + kSpinPad - 1) / kSpinPad * kSpinPad;
+    h.words = (nprime + 31) / 32;
+
+    // Scalars (Sec. III-A, IV-A, IV-B), each rounded once to FP32.
+    h.sf = maxabs_f > 0 ? (float)(1.0 / (double)maxabs_f) : 1.0f;
+    h.sg = maxabs_g > 0 ? (float)(1.0 / (double)maxabs_g) : 1.0f;
+    if (d->density >= 0.0f)
+        h.d = (double)d->density;
+    else if (!h.has_w)
+        h.d = 2.0 / ((double)nprime + 1.0);
+    else
+        h.d = (double)nz / (0.5 * (double)n * (double)(n + 1));
+    h.P = d->penalty > 0.0f ? d->penalty : (float)((double)d->alpha * h.d * (double)nprime);
+    if (!(h.P >= 0.0f) || !std::isfinite(h.P)) return fail(SAIS_EINVAL, "penalty P is negative or not finite");
+    h.psg2 = (double)h.P * (double)h.sg * (double)h.sg;
+    h.kappa = (float)(2.0 * h.psg2);
+
+    // Spin-major constraint columns of A_ext, D_i and sum_k a_ki.
+    h.acol.assign((size_t)nprime * std::max(m, 1), 0);
+    h.D.assign(nprime, 0.f);
+    h.asum.assign(nprime, 0.f);
+    h.b.assign(m, 0);
+    for (int32_t k = 0; k < m; ++k) {
+        h.b[k] = (int32_t)d->b[k];
+        for (int32_t i = 0; i < n; ++i) h.acol[(size_t)i * m + k] = d->A[(size_t)k * n + i];
+        for (int32_t q = 0; q < h.Q[k]; ++q)
+            h.acol[(size_t)(h.slack_off[k] + q) * m + k] = 1 << q;
+    }
+    for (int32_t i = 0; i < nprime; ++i) {
+        int64_t s2 = 0, s1 = 0;
+        for (int32_t k = 0; k < m; ++k) {
+            const int64_t a = h.acol[(size_t)i * m + k];
+            s2 += a * a;
+            s1 += a;
+        }
+        h.D[i] = (float)(h.psg2 * (double)s2);
+        h.asum[i] = (float)s1;
+    }
+    h.hF.assign(h.npad, 0.f);
+    for (int32_t i = 0; i < n; ++i) h.hF[i] = (float)d->h[i];
+    return SAIS_OK;
+}
+
+uint16_t bf16_bits(float f) {  // f is an integer of magnitude < 2^16: round to nearest even
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    const uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7FFFu + lsb;
+    return (uint16_t)(u >> 16);
+}
+
+float bf16_value(uint16_t b) {
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct sais_problem {
+    int device = 0;
+    int count = 0;
+    int max_spins = 0, max_npad = 0, max_npad_w = 0, words = 0, m_stride = 1, max_m = 0;
+    bool any_w = false;
+    std::vector<HostInst> host;   // host copies (W pointer cleared after creation)
+    void *pool = nullptr;         // one device allocation for all instance arrays
+    InstDev *d_inst = nullptr;    // device array of count records (inside pool)
+};
+
+extern "C" {
+
+const char *sais_status_string(sais_status s) {
+    switch (s) {
+        case SAIS_OK: return "ok";
+        case SAIS_EINVAL: return "invalid argument";
+        case SAIS_ENOMEM: return "out of memory";
+        case SAIS_ECUDA: return "CUDA error";
+        case SAIS_EOVERFLOW: return "integer bound for exact fields exceeded";
+        case SAIS_ETIMEOUT: return "bounded device wait timed out";
+        case SAIS_EUNSUPPORTED: return "unsupported device or size";
+    }
+    return "unknown status";
+}
+
+const char *sais_last_error(void) { return g_last_error.c_str(); }
+
+sais_status sais_describe(const sais_problem_desc *desc, sais_problem_scalars *out) {
+    if (!out) return fail(SAIS_EINVAL, "out is NULL");
+    HostInst h;
+    sais_status s = build_host(desc, h);
+    if (s != SAIS_OK) return s;
+    out->n = h.n;
+    out->m = h.m;
+    out->n_spins = h.nprime;
+    out->words = h.words;
+    out->sigma_f = h.sf;
+    out->sigma_g = h.sg;
+    out->penalty = h.P;
+    out->reserved = 0.f;
+    out->density = h.d;
+    return SAIS_OK;
+}
+
+sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int32_t device,
+                              sais_problem **out) {
+    if (!out) return fail(SAIS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!descs || count < 1) return fail(SAIS_EINVAL, "need count >= 1 descriptors");
+    if (count > 65535) return fail(SAIS_EUNSUPPORTED, "count = %d: at most 65535 instances", count);
+    int ndev = 0;
+    SAIS_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev)
+        return fail(SAIS_EINVAL, "device %d out of range (%d devices)", device, ndev);
+    cudaDeviceProp prop;
+    SAIS_CUDA(cudaGetDeviceProperties(&prop, device));
+    if (!(prop.major == 10 && prop.minor == 3))
+        return fail(SAIS_EUNSUPPORTED, "device %d is sm_%d%d; libsais is built for sm_103a",
+                    device, prop.major, prop.minor);
+
+    sais_problem *p = new (std::nothrow) sais_problem;
+    if (!p) return fail(SAIS_ENOMEM, "host allocation failed");
+    p->device = device;
+    p->count = count;
+    p->host.resize(count);
+    for (int32_t j = 0; j < count; ++j) {
+        sais_status s = build_host(descs + j, p->host[j]);
+        if (s != SAIS_OK) {
+            std::string msg = g_last_error;
+            delete p;
+            return fail(s, "instance %d: %s", j, msg.c_str());
+        }
+        const HostInst &h = p->host[j];
+        p->max_spins = std::max(p->max_spins, h.nprime);
+        p->max_npad = std::max(p->max_npad, h.npad);
+        if (h.has_w) p->max_npad_w = std::max(p->max_npad_w, h.npad);
+        p->max_m = std::max(p->max_m, h.m);
+        p->any_w = p->any_w || h.has_w;
+    }
+    p->words = (p->max_spins + 31) / 32;
+    p->m_stride = std::max(1, p->max_m);
+
+    // Pool layout: [InstDev x count] then per instance W, Wbf(, Wbf_lo), hF, acol, D, asum, b,
+    // slack_off, each 256-byte aligned.
+    struct Off {
+        size_t W, Wbf, Wlo, hF, acol, D, asum, b, so;
+    };
+    std::vector<Off> off(count);
+    size_t cur = align_up(sizeof(InstDev) * count, 256);
+    for (int32_t j = 0; j < count; ++j) {
+        const HostInst &h = p->host[j];
+        const size_t nn = (size_t)h.npad * h.npad;
+        Off &o = off[j];
+        o.W = o.Wbf = o.Wlo = SIZE_MAX;
+        if (h.has_w) {
+            o.W = cur;
+            cur = align_up(cur + nn * 2, 256);
+            o.Wbf = cur;
+            cur = align_up(cur + nn * 2, 256);
+            if (h.need_lo) {
+                o.Wlo = cur;
+                cur = align_up(cur + nn * 2, 256);
+            }
+        }
+        o.hF = cur;
+        cur = align_up(cur + (size_t)h.npad * 4, 256);
+        o.acol = cur;
+        cur = align_up(cur + h.acol.size() * 4, 256);
+        o.D = cur;
+        cur = align_up(cur + (size_t)h.nprime * 4, 256);
+        o.asum = cur;
+        cur = align_up(cur + (size_t)h.nprime * 4, 256);
+        o.b = cur;
+        cur = align_up(cur + (size_t)std::max(h.m, 1) * 4, 256);
+        o.so = cur;
+        cur = align_up(cur + (size_t)(h.m + 1) * 4, 256);
+    }
+    std::vector<unsigned char> stage;
+    try {
+        stage.assign(cur, 0);
+    } catch (...) {
+        delete p;
+        return fail(SAIS_ENOMEM, "host staging allocation of %zu bytes failed", cur);
+    }
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(device);
+    cudaError_t ce = cudaMalloc(&p->pool, cur);
+    if (ce != cudaSuccess) {
+        cudaSetDevice(prev);
+        delete p;
+        return fail(ce == cudaErrorMemoryAllocation ? SAIS_ENOMEM : SAIS_ECUDA,
+                    "cudaMalloc(%zu): %s", cur, cudaGetErrorString(ce));
+    }
+    unsigned char *base = static_cast<unsigned char *>(p->pool);
+    InstDev *recs = reinterpret_cast<InstDev *>(stage.data());
+    for (int32_t j = 0; j < count; ++j) {
+        HostInst &h = p->host[j];
+        const Off &o = off[j];
+        InstDev r{};
+        r.n = h.n;
+        r.m = h.m;
+        r.nprime = h.nprime;
+        r.npad = h.npad;
+        r.words = h.words;
+        r.has_w = h.has_w ? 1 : 0;
+        r.sigma_f = h.sf;
+        r.sigma_g = h.sg;
+        r.P = h.P;
+        r.kappa = h.kappa;
+        r.psg2 = h.psg2;
+        if (h.has_w) {
+            int16_t *W16 = reinterpret_cast<int16_t *>(stage.data() + o.W);
+            uint16_t *Wb = reinterpret_cast<uint16_t *>(stage.data() + o.Wbf);
+            uint16_t *Wl = h.need_lo ? reinterpret_cast<uint16_t *>(stage.data() + o.Wlo) : nullptr;
+            for (int32_t i = 0; i < h.n; ++i)
+                for (int32_t jj = 0; jj < h.n; ++jj) {
+                    const int32_t w = h.W[(size_t)i * h.n + jj];
+                    const size_t e = (size_t)i * h.npad + jj;
+                    W16[e] = (int16_t)w;
+                    const uint16_t hi = bf16_bits((float)w);
+                    Wb[e] = hi;
+                    if (Wl) Wl[e] = bf16_bits((float)w - bf16_value(hi));
+                }
+            r.W = reinterpret_cast<const int16_t *>(base + o.W);
+            r.Wbf = reinterpret_cast<const uint16_t *>(base + o.Wbf);
+            r.Wbf_lo = h.need_lo ? reinterpret_cast<const uint16_t *>(base + o.Wlo) : nullptr;
+        }
+        std::memcpy(stage.data() + o.hF, h.hF.data(), h.hF.size() * 4);
+        std::memcpy(stage.data() + o.acol, h.acol.data(), h.acol.size() * 4);
+        std::memcpy(stage.data() + o.D, h.D.data(), h.D.size() * 4);
+        std::memcpy(stage.data() + o.asum, h.asum.data(), h.asum.size() * 4);
+        if (h.m) std::memcpy(stage.data() + o.b, h.b.data(), h.b.size() * 4);
+        std::memcpy(stage.data() + o.so, h.slack_off.data(), h.slack_off.size() * 4);
+        r.hF = reinterpret_cast<const float *>(base + o.hF);
+        r.acol = reinterpret_cast<const int32_t *>(base + o.acol);
+        r.D = reinterpret_cast<const float *>(base + o.D);
+        r.asum = reinterpret_cast<const float *>(base + o.asum);
+        r.b = reinterpret_cast<const int32_t *>(base + o.b);
+        r.slack_off = reinterpret_cast<const int32_t *>(base + o.so);
+        recs[j] = r;
+        h.W = nullptr;
+    }
+    ce = cudaMemcpy(p->pool, stage.data(), cur, cudaMemcpyHostToDevice);
+    cudaSetDevice(prev);
+    if (ce != cudaSuccess) {
+        cudaFree(p->pool);
+        delete p;
+        return fail(SAIS_ECUDA, "copy of problem data: %s", cudaGetErrorString(ce));
+    }
+    p->d_inst = reinterpret_cast<InstDev *>(p->pool);
+    *out = p;
+    return SAIS_OK;
+}
+
+sais_status sais_create_problem(const sais_problem_desc *desc, int32_t device,
+                                sais_problem **out) {
+    return sais_create_batch(desc, 1, device, out);
+}
+
+sais_status sais_destroy_problem(sais_problem *p) {
+    if (!p) return SAIS_OK;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(p->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (p->pool) cudaFree(p->pool);
+    cudaSetDevice(prev);
+    delete p;
+    if (e != cudaSuccess) return fail(SAIS_ECUDA, "synchronize before free: %s", cudaGetErrorString(e));
+    return SAIS_OK;
+}
+
+sais_status sais_problem_info(const sais_problem *p, sais_layout *out) {
+    if (!p || !out) return fail(SAIS_EINVAL, "NULL argument");
+    out->count = p->count;
+    out->max_spins = p->max_spins;
+    out->words = p->words;
+    out->m_stride = p->m_stride;
+    out->device = p->device;
+    out->has_quadratic = p->any_w ? 1 : 0;
+    return SAIS_OK;
+}
+
+sais_status sais_instance_scalars(const sais_problem *p, int32_t index, sais_problem_scalars *out) {
+    if (!p || !out) return fail(SAIS_EINVAL, "NULL argument");
+    if (index < 0 || index >= p->count) return fail(SAIS_EINVAL, "index %d out of range", index);
+    const HostInst &h = p->host[index];
+    out->n = h.n;
+    out->m = h.m;
+    out->n_spins = h.nprime;
+    out->words = h.words;
+    out->sigma_f = h.sf;
+    out->sigma_g = h.sg;
+    out->penalty = h.P;
+    out->reserved = 0.f;
+    out->density = h.d;
+    return SAIS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+struct DeviceGuard {
+    int prev = 0;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        cudaSetDevice(dev);
+    }
+    ~DeviceGuard() { cudaSetDevice(prev); }
+};
+
+sais_status check_sample_params(const sais_problem *p, const sais_sample_params *prm) {
+    if (!p || !prm) return fail(SAIS_EINVAL, "NULL problem or params");
+    if (prm->chains < 1) return fail(SAIS_EINVAL, "chains = %d: need >= 1", prm->chains);
+    if (prm->sweeps < 1) return fail(SAIS_EINVAL, "sweeps = %d: need >= 1", prm->sweeps);
+    if (!(prm->beta_max >= 0.0f) || !std::isfinite(prm->beta_max))
+        return fail(SAIS_EINVAL, "beta_max must be finite and >= 0");
+    if (prm->variant != SAIS_PLAIN && prm->variant != SAIS_BLOCKED)
+        return fail(SAIS_EINVAL, "unknown variant %d", prm->variant);
+    if (prm->chains_per_cta != 0 && prm->chains_per_cta != 32 && prm->chains_per_cta != 64 &&
+        prm->chains_per_cta != 128)
+        return fail(SAIS_EINVAL, "chains_per_cta = %d: need 0, 32, 64 or 128", prm->chains_per_cta);
+    if (prm->block_k != 0 && prm->block_k != 16 && prm->block_k != 32 && prm->block_k != 64)
+        return fail(SAIS_EINVAL, "block_k = %d: need 0, 16, 32 or 64", prm->block_k);
+    return SAIS_OK;
+}
+
+// Plain sampler CTA size: one warp per CTA by default (shared memory, not threads, bounds how
+// many chains an SM holds, so small CTAs pack best), or the caller's choice.
+sais_status plain_cpb(const sais_problem *p, int want, int *cpb) {
+    const int c = want ? want : 32;
+    const size_t need = plain_smem_bytes(p->max_npad_w, p->words, p->any_w, c);
+    if (need > (size_t)kMaxPlainSmem)
+        return fail(SAIS_EUNSUPPORTED,
+                    "plain sampler: N'=%d needs %zu bytes of shared memory at %d chains per CTA",
+                    p->max_spins, need, c);
+    *cpb = c;
+    return SAIS_OK;
+}
+
+sais_status enqueue_sample(sais_problem *p, const sais_sample_params *prm, const float *lambda,
+                           const uint32_t *iter_dev, uint32_t *x, int64_t *cost, int64_t *g,
+                           uint8_t *feasible, uint32_t *trace, cudaStream_t st) {
+    SampleArgs a{};
+    a.inst = p->d_inst;
+    a.count = p->count;
+    a.chains = prm->chains;
+    a.sweeps = prm->sweeps;
+    a.beta_max = prm->beta_max;
+    a.iter = prm->iter;
+    a.iter_dev = iter_dev;
+    a.seed = prm->seed;
+    a.words = p->words;
+    a.m_stride = p->m_stride;
+    a.lambda = lambda;
+    a.x = x;
+    a.cost = cost;
+    a.g = g;
+    a.feasible = feasible;
+    a.trace = trace;
+    a.status = nullptr;
+    cudaError_t e;
+    if (prm->variant == SAIS_BLOCKED) {
+        const char *why = nullptr;
+        e = launch_blocked_sampler(a, p->max_m, p->max_npad, p->words,
+                                   prm->block_k ? prm->block_k : 32, st, &why);
+        if (why) return fail(SAIS_EUNSUPPORTED, "blocked sampler: %s", why);
+    } else {
+        int cpb = 0;
+        sais_status s = plain_cpb(p, prm->chains_per_cta, &cpb);
+        if (s != SAIS_OK) return s;
+        e = launch_plain_sampler(a, p->max_m, p->max_npad_w, p->words, cpb, st);
+    }
+    if (e != cudaSuccess) return fail(SAIS_ECUDA, "sampler launch: %s", cudaGetErrorString(e));
+    return SAIS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sais_status sais_sample(sais_problem *p, const sais_sample_params *prm, const float *lambda,
+                        uint32_t *x, int64_t *cost, int64_t *g, uint8_t *feasible, void *stream) {
+    sais_status s = check_sample_params(p, prm);
+    if (s != SAIS_OK) return s;
+    if (!lambda || !x || !cost || !g) return fail(SAIS_EINVAL, "NULL device buffer");
+    DeviceGuard dg(p->device);
+    return enqueue_sample(p, prm, lambda, nullptr, x, cost, g, feasible, nullptr,
+                          static_cast<cudaStream_t>(stream));
+}
+
+sais_status sais_sample_trace(sais_problem *p, const sais_sample_params *prm, const float *lambda,
+                              uint32_t *x, int64_t *cost, int64_t *g, uint8_t *feasible,
+                              uint32_t *trace, void *stream) {
+    sais_status s = check_sample_params(p, prm);
+    if (s != SAIS_OK) return s;
+    if (!lambda || !x || !cost || !g || !trace) return fail(SAIS_EINVAL, "NULL device buffer");
+    DeviceGuard dg(p->device);
+    return enqueue_sample(p, prm, lambda, nullptr, x, cost, g, feasible, trace,
+                          static_cast<cudaStream_t>(stream));
+}
+
+sais_status sais_update_lambda(sais_problem *p, const int64_t *g, int32_t chains, double eta,
+                               int32_t project_nonneg, float *lambda, void *stream) {
+    if (!p || !g || !lambda) return fail(SAIS_EINVAL, "NULL argument");
+    if (chains < 1) return fail(SAIS_EINVAL, "chains = %d: need >= 1", chains);
+    if (!std::isfinite(eta)) return fail(SAIS_EINVAL, "eta must be finite");
+    DeviceGuard dg(p->device);
+    PostArgs a{};
+    a.inst = p->d_inst;
+    a.count = p->count;
+    a.chains = chains;
+    a.words = p->words;
+    a.m_stride = p->m_stride;
+    a.eta = eta;
+    a.project = project_nonneg ? 1 : 0;
+    a.track_best = 0;
+    a.do_lambda = 1;
+    a.g = g;
+    a.lambda = lambda;
+    cudaError_t e = launch_post(a, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(SAIS_ECUDA, "multiplier update launch: %s", cudaGetErrorString(e));
+    return SAIS_OK;
+}
+
+sais_status sais_track_best(sais_problem *p, const uint32_t *x, const int64_t *cost,
+                            const uint8_t *feasible, int32_t chains, uint32_t iter,
+                            int64_t *best_cost, uint32_t *best_x, int32_t *best_iter,
+                            int32_t *best_chain, int64_t *feasible_count, void *stream) {
+    if (!p || !x || !cost || !feasible || !best_cost || !best_x || !best_iter || !best_chain ||
+        !feasible_count)
+        return fail(SAIS_EINVAL, "NULL argument");
+    if (chains < 1) return fail(SAIS_EINVAL, "chains = %d: need >= 1", chains);
+    DeviceGuard dg(p->device);
+    PostArgs a{};
+    a.inst = p->d_inst;
+    a.count = p->count;
+    a.chains = chains;
+    a.words = p->words;
+    a.m_stride = p->m_stride;
+    a.track_best = 1;
+    a.do_lambda = 0;
+    a.x = x;
+    a.cost = cost;
+    a.feasible = feasible;
+    a.iter = iter;
+    a.best_cost = best_cost;
+    a.best_x = best_x;
+    a.best_iter = best_iter;
+    a.best_chain = best_chain;
+    a.feasible_count = feasible_count;
+    cudaError_t e = launch_post(a, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(SAIS_ECUDA, "best-tracking launch: %s", cudaGetErrorString(e));
+    return SAIS_OK;
+}
+
+sais_status sais_solve(sais_problem *p, const sais_solve_params *prm, sais_solve_result *res,
+                       void *stream) {
+    if (!p || !prm || !res) return fail(SAIS_EINVAL, "NULL argument");
+    if (prm->iters < 1) return fail(SAIS_EINVAL, "iters = %d: need >= 1", prm->iters);
+    if (!std::isfinite(prm->eta)) return fail(SAIS_EINVAL, "eta must be finite");
+    sais_sample_params sp{};
+    sp.chains = prm->chains;
+    sp.sweeps = prm->sweeps;
+    sp.beta_max = prm->beta_max;
+    sp.iter = prm->iter0;
+    sp.seed = prm->seed;
+    sp.variant = prm->variant;
+    sp.block_k = prm->block_k;
+    sp.chains_per_cta = prm->chains_per_cta;
+    sais_status s = check_sample_params(p, &sp);
+    if (s != SAIS_OK) return s;
+    DeviceGuard dg(p->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    const int count = p->count, C = prm->chains, K = prm->iters;
+    const size_t nch = (size_t)count * C;
+    // Device scratch owned by this call.
+    size_t sz_lam = (size_t)count * p->m_stride * 4, sz_x = nch * p->words * 4, sz_cost = nch * 8,
+           sz_g = nch * p->m_stride * 8, sz_feas = nch, sz_bc = (size_t)count * 8,
+           sz_bx = (size_t)count * p->words * 4, sz_bi = (size_t)count * 4,
+           sz_fc = (size_t)count * 8, sz_tr = (size_t)K * count * p->m_stride * 4;
+    size_t offs[12], cur = 0;
+    const size_t sizes[12] = {sz_lam, sz_x, sz_cost, sz_g, sz_feas, sz_bc, sz_bx, sz_bi, sz_bi, sz_fc, sz_tr, 4};
+    for (int i = 0; i < 12; ++i) {
+        offs[i] = cur;
+        cur = align_up(cur + sizes[i], 256);
+    }
+    unsigned char *scr = nullptr;
+    SAIS_CUDA(cudaMalloc(&scr, cur));
+    struct Free {
+        unsigned char *q;
+        ~Free() { cudaFree(q); }
+    } free_scr{scr};
+    float *d_lam = reinterpret_cast<float *>(scr + offs[0]);
+    uint32_t *d_x = reinterpret_cast<uint32_t *>(scr + offs[1]);
+    int64_t *d_cost = reinterpret_cast<int64_t *>(scr + offs[2]);
+    int64_t *d_g = reinterpret_cast<int64_t *>(scr + offs[3]);
+    uint8_t *d_feas = scr + offs[4];
+    int64_t *d_bc = reinterpret_cast<int64_t *>(scr + offs[5]);
+    uint32_t *d_bx = reinterpret_cast<uint32_t *>(scr + offs[6]);
+    int32_t *d_bi = reinterpret_cast<int32_t *>(scr + offs[7]);
+    int32_t *d_bch = reinterpret_cast<int32_t *>(scr + offs[8]);
+    int64_t *d_fc = reinterpret_cast<int64_t *>(scr + offs[9]);
+    float *d_tr = reinterpret_cast<float *>(scr + offs[10]);
+    uint32_t *d_iter = reinterpret_cast<uint32_t *>(scr + offs[11]);
+
+    std::vector<int64_t> h_bc(count, std::numeric_limits<int64_t>::max());
+    std::vector<int32_t> h_m1(count, -1);
+    SAIS_CUDA(cudaMemsetAsync(scr, 0, cur, st));
+    if (prm->lambda0)
+        SAIS_CUDA(cudaMemcpyAsync(d_lam, prm->lambda0, sz_lam, cudaMemcpyHostToDevice, st));
+    SAIS_CUDA(cudaMemcpyAsync(d_bc, h_bc.data(), sz_bc, cudaMemcpyHostToDevice, st));
+    SAIS_CUDA(cudaMemcpyAsync(d_bi, h_m1.data(), sz_bi, cudaMemcpyHostToDevice, st));
+    SAIS_CUDA(cudaMemcpyAsync(d_bch, h_m1.data(), sz_bi, cudaMemcpyHostToDevice, st));
+    SAIS_CUDA(cudaMemcpyAsync(d_iter, &prm->iter0, 4, cudaMemcpyHostToDevice, st));
+
+    PostArgs pa{};
+    pa.inst = p->d_inst;
+    pa.count = count;
+    pa.chains = C;
+    pa.words = p->words;
+    pa.m_stride = p->m_stride;
+    pa.eta = prm->eta;
+    pa.project = prm->project_nonneg ? 1 : 0;
+    pa.track_best = 1;
+    pa.do_lambda = 1;
+    pa.x = d_x;
+    pa.cost = d_cost;
+    pa.g = d_g;
+    pa.feasible = d_feas;
+    pa.lambda = d_lam;
+    pa.lambda_trace = d_tr;
+    pa.iter_dev = d_iter;
+    pa.iter0 = prm->iter0;
+    pa.best_cost = d_bc;
+    pa.best_x = d_bx;
+    pa.best_iter = d_bi;
+    pa.best_chain = d_bch;
+    pa.feasible_count = d_fc;
+
+    auto one_iteration = [&]() -> sais_status {
+        sais_status r = enqueue_sample(p, &sp, d_lam, d_iter, d_x, d_cost, d_g, d_feas, nullptr, st);
+        if (r != SAIS_OK) return r;
+        cudaError_t e = launch_post(pa, st);
+        if (e == cudaSuccess) e = launch_advance_iter(d_iter, st);
+        if (e != cudaSuccess) return fail(SAIS_ECUDA, "post launch: %s", cudaGetErrorString(e));
+        return SAIS_OK;
+    };
+
+    cudaEvent_t ev0, ev1;
+    SAIS_CUDA(cudaEventCreate(&ev0));
+    SAIS_CUDA(cudaEventCreate(&ev1));
+    struct Ev {
+        cudaEvent_t a, b;
+        ~Ev() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } evs{ev0, ev1};
+    cudaGraphExec_t exec = nullptr;
+    if (prm->use_graph) {
+        cudaStream_t cap = st;
+        bool own = false;
+        if (cap == nullptr) {  // the legacy stream cannot be captured
+            SAIS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+            own = true;
+        }
+        cudaStream_t saved = st;
+        st = cap;
+        cudaGraph_t graph = nullptr;
+        SAIS_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed));
+        sais_status r = one_iteration();
+        cudaError_t e = cudaStreamEndCapture(cap, &graph);
+        if (r != SAIS_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            if (own) cudaStreamDestroy(cap);
+            return r;
+        }
+        if (e != cudaSuccess) {
+            if (own) cudaStreamDestroy(cap);
+            return fail(SAIS_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        }
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (own) cudaStreamDestroy(cap);
+        st = saved;
+        if (e != cudaSuccess) return fail(SAIS_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    SAIS_CUDA(cudaEventRecord(ev0, st));
+    for (int k = 0; k < K; ++k) {
+        if (exec) {
+            cudaError_t e = cudaGraphLaunch(exec, st);
+            if (e != cudaSuccess) {
+                cudaGraphExecDestroy(exec);
+                return fail(SAIS_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+            }
+        } else {
+            sais_status r = one_iteration();
+            if (r != SAIS_OK) return r;
+        }
+    }
+    SAIS_CUDA(cudaEventRecord(ev1, st));
+    if (exec) cudaGraphExecDestroy(exec);
+
+    if (res->best_cost) SAIS_CUDA(cudaMemcpyAsync(res->best_cost, d_bc, sz_bc, cudaMemcpyDeviceToHost, st));
+    if (res->best_x) SAIS_CUDA(cudaMemcpyAsync(res->best_x, d_bx, sz_bx, cudaMemcpyDeviceToHost, st));
+    if (res->best_iter) SAIS_CUDA(cudaMemcpyAsync(res->best_iter, d_bi, sz_bi, cudaMemcpyDeviceToHost, st));
+    if (res->best_chain) SAIS_CUDA(cudaMemcpyAsync(res->best_chain, d_bch, sz_bi, cudaMemcpyDeviceToHost, st));
+    if (res->feasible_count) SAIS_CUDA(cudaMemcpyAsync(res->feasible_count, d_fc, sz_fc, cudaMemcpyDeviceToHost, st));
+    if (res->lambda_final) SAIS_CUDA(cudaMemcpyAsync(res->lambda_final, d_lam, sz_lam, cudaMemcpyDeviceToHost, st));
+    if (res->lambda_trace) SAIS_CUDA(cudaMemcpyAsync(res->lambda_trace, d_tr, sz_tr, cudaMemcpyDeviceToHost, st));
+    SAIS_CUDA(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    SAIS_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+    res->elapsed_ms = ms;
+    int64_t upd = 0;
+    for (const HostInst &h : p->host) upd += (int64_t)h.nprime;
+    res->spin_updates = upd * C * (int64_t)prm->sweeps * K;
+    return SAIS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,102 @@
+// sais_internal.h -- data shared by the host code and the kernels of libsais.
+//
+// One instance of the slack-extended, normalised knapsack problem lives on the device as an
+// InstDev record plus the arrays it points to.  All arrays of a handle sit in one device pool.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "sais.h"
+
+namespace sais {
+
+constexpr int kMaxConstraints = 32;    // m <= 32: per-chain constraint state lives in registers
+constexpr int kSpinPad = 64;           // N' is padded to a multiple of 64 spins
+constexpr int kMaxPlainSmem = 220 * 1024;
+
+// Device view of one instance.  Spins are ordered items first, then the slack bits of
+// constraint 0, 1, ... (bit q of constraint k has coefficient 2^q in row k of A_ext).
+struct InstDev {
+    int32_t n;          // items
+    int32_t m;          // constraints
+    int32_t nprime;     // spins N' = n + sum_k Q_k
+    int32_t npad;       // N' rounded up to kSpinPad
+    int32_t words;      // ceil(N'/32)
+    int32_t has_w;      // 1: quadratic objective (QKP), 0: linear (MKP)
+    float sigma_f;      // 1/max(|W|,|h|)
+    float sigma_g;      // 1/max(|A|,|b|)
+    float P;            // penalty
+    float kappa;        // fl(2 P sigma_g^2), FP64 product rounded once
+    double psg2;        // P sigma_g^2 in FP64 (exact-path evaluation)
+    const int16_t *W;   // npad x npad row-major pair values, zero padded (NULL if !has_w)
+    const float *hF;    // npad: h_i as FP32 (exact integers), 0 for slack/padding
+    const int32_t *acol;   // nprime x m, spin-major: a_ki of A_ext
+    const float *D;        // nprime: fl(P sigma_g^2 sum_k a_ki^2)
+    const float *asum;     // nprime: sum_k a_ki (exact in FP32)
+    const int32_t *b;      // m capacities
+    const int32_t *slack_off;  // m+1: first slack spin of constraint k; [m] = N'
+    const uint16_t *Wbf;   // npad x npad BF16 of W (blocked sampler), or NULL
+    const uint16_t *Wbf_lo;    // npad x npad BF16 of W - Wbf when |W| > 256, or NULL
+};
+
+// Arguments of one sampling launch over all instances of a handle.
+struct SampleArgs {
+    const InstDev *inst;
+    int32_t count;
+    int32_t chains;
+    int32_t sweeps;
+    float beta_max;
+    uint32_t iter;
+    const uint32_t *iter_dev;  // if not NULL, the outer-iteration index is read here
+    uint64_t seed;
+    int32_t words;       // stride of x
+    int32_t m_stride;    // stride of lambda and g
+    const float *lambda;     // [count*m_stride]
+    uint32_t *x;             // [count*chains*words]
+    int64_t *cost;           // [count*chains]
+    int64_t *g;              // [count*chains*m_stride]
+    uint8_t *feasible;       // [count*chains] or NULL
+    uint32_t *trace;         // [count*chains*sweeps*words] or NULL
+    int32_t *status;         // device status word (SAIS_ETIMEOUT etc.), or NULL
+};
+
+// Arguments of the per-instance post-processing launch (readout reduction, best-so-far,
+// multiplier step).
+struct PostArgs {
+    const InstDev *inst;
+    int32_t count;
+    int32_t chains;
+    int32_t words;
+    int32_t m_stride;
+    double eta;
+    int32_t project;
+    int32_t track_best;      // keep the best feasible sample (sais_track_best)
+    int32_t do_lambda;       // take the multiplier step (sais_update_lambda)
+    const uint32_t *x;
+    const int64_t *cost;
+    const int64_t *g;
+    const uint8_t *feasible;
+    float *lambda;           // in/out
+    float *lambda_trace;     // [iters*count*m_stride] or NULL
+    const uint32_t *iter_dev;    // current iteration (trace row = *iter_dev - iter0)
+    uint32_t iter;               // used when iter_dev is NULL
+    uint32_t iter0;
+    int64_t *best_cost;      // [count]
+    uint32_t *best_x;        // [count*words]
+    int32_t *best_iter;      // [count]
+    int32_t *best_chain;     // [count]
+    int64_t *feasible_count; // [count]
+};
+
+// Launchers (defined in the .cu files); they only enqueue work on `stream`.
+cudaError_t launch_plain_sampler(const SampleArgs &a, int max_m, int max_npad, int max_words,
+                                 int chains_per_cta, cudaStream_t stream);
+cudaError_t launch_blocked_sampler(const SampleArgs &a, int max_m, int max_npad,
+                                   int max_words, int block_k, cudaStream_t stream,
+                                   const char **why_unsupported);
+cudaError_t launch_post(const PostArgs &a, cudaStream_t stream);
+cudaError_t launch_advance_iter(uint32_t *iter_dev, cudaStream_t stream);
+
+}  // namespace sais

@@ -1,0 +1,215 @@
+// sais_plain.cu -- the plain per-spin p-bit sampler (Sec. III-B, Eq. 9-10) on sm_103a.
+//
+// Layout.  One thread owns one chain; a CTA holds `cpb` chains of one instance (blockIdx.y).
+// The objective part of the local field, F_i = h_i + sum_j W_ij x_j (an exact integer held in
+// FP32), lives in shared memory chain-minor, F[i][chain], so a warp touching spin i reads and
+// writes 32 consecutive words.  The bit-packed state sits beside it.  Per chain the constraint
+// values g_k = (A_ext x - b)_k are int32 registers, and c_k = sigma_g lambda_k + 2 P sigma_g^2 g_k
+// (FP32) is refreshed whenever g_k changes.
+//
+// One update of spin i (sequential, i = 0..N'-1, Sec. III-B):
+//   2 I_i = sigma_f F_i - sum_k a_ki c_k - (1 - 2 x_i) D_i,  D_i = P sigma_g^2 sum_k a_ki^2,
+// which is -dL_i with dL_i = L(x_i = 1) - L(x_i = 0) of Eq. 5 (the p-bit input of Eq. 9 for
+// the Ising form of L).  The decision follows sais_device.cuh.  On a flip the constraint values
+// change by a_ki and, if any chain of the warp flipped, the warp adds W[i,:] * delta to its
+// chains' F columns (rank-1 update, W row broadcast from L1/L2).
+//
+// Error bound of the FP32 field (u = 2^-24): t0 = fl(sigma_f F_i) carries u|sigma_f F_i|; each
+// c_k carries at most 3.02 u M_k with M_k = |2 P sigma_g^2 g_k| + |sigma_g lambda_k|; the chain
+// of m + 1 fused multiply-adds adds gamma_{m+1} times the sum of the magnitudes; D_i carries
+// 1.01 u D_i; the final product by beta/2 one more u.  Altogether
+//   |z - beta I_i| <= (beta/2) (m + 6.2) u (|sigma_f F_i| + sum_k a_ki M_k + D_i),
+// and sum_k a_ki M_k <= (sum_k a_ki) max_k M_k.  field_err_factor() uses m + 12 with a margin.
+#include <climits>
+
+#include "sais_device.cuh"
+
+namespace sais {
+namespace {
+
+template <int MC>
+__global__ void __launch_bounds__(128) plain_sampler_kernel(SampleArgs a) {
+    const int j = blockIdx.y;
+    const InstDev *__restrict__ ip = a.inst + j;
+    const int m = ip->m, nprime = ip->nprime, npad = ip->npad, words = ip->words;
+    const bool has_w = ip->has_w != 0;
+    const float sf = ip->sigma_f, sg = ip->sigma_g, kappa = ip->kappa;
+    const double psg2 = ip->psg2;
+    const int16_t *__restrict__ W = ip->W;
+    const float *__restrict__ hF = ip->hF;
+    const int32_t *__restrict__ acol = ip->acol;
+    const float *__restrict__ Dv = ip->D;
+    const float *__restrict__ asum = ip->asum;
+
+    const int cpb = blockDim.x, tid = threadIdx.x;
+    const int chain = blockIdx.x * cpb + tid;
+    const bool valid = chain < a.chains;
+    const uint32_t iter = a.iter_dev ? *a.iter_dev : a.iter;
+    const uint64_t seed = a.seed + (uint64_t)j;
+    const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *Fs = reinterpret_cast<float *>(smem_raw);
+    uint32_t *xs = reinterpret_cast<uint32_t *>(smem_raw + (has_w ? (size_t)npad * cpb * 4 : 0));
+
+    const float *lam = a.lambda + (size_t)j * a.m_stride;
+    int32_t g[MC];
+    float c[MC], cA[MC];
+    float Mmax = 0.f;
+#pragma unroll
+    for (int k = 0; k < MC; ++k) {
+        if (k < m) {
+            cA[k] = __double2float_rn((double)sg * (double)lam[k]);
+            g[k] = -ip->b[k];
+            c[k] = fmaf(kappa, (float)g[k], cA[k]);
+            Mmax = fmaxf(Mmax, fmaf(fabsf(kappa), fabsf((float)g[k]), fabsf(cA[k])));
+        } else {
+            cA[k] = 0.f;
+            g[k] = 0;
+            c[k] = 0.f;
+        }
+    }
+    if (has_w)
+        for (int i = 0; i < npad; ++i) Fs[i * cpb + tid] = hF[i];
+    for (int w = 0; w < words; ++w) xs[w * cpb + tid] = 0u;
+    const float errk = field_err_factor(m);
+
+    for (int t = 0; t < a.sweeps; ++t) {
+        const float beta = beta_of_sweep(a.beta_max, t, a.sweeps);
+        const float hb = 0.5f * beta;
+        const float ez = hb * errk;
+        uint32_t xw = 0u;
+        for (int i0 = 0; i0 < nprime; i0 += 4) {
+            const uint4 rw = philox4x32_10(
+                make_uint4((uint32_t)(i0 >> 2), (uint32_t)t, (uint32_t)chain, iter), key0, key1);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = i0 + q;
+                if (i >= nprime) break;
+                if ((i & 31) == 0) xw = xs[(i >> 5) * cpb + tid];
+                const float rho = rho_of_word(word_of(rw, q));
+                const float theta = atanhf(rho);
+                const float Fi = has_w ? Fs[i * cpb + tid] : __ldg(hF + i);
+                const int xi = (xw >> (i & 31)) & 1;
+                int32_t ak[MC];
+                float acc = sf * Fi;
+                const float tabs = fabsf(acc);
+#pragma unroll
+                for (int k = 0; k < MC; ++k) {
+                    ak[k] = (k < m) ? __ldg(acol + (size_t)i * m + k) : 0;
+                    acc = fmaf(-(float)ak[k], c[k], acc);
+                }
+                const float Di = __ldg(Dv + i);
+                acc = fmaf(xi ? 1.f : -1.f, Di, acc);
+                const float z = hb * acc;
+                const float y = z + theta;
+                const float bound =
+                    ez * (tabs + __ldg(asum + i) * Mmax + Di) + kThetaRelErr * fabsf(theta);
+                int xn;
+                if (fabsf(y) > bound)
+                    xn = y > 0.f;
+                else
+                    xn = decide_exact<MC>(Fi, xi, ak, g, lam, m, sf, sg, psg2, beta, rho);
+                const int d = xn - xi;
+                if (d != 0) {
+                    xw ^= 1u << (i & 31);
+                    Mmax = 0.f;
+#pragma unroll
+                    for (int k = 0; k < MC; ++k) {
+                        if (k < m) {
+                            g[k] += ak[k] * d;
+                            c[k] = fmaf(kappa, (float)g[k], cA[k]);
+                            Mmax = fmaxf(Mmax, fmaf(fabsf(kappa), fabsf((float)g[k]), fabsf(cA[k])));
+                        }
+                    }
+                }
+                if (has_w && __any_sync(0xffffffffu, d != 0)) {
+                    const float df = (float)d;
+                    const int4 *Wi = reinterpret_cast<const int4 *>(W + (size_t)i * npad);
+                    float *Fc = Fs + tid;
+                    for (int j8 = 0; j8 < (npad >> 3); ++j8) {
+                        const int4 v = __ldg(Wi + j8);
+                        const uint32_t u[4] = {(uint32_t)v.x, (uint32_t)v.y, (uint32_t)v.z,
+                                               (uint32_t)v.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int r = (j8 * 8 + 2 * e) * cpb;
+                            const float wlo = (float)(int16_t)(u[e] & 0xffffu);
+                            const float whi = (float)(int16_t)(u[e] >> 16);
+                            Fc[r] = fmaf(df, wlo, Fc[r]);
+                            Fc[r + cpb] = fmaf(df, whi, Fc[r + cpb]);
+                        }
+                    }
+                }
+                if ((i & 31) == 31 || i == nprime - 1) xs[(i >> 5) * cpb + tid] = xw;
+            }
+        }
+        if (a.trace && valid) {
+            uint32_t *tr = a.trace + (((size_t)j * a.chains + chain) * a.sweeps + t) * a.words;
+            for (int w = 0; w < a.words; ++w) tr[w] = w < words ? xs[w * cpb + tid] : 0u;
+        }
+    }
+
+    // Readout of the last sample (Sec. III-B): state, cost c(x) = -(sum_i x_i F_i + h^T x)/2
+    // (F_i = h_i + (W x)_i), constraint values and items-only feasibility (Sec. IV-A).
+    if (!valid) return;
+    const size_t cidx = (size_t)j * a.chains + chain;
+    long long sumF = 0, sumh = 0;
+    for (int w = 0; w < words; ++w) {
+        uint32_t bits = xs[w * cpb + tid];
+        a.x[cidx * a.words + w] = bits;
+        while (bits) {
+            const int i = w * 32 + __ffs(bits) - 1;
+            bits &= bits - 1u;
+            sumh += (long long)__ldg(hF + i);
+            sumF += has_w ? (long long)Fs[i * cpb + tid] : (long long)__ldg(hF + i);
+        }
+    }
+    for (int w = words; w < a.words; ++w) a.x[cidx * a.words + w] = 0u;
+    a.cost[cidx] = -(sumF + sumh) / 2;
+    bool feas = true;
+#pragma unroll
+    for (int k = 0; k < MC; ++k) {
+        if (k < m) {
+            const int o0 = ip->slack_off[k], o1 = ip->slack_off[k + 1];
+            long long sv = 0;
+            for (int s = o0; s < o1; ++s)
+                if ((xs[(s >> 5) * cpb + tid] >> (s & 31)) & 1u) sv += 1LL << (s - o0);
+            if ((long long)g[k] - sv > 0) feas = false;
+            a.g[cidx * a.m_stride + k] = g[k];
+        }
+    }
+    for (int k = m; k < a.m_stride; ++k) a.g[cidx * a.m_stride + k] = 0;
+    if (a.feasible) a.feasible[cidx] = feas ? 1 : 0;
+}
+
+template <int MC>
+cudaError_t launch_mc(const SampleArgs &a, int cpb, size_t smem, cudaStream_t s) {
+    auto kern = plain_sampler_kernel<MC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.chains + cpb - 1) / cpb, a.count);
+    kern<<<grid, cpb, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t plain_smem_bytes(int max_npad, int max_words, bool any_w, int cpb) {
+    return (any_w ? (size_t)max_npad * cpb * 4 : 0) + (size_t)max_words * cpb * 4;
+}
+
+cudaError_t launch_plain_sampler(const SampleArgs &a, int max_m, int max_npad, int max_words,
+                                 int cpb, cudaStream_t stream) {
+    const bool any_w = max_npad > 0;
+    const size_t smem = plain_smem_bytes(max_npad, max_words, any_w, cpb);
+    if (max_m <= 1) return launch_mc<1>(a, cpb, smem, stream);
+    if (max_m <= 2) return launch_mc<2>(a, cpb, smem, stream);
+    if (max_m <= 4) return launch_mc<4>(a, cpb, smem, stream);
+    if (max_m <= 8) return launch_mc<8>(a, cpb, smem, stream);
+    if (max_m <= 16) return launch_mc<16>(a, cpb, smem, stream);
+    return launch_mc<32>(a, cpb, smem, stream);
+}
+
+}  // namespace sais

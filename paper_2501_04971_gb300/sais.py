@@ -1,0 +1,352 @@
+"""Thin ctypes binding of libsais (include/sais.h).
+
+Argument marshalling only: every step of the sampling path runs in the library's CUDA kernels.
+PyTorch provides device memory and streams.  The raw entry points keep the C names
+(``sais_create_problem``, ``sais_sample``, ...); :class:`Problem` wraps a handle for tests and
+benchmarks.  There is no CPU fallback: a missing library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libsais.so")
+
+_i32, _i64, _u32, _u64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
+_f32, _f64, _P = ctypes.c_float, ctypes.c_double, ctypes.c_void_p
+
+SAIS_OK, SAIS_EINVAL, SAIS_ENOMEM, SAIS_ECUDA, SAIS_EOVERFLOW, SAIS_ETIMEOUT, \
+    SAIS_EUNSUPPORTED = range(7)
+SAIS_PLAIN, SAIS_BLOCKED = 0, 1
+_VARIANTS = {"plain": SAIS_PLAIN, "blocked": SAIS_BLOCKED}
+
+
+class sais_problem_desc(ctypes.Structure):
+    _fields_ = [("n", _i32), ("m", _i32), ("W", _P), ("h", _P), ("A", _P), ("b", _P),
+                ("alpha", _f32), ("density", _f32), ("penalty", _f32)]
+
+
+class sais_problem_scalars(ctypes.Structure):
+    _fields_ = [("n", _i32), ("m", _i32), ("n_spins", _i32), ("words", _i32),
+                ("sigma_f", _f32), ("sigma_g", _f32), ("penalty", _f32), ("reserved", _f32),
+                ("density", _f64)]
+
+
+class sais_layout(ctypes.Structure):
+    _fields_ = [("count", _i32), ("max_spins", _i32), ("words", _i32), ("m_stride", _i32),
+                ("device", _i32), ("has_quadratic", _i32)]
+
+
+class sais_sample_params(ctypes.Structure):
+    _fields_ = [("chains", _i32), ("sweeps", _i32), ("beta_max", _f32), ("iter", _u32),
+                ("seed", _u64), ("variant", _i32), ("block_k", _i32),
+                ("chains_per_cta", _i32), ("reserved", _i32)]
+
+
+class sais_solve_params(ctypes.Structure):
+    _fields_ = [("iters", _i32), ("chains", _i32), ("sweeps", _i32), ("beta_max", _f32),
+                ("eta", _f64), ("seed", _u64), ("iter0", _u32), ("project_nonneg", _i32),
+                ("variant", _i32), ("block_k", _i32), ("chains_per_cta", _i32),
+                ("use_graph", _i32), ("lambda0", _P)]
+
+
+class sais_solve_result(ctypes.Structure):
+    _fields_ = [("best_cost", _P), ("best_x", _P), ("best_iter", _P), ("best_chain", _P),
+                ("feasible_count", _P), ("lambda_final", _P), ("lambda_trace", _P),
+                ("elapsed_ms", _f64), ("spin_updates", _i64)]
+
+
+_SIGS = {
+    "sais_describe": [ctypes.POINTER(sais_problem_desc), ctypes.POINTER(sais_problem_scalars)],
+    "sais_create_problem": [ctypes.POINTER(sais_problem_desc), _i32, ctypes.POINTER(_P)],
+    "sais_create_batch": [ctypes.POINTER(sais_problem_desc), _i32, _i32, ctypes.POINTER(_P)],
+    "sais_destroy_problem": [_P],
+    "sais_problem_info": [_P, ctypes.POINTER(sais_layout)],
+    "sais_instance_scalars": [_P, _i32, ctypes.POINTER(sais_problem_scalars)],
+    "sais_sample": [_P, ctypes.POINTER(sais_sample_params), _P, _P, _P, _P, _P, _P],
+    "sais_sample_trace": [_P, ctypes.POINTER(sais_sample_params), _P, _P, _P, _P, _P, _P, _P],
+    "sais_update_lambda": [_P, _P, _i32, _f64, _i32, _P, _P],
+    "sais_track_best": [_P, _P, _P, _P, _i32, _u32, _P, _P, _P, _P, _P, _P],
+    "sais_solve": [_P, ctypes.POINTER(sais_solve_params), ctypes.POINTER(sais_solve_result), _P],
+}
+EXPORTS = list(_SIGS) + ["sais_status_string", "sais_last_error"]
+
+_lib = None
+_lock = threading.Lock()
+
+
+class SaisError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: status {status}: {msg}")
+        self.status = status
+
+
+def lib(path: Optional[str] = None):
+    """Open libsais.so (built by ``paper_2501_04971_gb300.build``); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libsais is not built ({p} missing): run "
+                               "paper_2501_04971_gb300.build.build() first")
+        L = ctypes.CDLL(p)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = _i32
+        L.sais_status_string.argtypes = [_i32]
+        L.sais_status_string.restype = ctypes.c_char_p
+        L.sais_last_error.argtypes = []
+        L.sais_last_error.restype = ctypes.c_char_p
+        if path is None:
+            _lib = L
+        return L
+
+
+def _check(st: int, where: str):
+    if st != SAIS_OK:
+        raise SaisError(st, where, lib().sais_last_error().decode())
+
+
+# --- raw entry points, same names as the C-ABI ----------------------------------------------
+
+def sais_describe(desc):
+    out = sais_problem_scalars()
+    _check(lib().sais_describe(ctypes.byref(desc), ctypes.byref(out)), "sais_describe")
+    return out
+
+
+def sais_create_problem(desc, device: int = 0):
+    h = _P()
+    _check(lib().sais_create_problem(ctypes.byref(desc), device, ctypes.byref(h)),
+           "sais_create_problem")
+    return h
+
+
+def sais_create_batch(descs, device: int = 0):
+    arr = (sais_problem_desc * len(descs))(*descs)
+    h = _P()
+    _check(lib().sais_create_batch(arr, len(descs), device, ctypes.byref(h)), "sais_create_batch")
+    return h
+
+
+def sais_destroy_problem(h):
+    _check(lib().sais_destroy_problem(h), "sais_destroy_problem")
+
+
+def sais_problem_info(h):
+    out = sais_layout()
+    _check(lib().sais_problem_info(h, ctypes.byref(out)), "sais_problem_info")
+    return out
+
+
+def sais_instance_scalars(h, index: int):
+    out = sais_problem_scalars()
+    _check(lib().sais_instance_scalars(h, index, ctypes.byref(out)), "sais_instance_scalars")
+    return out
+
+
+def sais_sample(h, prm, lam_ptr, x_ptr, cost_ptr, g_ptr, feas_ptr, stream_ptr):
+    _check(lib().sais_sample(h, ctypes.byref(prm), lam_ptr, x_ptr, cost_ptr, g_ptr, feas_ptr,
+                             stream_ptr), "sais_sample")
+
+
+def sais_sample_trace(h, prm, lam_ptr, x_ptr, cost_ptr, g_ptr, feas_ptr, trace_ptr, stream_ptr):
+    _check(lib().sais_sample_trace(h, ctypes.byref(prm), lam_ptr, x_ptr, cost_ptr, g_ptr,
+                                   feas_ptr, trace_ptr, stream_ptr), "sais_sample_trace")
+
+
+def sais_update_lambda(h, g_ptr, chains: int, eta: float, project: int, lam_ptr, stream_ptr):
+    _check(lib().sais_update_lambda(h, g_ptr, chains, eta, project, lam_ptr, stream_ptr),
+           "sais_update_lambda")
+
+
+def sais_track_best(h, x_ptr, cost_ptr, feas_ptr, chains: int, it: int, best_cost_ptr,
+                    best_x_ptr, best_iter_ptr, best_chain_ptr, feas_count_ptr, stream_ptr):
+    _check(lib().sais_track_best(h, x_ptr, cost_ptr, feas_ptr, chains, it, best_cost_ptr,
+                                 best_x_ptr, best_iter_ptr, best_chain_ptr, feas_count_ptr,
+                                 stream_ptr), "sais_track_best")
+
+
+def sais_solve(h, prm, res, stream_ptr):
+    _check(lib().sais_solve(h, ctypes.byref(prm), ctypes.byref(res), stream_ptr), "sais_solve")
+
+
+def sais_status_string(st: int) -> str:
+    return lib().sais_status_string(st).decode()
+
+
+def sais_last_error() -> str:
+    return lib().sais_last_error().decode()
+
+
+# --- convenience wrapper ------------------------------------------------------------------
+
+def _desc(inst, keep: list) -> sais_problem_desc:
+    """sais_problem_desc for an object with n, m, W, h, A, b, alpha, density (+ penalty)."""
+    def arr(a, dt):
+        if a is None:
+            return None
+        c = np.ascontiguousarray(a, dtype=dt)
+        keep.append(c)
+        return c.ctypes.data_as(_P)
+    d = sais_problem_desc()
+    d.n, d.m = int(inst.n), int(inst.m)
+    d.W = arr(inst.W, np.int32)
+    d.h = arr(inst.h, np.int32)
+    d.A = arr(np.asarray(inst.A).reshape(inst.m, inst.n) if inst.m else None, np.int32)
+    d.b = arr(inst.b if inst.m else None, np.int64)
+    d.alpha = float(inst.alpha)
+    d.density = float(inst.density)
+    d.penalty = float(getattr(inst, "penalty", 0.0) or 0.0)
+    return d
+
+
+def describe(inst) -> sais_problem_scalars:
+    keep = []
+    return sais_describe(_desc(inst, keep))
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _P(s.cuda_stream)
+
+
+class Problem:
+    """A handle over one or more instances (``workloads.Instance``-like objects)."""
+
+    def __init__(self, instances, device: int = 0):
+        if not isinstance(instances, (list, tuple)):
+            instances = [instances]
+        keep: list = []
+        descs = [_desc(i, keep) for i in instances]
+        self.handle = sais_create_batch(descs, device)
+        self.device = device
+        self.layout = sais_problem_info(self.handle)
+        self.count = self.layout.count
+        self.words = self.layout.words
+        self.m_stride = self.layout.m_stride
+        self.scalars = [sais_instance_scalars(self.handle, j) for j in range(self.count)]
+
+    def close(self):
+        if self.handle:
+            sais_destroy_problem(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _params(self, chains, sweeps, beta_max, seed, it, variant, block_k, chains_per_cta):
+        p = sais_sample_params()
+        p.chains, p.sweeps, p.beta_max, p.iter, p.seed = chains, sweeps, beta_max, it, seed
+        p.variant = _VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        p.block_k, p.chains_per_cta = block_k, chains_per_cta
+        return p
+
+    def alloc_outputs(self, chains: int, trace_sweeps: int = 0):
+        import torch
+        dev = torch.device("cuda", self.device)
+        n = self.count * chains
+        out = {
+            "x": torch.empty(n * self.words, dtype=torch.int32, device=dev),
+            "cost": torch.empty(n, dtype=torch.int64, device=dev),
+            "g": torch.empty(n * self.m_stride, dtype=torch.int64, device=dev),
+            "feasible": torch.empty(n, dtype=torch.uint8, device=dev),
+        }
+        if trace_sweeps:
+            out["trace"] = torch.empty(n * trace_sweeps * self.words, dtype=torch.int32, device=dev)
+        return out
+
+    def sample(self, lam, chains: int, sweeps: int, beta_max: float, seed: int, it: int = 0,
+               variant="plain", block_k: int = 0, chains_per_cta: int = 0, trace: bool = False,
+               out=None, stream=None):
+        """One annealing run per chain (sais_sample / sais_sample_trace); returns device tensors
+        x [count, chains, words] (int32 bit patterns), cost [count, chains],
+        g [count, chains, m_stride], feasible [count, chains] (and trace)."""
+        prm = self._params(chains, sweeps, beta_max, seed, it, variant, block_k, chains_per_cta)
+        o = out or self.alloc_outputs(chains, sweeps if trace else 0)
+        sp = _stream_ptr(stream)
+        args = (_P(lam.data_ptr()), _P(o["x"].data_ptr()), _P(o["cost"].data_ptr()),
+                _P(o["g"].data_ptr()), _P(o["feasible"].data_ptr()))
+        if trace:
+            sais_sample_trace(self.handle, prm, *args, _P(o["trace"].data_ptr()), sp)
+        else:
+            sais_sample(self.handle, prm, *args, sp)
+        C = chains
+        res = {"x": o["x"].view(self.count, C, self.words),
+               "cost": o["cost"].view(self.count, C),
+               "g": o["g"].view(self.count, C, self.m_stride),
+               "feasible": o["feasible"].view(self.count, C)}
+        if trace:
+            res["trace"] = o["trace"].view(self.count, C, sweeps, self.words)
+        return res
+
+    def update_lambda(self, g, chains: int, eta: float, project: bool, lam, stream=None):
+        sais_update_lambda(self.handle, _P(g.data_ptr()), chains, eta, int(project),
+                           _P(lam.data_ptr()), _stream_ptr(stream))
+
+    def alloc_best(self):
+        """Device state of sais_track_best, initialised (best_cost INT64_MAX, indices -1)."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        return {"best_cost": torch.full((self.count,), np.iinfo(np.int64).max, dtype=torch.int64,
+                                        device=dev),
+                "best_x": torch.zeros(self.count * self.words, dtype=torch.int32, device=dev),
+                "best_iter": torch.full((self.count,), -1, dtype=torch.int32, device=dev),
+                "best_chain": torch.full((self.count,), -1, dtype=torch.int32, device=dev),
+                "feasible_count": torch.zeros(self.count, dtype=torch.int64, device=dev)}
+
+    def track_best(self, out: dict, chains: int, it: int, best: dict, stream=None):
+        """The "store feasible x_k" step (sais_track_best) for samples `out` of sample()."""
+        sais_track_best(self.handle, _P(out["x"].data_ptr()), _P(out["cost"].data_ptr()),
+                        _P(out["feasible"].data_ptr()), chains, it,
+                        _P(best["best_cost"].data_ptr()), _P(best["best_x"].data_ptr()),
+                        _P(best["best_iter"].data_ptr()), _P(best["best_chain"].data_ptr()),
+                        _P(best["feasible_count"].data_ptr()), _stream_ptr(stream))
+
+    def solve(self, iters: int, chains: int, sweeps: int, beta_max: float, eta: float,
+              seed: int, iter0: int = 0, project: bool = True, lambda0=None, variant="plain",
+              block_k: int = 0, chains_per_cta: int = 0, use_graph: bool = False,
+              stream=None) -> dict:
+        """Algorithm 1 on every instance (sais_solve); returns host numpy arrays."""
+        prm = sais_solve_params()
+        prm.iters, prm.chains, prm.sweeps, prm.beta_max = iters, chains, sweeps, beta_max
+        prm.eta, prm.seed, prm.iter0, prm.project_nonneg = eta, seed, iter0, int(project)
+        prm.variant = _VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        prm.block_k, prm.chains_per_cta, prm.use_graph = block_k, chains_per_cta, int(use_graph)
+        l0 = None
+        if lambda0 is not None:
+            l0 = np.ascontiguousarray(np.asarray(lambda0, dtype=np.float32).reshape(-1))
+            assert l0.size == self.count * self.m_stride
+            prm.lambda0 = l0.ctypes.data_as(_P)
+        cnt, W, M = self.count, self.words, self.m_stride
+        out = {"best_cost": np.zeros(cnt, np.int64), "best_x": np.zeros((cnt, W), np.uint32),
+               "best_iter": np.zeros(cnt, np.int32), "best_chain": np.zeros(cnt, np.int32),
+               "feasible_count": np.zeros(cnt, np.int64),
+               "lambda_final": np.zeros((cnt, M), np.float32),
+               "lambda_trace": np.zeros((iters, cnt, M), np.float32)}
+        res = sais_solve_result()
+        for k, v in out.items():
+            setattr(res, k, v.ctypes.data_as(_P))
+        sais_solve(self.handle, prm, res, _stream_ptr(stream) if stream is not None else None)
+        out["elapsed_ms"] = res.elapsed_ms
+        out["spin_updates"] = res.spin_updates
+        return out
+
+
+def unpack_bits(words: np.ndarray, nspins: int) -> np.ndarray:
+    """Bit-packed states [..., words] (spin i = bit i%32 of word i/32) -> uint8 [..., nspins]."""
+    w = np.ascontiguousarray(words).view(np.uint32)
+    bits = (w[..., :, None] >> np.arange(32, dtype=np.uint32)) & 1
+    return bits.reshape(*w.shape[:-1], -1)[..., :nspins].astype(np.uint8)

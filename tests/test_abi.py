@@ -1,0 +1,111 @@
+"""The C-ABI library loads, exports every symbol include/sais.h declares, and its host-side
+problem scalars (slack extension, normalisation, penalty; no GPU involved) agree bit-for-bit
+with the independently written CPU oracle.  CPU only: no compute call touches a GPU."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_04971_gb300 import build as libbuild
+from paper_2501_04971_gb300 import sais, workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    libbuild.build()
+    return sais.lib()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "sais.h")).read()
+    return sorted(set(re.findall(r"SAIS_API\s+[\w\s\*]+?\b(sais_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for want in ("sais_create_problem", "sais_sample", "sais_update_lambda", "sais_solve"):
+        assert want in names
+    assert set(names) == set(sais.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(L):
+    for name in _declared():
+        assert hasattr(L, name), name
+
+
+def test_status_strings(L):
+    for s in range(7):
+        assert sais.sais_status_string(s)
+    assert sais.sais_status_string(99) == "unknown status"
+
+
+def _pairs():
+    out = [wl.qkp(100, 0.25, s) for s in range(5)]
+    out += [wl.qkp(300, d, s) for d in (0.25, 0.5, 0.75, 1.0) for s in range(3)]
+    out += [wl.mkp(250, 5, s) for s in range(3)] + [wl.mkp(500, 30, 1), wl.mkp(37, 3, 2)]
+    out += [wl.qkp(700, 0.5, 4, profit_max=10000)]
+    return out
+
+
+@pytest.mark.parametrize("idx", range(len(_pairs())))
+def test_describe_matches_oracle_scalars(L, idx):
+    inst = _pairs()[idx]
+    s = sais.describe(inst)
+    ref = oracle.Problem(inst.n, inst.m, inst.W, inst.h, inst.A, inst.b, alpha=inst.alpha,
+                         density=inst.density)
+    assert s.n_spins == ref.nprime
+    assert s.words == (ref.nprime + 31) // 32
+    assert np.float32(s.sigma_f) == ref.sigma_f
+    assert np.float32(s.sigma_g) == ref.sigma_g
+    assert np.float32(s.penalty) == ref.P
+    assert s.density == ref.d_used
+
+
+def test_describe_measured_density_and_override(L):
+    inst = wl.qkp(50, 0.5, 3)
+    inst.density = -1.0
+    s = sais.describe(inst)
+    ref = oracle.Problem(inst.n, inst.m, inst.W, inst.h, inst.A, inst.b, alpha=2.0, density=-1.0)
+    assert s.density == ref.d_used and np.float32(s.penalty) == ref.P
+    inst.penalty = 7.5
+    assert sais.describe(inst).penalty == 7.5
+
+
+def _bad(inst, status):
+    with pytest.raises(sais.SaisError) as e:
+        sais.describe(inst)
+    assert e.value.status == status, str(e.value)
+
+
+def test_describe_rejects_invalid_instances(L):
+    base = wl.qkp(20, 0.5, 1)
+    x = wl.qkp(20, 0.5, 1); x.W = x.W.copy(); x.W[0, 1] += 1
+    _bad(x, sais.SAIS_EINVAL)                       # not symmetric
+    x = wl.qkp(20, 0.5, 1); x.W = x.W.copy(); x.W[3, 3] = 5
+    _bad(x, sais.SAIS_EINVAL)                       # nonzero diagonal
+    x = wl.qkp(20, 0.5, 1); x.b = np.array([0])
+    _bad(x, sais.SAIS_EINVAL)                       # capacity < 1
+    x = wl.qkp(20, 0.5, 1); x.A = -base.A
+    _bad(x, sais.SAIS_EINVAL)                       # negative weight
+    x = wl.qkp(20, 0.5, 1); x.W = x.W.copy(); x.W[0, 1] = x.W[1, 0] = 40000
+    _bad(x, sais.SAIS_EOVERFLOW)                    # int16 range
+    x = wl.qkp(1200, 1.0, 1, profit_max=30000)
+    _bad(x, sais.SAIS_EOVERFLOW)                    # |F| >= 2^24
+    x = wl.mkp(20, 2, 1); x.b = np.array([2**24, 5])
+    _bad(x, sais.SAIS_EOVERFLOW)                    # constraint range >= 2^24
+    x = wl.mkp(20, 2, 1); x.m = 33
+    with pytest.raises(Exception):
+        sais.describe(x)
+    x = wl.qkp(20, 0.5, 1); x.alpha = float("nan")
+    _bad(x, sais.SAIS_EINVAL)
+
+
+def test_last_error_message(L):
+    x = wl.qkp(20, 0.5, 1); x.b = np.array([-3])
+    with pytest.raises(sais.SaisError):
+        sais.describe(x)
+    assert "b[0]" in sais.sais_last_error()
