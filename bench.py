@@ -105,15 +105,17 @@ def reference_arm(a):
     per = max(2.0, a.cpu_seconds / max(1, a.steps + a.warmup))
     for _ in range(a.warmup):
         oracle_rate(insts, per / 4, 2 * (os.cpu_count() or 1))
-    vals, cores, desc = [], 1, ""
+    vals, cores, desc, secs = [], 1, "", []
     for _ in range(a.steps):
+        t0 = time.perf_counter()
         v, cores, desc = oracle_rate(insts, per, 2 * (os.cpu_count() or 1))
+        secs.append(time.perf_counter() - t0)
         vals.append(v)
     v = float(statistics.median(vals))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
             "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
-            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(a), "sample": "bounded CPU sample"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": desc},

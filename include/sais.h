@@ -120,9 +120,13 @@ typedef struct sais_sample_params {
     uint32_t iter;           /* outer-iteration index k (selects the random stream)         */
     uint64_t seed;           /* instance j uses seed + j                                    */
     int32_t variant;         /* sais_variant                                                */
-    int32_t block_k;         /* SAIS_BLOCKED: spins per block (16, 32 or 64); 0 = default   */
+    int32_t block_k;         /* SAIS_BLOCKED: spins per block (16 or 32); 0 = default (32)   */
     int32_t chains_per_cta;  /* 0 = library choice; else 32, 64 or 128                      */
-    int32_t reserved;
+    int32_t debug_wait_polls; /* 0 = normal.  > 0 (fault-injection tests of the timeout path):
+                                the blocked sampler's decision warps first wait, for at most
+                                this many polls, on a barrier nothing completes, so the kernel
+                                stops early, records SAIS_ETIMEOUT (see sais_synchronize),
+                                releases its resources and exits; outputs are not written   */
 } sais_sample_params;
 
 /* Algorithm 1 (Sec. III-A) on every instance of the handle. */
@@ -238,6 +242,12 @@ SAIS_API sais_status sais_track_best(sais_problem *p, const uint32_t *x, const i
  * the host arrays of `res`.  Errors: as sais_sample, plus SAIS_ENOMEM. */
 SAIS_API sais_status sais_solve(sais_problem *p, const sais_solve_params *prm,
                                 sais_solve_result *res, void *stream);
+
+/* Wait for the work queued on `stream` and report device-side failures of this problem's
+ * kernels since the last call: SAIS_ETIMEOUT if a bounded wait inside a kernel gave up (the
+ * kernel then stopped early and its outputs are not valid).  Resets the device status word.
+ * Errors: SAIS_EINVAL, SAIS_ECUDA, SAIS_ETIMEOUT. */
+SAIS_API sais_status sais_synchronize(sais_problem *p, void *stream);
 
 /* Static text for a status code. */
 SAIS_API const char *sais_status_string(sais_status s);

@@ -15,10 +15,6 @@
 #include "sais.h"
 #include "sais_internal.h"
 
-namespace sais {
-size_t plain_smem_bytes(int max_npad, int max_words, bool any_w, int cpb);
-}
-
 using namespace sais;
 
 namespace {
@@ -204,8 +200,11 @@ struct sais_problem {
     int max_spins = 0, max_npad = 0, max_npad_w = 0, words = 0, m_stride = 1, max_m = 0;
     bool any_w = false;
     std::vector<HostInst> host;   // host copies (W pointer cleared after creation)
+    bool any_lo = false;          // some instance needs the BF16 hi/lo split
+    bool all_w = true;            // every instance has a quadratic objective
     void *pool = nullptr;         // one device allocation for all instance arrays
     InstDev *d_inst = nullptr;    // device array of count records (inside pool)
+    int32_t *d_status = nullptr;  // device status word written by kernels (inside pool)
 };
 
 extern "C" {
@@ -276,6 +275,8 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
         if (h.has_w) p->max_npad_w = std::max(p->max_npad_w, h.npad);
         p->max_m = std::max(p->max_m, h.m);
         p->any_w = p->any_w || h.has_w;
+        p->all_w = p->all_w && h.has_w;
+        p->any_lo = p->any_lo || h.need_lo;
     }
     p->words = (p->max_spins + 31) / 32;
     p->m_stride = std::max(1, p->max_m);
@@ -287,6 +288,8 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
     };
     std::vector<Off> off(count);
     size_t cur = align_up(sizeof(InstDev) * count, 256);
+    const size_t status_off = cur;
+    cur = align_up(cur + 4, 256);
     for (int32_t j = 0; j < count; ++j) {
         const HostInst &h = p->host[j];
         const size_t nn = (size_t)h.npad * h.npad;
@@ -356,8 +359,10 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
             for (int32_t i = 0; i < h.n; ++i)
                 for (int32_t jj = 0; jj < h.n; ++jj) {
                     const int32_t w = h.W[(size_t)i * h.n + jj];
-                    const size_t e = (size_t)i * h.npad + jj;
-                    W16[e] = (int16_t)w;
+                    W16[(size_t)i * h.npad + jj] = (int16_t)w;
+                    // shared-memory image of the blocked sampler: element (row i, column jj)
+                    // at ((jj/8) npad + i) 8 + jj%8
+                    const size_t e = ((size_t)(jj >> 3) * h.npad + i) * 8 + (jj & 7);
                     const uint16_t hi = bf16_bits((float)w);
                     Wb[e] = hi;
                     if (Wl) Wl[e] = bf16_bits((float)w - bf16_value(hi));
@@ -389,6 +394,7 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
         return fail(SAIS_ECUDA, "copy of problem data: %s", cudaGetErrorString(ce));
     }
     p->d_inst = reinterpret_cast<InstDev *>(p->pool);
+    p->d_status = reinterpret_cast<int32_t *>(base + status_off);
     *out = p;
     return SAIS_OK;
 }
@@ -464,6 +470,8 @@ sais_status check_sample_params(const sais_problem *p, const sais_sample_params 
         return fail(SAIS_EINVAL, "chains_per_cta = %d: need 0, 32, 64 or 128", prm->chains_per_cta);
     if (prm->block_k != 0 && prm->block_k != 16 && prm->block_k != 32 && prm->block_k != 64)
         return fail(SAIS_EINVAL, "block_k = %d: need 0, 16, 32 or 64", prm->block_k);
+    if (prm->debug_wait_polls < 0)
+        return fail(SAIS_EINVAL, "debug_wait_polls = %d: need >= 0", prm->debug_wait_polls);
     return SAIS_OK;
 }
 
@@ -502,11 +510,28 @@ sais_status enqueue_sample(sais_problem *p, const sais_sample_params *prm, const
     a.trace = trace;
     a.status = nullptr;
     cudaError_t e;
+    a.status = p->d_status;
     if (prm->variant == SAIS_BLOCKED) {
-        const char *why = nullptr;
-        e = launch_blocked_sampler(a, p->max_m, p->max_npad, p->words,
-                                   prm->block_k ? prm->block_k : 32, st, &why);
-        if (why) return fail(SAIS_EUNSUPPORTED, "blocked sampler: %s", why);
+        const int k = prm->block_k ? prm->block_k : 32;
+        if (!p->all_w)
+            return fail(SAIS_EUNSUPPORTED,
+                        "blocked sampler: every instance needs a quadratic objective W "
+                        "(linear objectives have no dense field to update; use SAIS_PLAIN)");
+        if (p->any_lo)
+            return fail(SAIS_EUNSUPPORTED,
+                        "blocked sampler: pair values above 256 need the BF16 hi/lo split, "
+                        "not available in this build");
+        if (k == 64) return fail(SAIS_EUNSUPPORTED, "blocked sampler: block_k = 64 not available");
+        if (p->max_npad > 512)
+            return fail(SAIS_EUNSUPPORTED, "blocked sampler: N'=%d exceeds 512 TMEM columns",
+                        p->max_spins);
+        const size_t smem = blocked_smem_bytes(p->max_npad, p->words, k);
+        if (smem > kMaxSmemPerBlock)
+            return fail(SAIS_EUNSUPPORTED,
+                        "blocked sampler: N'=%d needs %zu bytes of shared memory (max %zu)",
+                        p->max_spins, smem, kMaxSmemPerBlock);
+        e = launch_blocked_sampler(a, p->max_m, p->max_npad, p->words, k, p->d_status,
+                                   (long long)prm->debug_wait_polls, st);
     } else {
         int cpb = 0;
         sais_status s = plain_cpb(p, prm->chains_per_cta, &cpb);
@@ -540,6 +565,21 @@ sais_status sais_sample_trace(sais_problem *p, const sais_sample_params *prm, co
     DeviceGuard dg(p->device);
     return enqueue_sample(p, prm, lambda, nullptr, x, cost, g, feasible, trace,
                           static_cast<cudaStream_t>(stream));
+}
+
+sais_status sais_synchronize(sais_problem *p, void *stream) {
+    if (!p) return fail(SAIS_EINVAL, "NULL problem");
+    DeviceGuard dg(p->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    SAIS_CUDA(cudaStreamSynchronize(st));
+    int32_t v = 0;
+    SAIS_CUDA(cudaMemcpy(&v, p->d_status, 4, cudaMemcpyDeviceToHost));
+    if (v != SAIS_OK) {
+        SAIS_CUDA(cudaMemset(p->d_status, 0, 4));
+        return fail((sais_status)v, "a kernel on this problem reported: %s",
+                    sais_status_string((sais_status)v));
+    }
+    return SAIS_OK;
 }
 
 sais_status sais_update_lambda(sais_problem *p, const int64_t *g, int32_t chains, double eta,
@@ -753,6 +793,15 @@ sais_status sais_solve(sais_problem *p, const sais_solve_params *prm, sais_solve
     if (res->lambda_final) SAIS_CUDA(cudaMemcpyAsync(res->lambda_final, d_lam, sz_lam, cudaMemcpyDeviceToHost, st));
     if (res->lambda_trace) SAIS_CUDA(cudaMemcpyAsync(res->lambda_trace, d_tr, sz_tr, cudaMemcpyDeviceToHost, st));
     SAIS_CUDA(cudaStreamSynchronize(st));
+    {
+        int32_t v = 0;
+        SAIS_CUDA(cudaMemcpy(&v, p->d_status, 4, cudaMemcpyDeviceToHost));
+        if (v != SAIS_OK) {
+            SAIS_CUDA(cudaMemset(p->d_status, 0, 4));
+            return fail((sais_status)v, "a sampler kernel reported: %s",
+                        sais_status_string((sais_status)v));
+        }
+    }
     float ms = 0.f;
     SAIS_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
     res->elapsed_ms = ms;

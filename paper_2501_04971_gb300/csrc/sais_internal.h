@@ -37,8 +37,10 @@ struct InstDev {
     const float *asum;     // nprime: sum_k a_ki (exact in FP32)
     const int32_t *b;      // m capacities
     const int32_t *slack_off;  // m+1: first slack spin of constraint k; [m] = N'
-    const uint16_t *Wbf;   // npad x npad BF16 of W (blocked sampler), or NULL
-    const uint16_t *Wbf_lo;    // npad x npad BF16 of W - Wbf when |W| > 256, or NULL
+    // BF16 copy of W for the blocked sampler in its shared-memory image: column-chunk major,
+    // element (j, s) at index ((s/8) npad + j) 8 + s%8; Wbf_lo holds W - Wbf when |W| > 256.
+    const uint16_t *Wbf;
+    const uint16_t *Wbf_lo;
 };
 
 // Arguments of one sampling launch over all instances of a handle.
@@ -94,8 +96,11 @@ struct PostArgs {
 cudaError_t launch_plain_sampler(const SampleArgs &a, int max_m, int max_npad, int max_words,
                                  int chains_per_cta, cudaStream_t stream);
 cudaError_t launch_blocked_sampler(const SampleArgs &a, int max_m, int max_npad,
-                                   int max_words, int block_k, cudaStream_t stream,
-                                   const char **why_unsupported);
+                                   int max_words, int block_k, int32_t *status,
+                                   long long dec_wait_polls, cudaStream_t stream);
+size_t blocked_smem_bytes(int max_npad, int max_words, int block_k);
+size_t plain_smem_bytes(int max_npad, int max_words, bool any_w, int cpb);
+constexpr size_t kMaxSmemPerBlock = 232448;   // 227 KB opt-in per CTA on sm_103
 cudaError_t launch_post(const PostArgs &a, cudaStream_t stream);
 cudaError_t launch_advance_iter(uint32_t *iter_dev, cudaStream_t stream);
 

@@ -45,7 +45,7 @@ class sais_layout(ctypes.Structure):
 class sais_sample_params(ctypes.Structure):
     _fields_ = [("chains", _i32), ("sweeps", _i32), ("beta_max", _f32), ("iter", _u32),
                 ("seed", _u64), ("variant", _i32), ("block_k", _i32),
-                ("chains_per_cta", _i32), ("reserved", _i32)]
+                ("chains_per_cta", _i32), ("debug_wait_polls", _i32)]
 
 
 class sais_solve_params(ctypes.Structure):
@@ -73,6 +73,7 @@ _SIGS = {
     "sais_update_lambda": [_P, _P, _i32, _f64, _i32, _P, _P],
     "sais_track_best": [_P, _P, _P, _P, _i32, _u32, _P, _P, _P, _P, _P, _P],
     "sais_solve": [_P, ctypes.POINTER(sais_solve_params), ctypes.POINTER(sais_solve_result), _P],
+    "sais_synchronize": [_P, _P],
 }
 EXPORTS = list(_SIGS) + ["sais_status_string", "sais_last_error"]
 
@@ -179,6 +180,10 @@ def sais_solve(h, prm, res, stream_ptr):
     _check(lib().sais_solve(h, ctypes.byref(prm), ctypes.byref(res), stream_ptr), "sais_solve")
 
 
+def sais_synchronize(h, stream_ptr):
+    _check(lib().sais_synchronize(h, stream_ptr), "sais_synchronize")
+
+
 def sais_status_string(st: int) -> str:
     return lib().sais_status_string(st).decode()
 
@@ -247,12 +252,18 @@ class Problem:
         except Exception:
             pass
 
-    def _params(self, chains, sweeps, beta_max, seed, it, variant, block_k, chains_per_cta):
+    def _params(self, chains, sweeps, beta_max, seed, it, variant, block_k, chains_per_cta,
+                debug_wait_polls=0):
         p = sais_sample_params()
         p.chains, p.sweeps, p.beta_max, p.iter, p.seed = chains, sweeps, beta_max, it, seed
         p.variant = _VARIANTS[variant] if isinstance(variant, str) else int(variant)
         p.block_k, p.chains_per_cta = block_k, chains_per_cta
+        p.debug_wait_polls = debug_wait_polls
         return p
+
+    def synchronize(self, stream=None):
+        """sais_synchronize: wait for the stream, raise SaisError on a device-side timeout."""
+        sais_synchronize(self.handle, _stream_ptr(stream))
 
     def alloc_outputs(self, chains: int, trace_sweeps: int = 0):
         import torch
@@ -270,11 +281,12 @@ class Problem:
 
     def sample(self, lam, chains: int, sweeps: int, beta_max: float, seed: int, it: int = 0,
                variant="plain", block_k: int = 0, chains_per_cta: int = 0, trace: bool = False,
-               out=None, stream=None):
+               out=None, stream=None, debug_wait_polls: int = 0):
         """One annealing run per chain (sais_sample / sais_sample_trace); returns device tensors
         x [count, chains, words] (int32 bit patterns), cost [count, chains],
         g [count, chains, m_stride], feasible [count, chains] (and trace)."""
-        prm = self._params(chains, sweeps, beta_max, seed, it, variant, block_k, chains_per_cta)
+        prm = self._params(chains, sweeps, beta_max, seed, it, variant, block_k, chains_per_cta,
+                           debug_wait_polls)
         o = out or self.alloc_outputs(chains, sweeps if trace else 0)
         sp = _stream_ptr(stream)
         args = (_P(lam.data_ptr()), _P(o["x"].data_ptr()), _P(o["cost"].data_ptr()),

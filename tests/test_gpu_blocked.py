@@ -1,0 +1,139 @@
+"""Blocked sampler (tcgen05 rank-k field update) against the plain sampler and the oracle.
+
+The rank-k update is exact (integer products and sums below 2^24 in FP32), so the blocked
+sampler must make every decision the plain sampler makes: identical states after every sweep,
+identical costs, constraint values and feasibility, and both identical to the CPU oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_04971_gb300 import sais, workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _lam(prob, lams):
+    a = np.zeros((prob.count, prob.m_stride), np.float32)
+    for j, l in enumerate(lams):
+        a[j, :len(l)] = l
+    return torch.tensor(a.reshape(-1), device="cuda:0")
+
+
+def _run(prob, lam, C, T, beta, seed, it, variant, block_k=0, trace=False):
+    out = prob.sample(lam, C, T, beta, seed, it, variant=variant, block_k=block_k, trace=trace)
+    prob.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def _compare(insts, lams, C, T, beta, seed, it, block_k, trace=False, oracle_chains=None):
+    prob = sais.Problem(insts)
+    lam = _lam(prob, lams)
+    p = _run(prob, lam, C, T, beta, seed, it, "plain", trace=trace)
+    b = _run(prob, lam, C, T, beta, seed, it, "blocked", block_k=block_k, trace=trace)
+    for k in p:
+        if not np.array_equal(p[k], b[k]):
+            diff = np.argwhere(p[k] != b[k])
+            raise AssertionError(f"{k}: blocked differs from plain at {len(diff)} places, "
+                                 f"first {diff[:4].tolist()}")
+    for j, inst in enumerate(insts):
+        ref = oracle.Problem(inst.n, inst.m, inst.W, inst.h, inst.A, inst.b, alpha=inst.alpha,
+                             density=inst.density)
+        J, hI, _ = ref.ising(np.asarray(lams[j], np.float32))
+        c0, nc = oracle_chains or (0, C)
+        want = oracle.anneal(J, hI, beta, T, seed + j, it, nc, chain0=c0)
+        got = sais.unpack_bits(b["x"][j], ref.nprime)[c0:c0 + nc]
+        assert np.array_equal(got, want), f"instance {j}: blocked states differ from the oracle"
+        x = sais.unpack_bits(b["x"][j], ref.nprime)
+        for c in range(0, C, max(1, C // 16)):
+            assert b["cost"][j, c] == ref.cost(x[c])
+            assert np.array_equal(b["g"][j, c, :ref.m], ref.constraints(x[c]))
+            assert bool(b["feasible"][j, c]) == ref.feasible(x[c])
+    prob.close()
+
+
+@pytest.mark.parametrize("block_k", [16, 32])
+def test_blocked_equals_plain_qkp_n100(block_k):
+    _compare([wl.qkp(100, 0.25, 0)], [[0.5]], C=128, T=200, beta=10.0, seed=3, it=1,
+             block_k=block_k)
+
+
+def test_blocked_fewer_chains_than_lanes():
+    _compare([wl.qkp(100, 0.25, 1)], [[0.9]], C=64, T=150, beta=10.0, seed=4, it=0, block_k=32)
+
+
+def test_blocked_ragged_chain_groups_and_spins():
+    """200 chains (two CTAs, the second ragged) on an instance whose N' is not a multiple of
+    the block size."""
+    inst = wl.qkp(45, 0.5, 5)
+    _compare([inst], [[0.4]], C=200, T=120, beta=10.0, seed=5, it=2, block_k=32)
+
+
+def test_blocked_mixed_batch_sizes():
+    """Instances of different N' (N'_pad 64 .. 320) in one launch."""
+    insts = [wl.qkp(50, 0.5, 6), wl.qkp(120, 0.75, 7), wl.qkp(300, 0.25, 8), wl.qkp(200, 1.0, 9)]
+    _compare(insts, [[0.3], [1.1], [2.0], [0.0]], C=128, T=100, beta=10.0, seed=6, it=4,
+             block_k=32, oracle_chains=(0, 8))
+
+
+def test_blocked_trace_every_sweep_equals_plain():
+    _compare([wl.qkp(80, 0.5, 10)], [[0.6]], C=128, T=60, beta=10.0, seed=7, it=3, block_k=32,
+             trace=True)
+
+
+def test_blocked_full_size_qkp300():
+    """QKP N=300 at the four densities, 128 chains, 1000 sweeps: blocked == plain everywhere,
+    sampled chains against the oracle."""
+    insts = [wl.qkp(300, d, s) for d in (0.25, 0.5, 0.75, 1.0) for s in range(2)]
+    lams = [[0.5 + 0.4 * j] for j in range(len(insts))]
+    _compare(insts, lams, C=128, T=1000, beta=10.0, seed=8, it=0, block_k=32,
+             oracle_chains=(0, 2))
+
+
+def test_blocked_solve_equals_plain_solve():
+    inst = wl.qkp(100, 0.5, 11)
+    prob = sais.Problem(inst)
+    a = prob.solve(6, 128, 200, 10.0, 20.0, 13, variant="plain")
+    b = prob.solve(6, 128, 200, 10.0, 20.0, 13, variant="blocked", use_graph=True)
+    prob.close()
+    for k in ("best_cost", "best_x", "best_iter", "best_chain", "feasible_count",
+              "lambda_trace", "lambda_final"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_blocked_timeout_path_reports_and_recovers():
+    """A wait bound of one poll makes the decision warps give up: the kernel records
+    SAIS_ETIMEOUT, drains its copies and MMAs, frees TMEM and exits; the context stays usable
+    and the next launch is correct."""
+    inst = wl.qkp(60, 0.5, 12)
+    prob = sais.Problem(inst)
+    lam = _lam(prob, [[0.5]])
+    prob.sample(lam, 128, 50, 10.0, 1, 0, variant="blocked", debug_wait_polls=1)
+    with pytest.raises(sais.SaisError) as e:
+        prob.synchronize()
+    assert e.value.status == sais.SAIS_ETIMEOUT
+    prob.synchronize()  # status word was reset
+    p = _run(prob, lam, 128, 50, 10.0, 1, 0, "plain")
+    b = _run(prob, lam, 128, 50, 10.0, 1, 0, "blocked")
+    assert np.array_equal(p["x"], b["x"])
+    prob.close()
+
+
+def test_blocked_unsupported_cases():
+    for inst in (wl.mkp(40, 3, 1), wl.qkp(50, 0.5, 2, profit_max=1000)):
+        prob = sais.Problem(inst)
+        lam = torch.zeros(prob.count * prob.m_stride, device="cuda:0")
+        with pytest.raises(sais.SaisError) as e:
+            prob.sample(lam, 128, 10, 10.0, 1, 0, variant="blocked")
+        assert e.value.status == sais.SAIS_EUNSUPPORTED
+        prob.close()
