@@ -120,7 +120,7 @@ typedef struct sais_sample_params {
     uint32_t iter;           /* outer-iteration index k (selects the random stream)         */
     uint64_t seed;           /* instance j uses seed + j                                    */
     int32_t variant;         /* sais_variant                                                */
-    int32_t block_k;         /* SAIS_BLOCKED: spins per block (16 or 32); 0 = default (32)   */
+    int32_t block_k;         /* SAIS_BLOCKED: spins per block (16 or 32); 0 = default (16)   */
     int32_t chains_per_cta;  /* 0 = library choice; else 32, 64 or 128                      */
     int32_t debug_wait_polls; /* 0 = normal.  > 0 (fault-injection tests of the timeout path):
                                 the blocked sampler's decision warps first wait, for at most

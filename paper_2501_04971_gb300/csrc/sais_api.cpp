@@ -512,7 +512,7 @@ sais_status enqueue_sample(sais_problem *p, const sais_sample_params *prm, const
     cudaError_t e;
     a.status = p->d_status;
     if (prm->variant == SAIS_BLOCKED) {
-        const int k = prm->block_k ? prm->block_k : 32;
+        const int k = prm->block_k ? prm->block_k : 16;
         if (!p->all_w)
             return fail(SAIS_EUNSUPPORTED,
                         "blocked sampler: every instance needs a quadratic objective W "

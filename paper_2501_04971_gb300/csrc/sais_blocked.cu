@@ -221,22 +221,26 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                       : true;
         if (ok) ok = wait_bounded_warp(&bars[0], 0, abort_flag, status, 0);
         uint32_t it = 0;
+        // Noise of the current block (theta = atanh(rho), independent of the state).  The next
+        // block's noise is computed inside the decision loop, one spin at a time, so that the
+        // scheduler can overlap it with the sequential decision chain.
+        float th[K];
+#pragma unroll
+        for (int q = 0; q < K / 4; ++q) {
+            const uint4 rw = philox4x32_10(make_uint4((uint32_t)q, 0u, (uint32_t)chain, iter),
+                                           key0, key1);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) th[4 * q + e] = theta_of_word(word_of(rw, e));
+        }
         for (int t = 0; ok && t < a.sweeps; ++t) {
             const float beta = beta_of_sweep(a.beta_max, t, a.sweeps);
             const float hb = 0.5f * beta;
             const float ez = hb * errk;
             for (int b = 0; b < nb; ++b) {
                 const int s0 = b * K;
-                // Noise of the block (independent of the state): theta = atanh(rho).
-                float th[K];
-#pragma unroll
-                for (int q = 0; q < K / 4; ++q) {
-                    const uint4 rw = philox4x32_10(
-                        make_uint4((uint32_t)((s0 >> 2) + q), (uint32_t)t, (uint32_t)chain, iter),
-                        key0, key1);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) th[4 * q + e] = atanhf(rho_of_word(word_of(rw, e)));
-                }
+                const bool last = b + 1 == nb;
+                const uint32_t nx_grp = last ? 0u : (uint32_t)((s0 + K) >> 2);
+                const uint32_t nx_t = last ? (uint32_t)(t + 1) : (uint32_t)t;
                 if (it > 0) {
                     if (!wait_bounded_warp(&bars[3], (it - 1u) & 1u, abort_flag, status,
                                            dec_wait_polls)) {
@@ -250,8 +254,15 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                 const int wi = s0 >> 5, sb = s0 & 31;
                 uint32_t xw = xs[wi * kLanes + r];
                 const uint32_t xold = xw;
+                float thn[K];
+                uint4 rwn = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
                 for (int ii = 0; ii < K; ++ii) {
+                    if ((ii & 3) == 0)
+                        rwn = philox4x32_10(make_uint4(nx_grp + (uint32_t)(ii >> 2), nx_t,
+                                                       (uint32_t)chain, iter),
+                                            key0, key1);
+                    thn[ii] = theta_of_word(word_of(rwn, ii & 3));
                     const int s = s0 + ii;
                     if (s < nprime) {
                         const float Fi = Fr[ii];
@@ -270,11 +281,9 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                         const float theta = th[ii];
                         const float y = z + theta;
                         const float bound = ez * (tabs + __ldg(asum + s) * Mmax + Di) +
-                                            kThetaRelErr * fabsf(theta);
-                        int xn;
-                        if (fabsf(y) > bound) {
-                            xn = y > 0.f;
-                        } else {
+                                            kThetaRelErr * fabsf(theta) + kThetaAbsErr;
+                        int xn = y > 0.f;
+                        if (!(fabsf(y) > bound)) {
                             const uint4 rw = philox4x32_10(
                                 make_uint4((uint32_t)(s >> 2), (uint32_t)t, (uint32_t)chain, iter),
                                 key0, key1);
@@ -282,17 +291,17 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                             xn = decide_exact<MC>(Fi, xi, ak, g, lam, m, sf, sg, psg2, beta, rho);
                         }
                         const int d = xn - xi;
-                        if (d != 0) {
-                            xw ^= 1u << (sb + ii);
-                            Mmax = 0.f;
+                        // Constraint state follows the flip without a branch (d = 0 leaves every
+                        // value bit-identical).
+                        xw ^= (uint32_t)(d != 0) << (sb + ii);
+                        Mmax = 0.f;
 #pragma unroll
-                            for (int k = 0; k < MC; ++k) {
-                                if (k < m) {
-                                    g[k] += ak[k] * d;
-                                    c[k] = fmaf(kappa, (float)g[k], cA[k]);
-                                    Mmax = fmaxf(Mmax, fmaf(fabsf(kappa), fabsf((float)g[k]),
-                                                            fabsf(cA[k])));
-                                }
+                        for (int k = 0; k < MC; ++k) {
+                            if (k < m) {
+                                g[k] += ak[k] * d;
+                                c[k] = fmaf(kappa, (float)g[k], cA[k]);
+                                Mmax = fmaxf(Mmax, fmaf(fabsf(kappa), fabsf((float)g[k]),
+                                                        fabsf(cA[k])));
                             }
                         }
                         if (ii + 1 < K && __any_sync(0xffffffffu, d != 0)) {
@@ -317,6 +326,8 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                         }
                     }
                 }
+#pragma unroll
+                for (int ii = 0; ii < K; ++ii) th[ii] = thn[ii];
                 xs[wi * kLanes + r] = xw;
                 // Delta of the block as a BF16 K-major row of the MMA's A operand.
                 unsigned char *Ab = Asm + (it & 1u) * K * 256;
@@ -437,8 +448,8 @@ cudaError_t launch_blocked_sampler(const SampleArgs &a, int max_m, int max_npad,
     const size_t floor_smem = per_sm / (max_ctas + 1) + 1;
     if (smem < floor_smem) smem = floor_smem;
     const long long polls = dec_wait_polls > 0 ? dec_wait_polls : 0;
-    if (block_k == 16) return launch_mc<16>(a, max_m, status, polls, smem, cols, stream);
-    return launch_mc<32>(a, max_m, status, polls, smem, cols, stream);
+    if (block_k == 32) return launch_mc<32>(a, max_m, status, polls, smem, cols, stream);
+    return launch_mc<16>(a, max_m, status, polls, smem, cols, stream);
 }
 
 }  // namespace sais

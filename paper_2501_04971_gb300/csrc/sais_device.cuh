@@ -52,8 +52,26 @@ __device__ __forceinline__ float beta_of_sweep(float beta_max, int t, int T) {
     return __double2float_rn(__ddiv_rn(__dmul_rn((double)beta_max, (double)t), (double)(T - 1)));
 }
 
-// Error bound on atanhf: CUDA documents at most 3 ulp; 2^-20 |theta| allows 8.
-constexpr float kThetaRelErr = 0x1p-20f;
+// theta = atanh(rho) for rho = (2v+1)/2^24 - 1 (v = word >> 8).  With u = (1+rho)/2 =
+// (2v+1)/2^25 and 1-u = (2^25-2v-1)/2^25 (both formed from exact integers and scaled by a power
+// of two), atanh(rho) = (1/2) ln(u/(1-u)) = (ln 2 / 2)(log2 u - log2(1-u)).  log2 is the
+// hardware approximation (lg2.approx.f32).  Both logarithms are of numbers in (0, 1) whose
+// ratio is the quantity of interest, so there is no cancellation near rho = 0.
+__device__ __forceinline__ float theta_of_word(uint32_t w) {
+    const uint32_t v = w >> 8;
+    const float u = (float)(2u * v + 1u) * 0x1p-25f;
+    const float um = (float)((1u << 25) - 2u * v - 1u) * 0x1p-25f;
+    float lu, lum;
+    asm("lg2.approx.f32 %0, %1;" : "=f"(lu) : "f"(u));
+    asm("lg2.approx.f32 %0, %1;" : "=f"(lum) : "f"(um));
+    return 0.34657359028f * (lu - lum);
+}
+
+// Bound on |theta_of_word(w) - atanh(rho)|: kThetaAbsErr + kThetaRelErr |theta|.  The noise takes
+// 2^24 distinct values; a GPU test evaluates all of them against FP64 atanh and checks the
+// bound (measured maximum reported there).
+constexpr float kThetaAbsErr = 0x1p-20f;
+constexpr float kThetaRelErr = 0x1p-21f;
 
 // Error factor of the FP32 field: the evaluation below has at most m + 7 roundings weighted by
 // the magnitudes it adds up (derivation in sais_plain.cu); (m + 12) u with u = 2^-24 and a

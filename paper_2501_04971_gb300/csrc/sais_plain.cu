@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(128) plain_sampler_kernel(SampleArgs a) {
                 if (i >= nprime) break;
                 if ((i & 31) == 0) xw = xs[(i >> 5) * cpb + tid];
                 const float rho = rho_of_word(word_of(rw, q));
-                const float theta = atanhf(rho);
+                const float theta = theta_of_word(word_of(rw, q));
                 const float Fi = has_w ? Fs[i * cpb + tid] : __ldg(hF + i);
                 const int xi = (xw >> (i & 31)) & 1;
                 int32_t ak[MC];
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(128) plain_sampler_kernel(SampleArgs a) {
                 const float z = hb * acc;
                 const float y = z + theta;
                 const float bound =
-                    ez * (tabs + __ldg(asum + i) * Mmax + Di) + kThetaRelErr * fabsf(theta);
+                    ez * (tabs + __ldg(asum + i) * Mmax + Di) + kThetaRelErr * fabsf(theta) + kThetaAbsErr;
                 int xn;
                 if (fabsf(y) > bound)
                     xn = y > 0.f;
