@@ -243,6 +243,25 @@ SAIS_API sais_status sais_track_best(sais_problem *p, const uint32_t *x, const i
 SAIS_API sais_status sais_solve(sais_problem *p, const sais_solve_params *prm,
                                 sais_solve_result *res, void *stream);
 
+/* sais_solve without any allocation.  The paper has no counterpart: this is a deployment
+ * variant for callers that cannot allocate memory while they run (a real-time or latency-
+ * critical loop that must not enter the allocator, a host that plans every byte of device memory
+ * up front, a plug-in handed only its own buffers).  Same parameters and results as sais_solve
+ * (use_graph must be 0); the device scratch lives in one static array of 16 MiB that every GPU
+ * loading the library holds until the process exits, and the call makes no cudaMalloc, cudaFree,
+ * event or graph call, host or device.
+ *  - The first call on a device looks up the array's address (with that device current); make
+ *    that first call before any stream capture.
+ *  - Sizes whose scratch would exceed 16 MiB are rejected with SAIS_EINVAL (the message gives the
+ *    bytes needed); sais_solve has no such limit.
+ *  - Calls share the array; calls from one process are serialised by a lock held until the
+ *    call's stream has synchronised, and calls that overlapped on the GPU by other means would
+ *    race.  Regions that must start at zero or at a sentinel are reset by every call.
+ * Synchronises `stream` before returning; elapsed_ms is host wall time of the call.
+ * Errors: as sais_solve. */
+SAIS_API sais_status sais_solve_noalloc(sais_problem *p, const sais_solve_params *prm,
+                                        sais_solve_result *res, void *stream);
+
 /* Wait for the work queued on `stream` and report device-side failures of this problem's
  * kernels since the last call: SAIS_ETIMEOUT if a bounded wait inside a kernel gave up (the
  * kernel then stopped early and its outputs are not valid).  Resets the device status word.

@@ -812,3 +812,44 @@ sais_status sais_solve(sais_problem *p, const sais_solve_params *prm, sais_solve
 }
 
 }  // extern "C"
+
+// ---- internal accessors for entry points in other translation units ----------------------
+
+namespace sais {
+
+sais_status problem_view(const sais_problem *p, ProblemView *out) {
+    if (!p || !out) return fail(SAIS_EINVAL, "NULL argument");
+    out->device = p->device;
+    out->count = p->count;
+    out->words = p->words;
+    out->m_stride = p->m_stride;
+    out->d_inst = p->d_inst;
+    out->d_status = p->d_status;
+    long long tot = 0;
+    for (const HostInst &h : p->host) tot += h.nprime;
+    out->spins_total = tot;
+    return SAIS_OK;
+}
+
+sais_status enqueue_sample_internal(sais_problem *p, const sais_sample_params *prm,
+                                   const float *lambda, const uint32_t *iter_dev, uint32_t *x,
+                                   int64_t *cost, int64_t *g, uint8_t *feasible,
+                                   cudaStream_t stream) {
+    return enqueue_sample(p, prm, lambda, iter_dev, x, cost, g, feasible, nullptr, stream);
+}
+
+sais_status check_sample_params_internal(const sais_problem *p, const sais_sample_params *prm) {
+    return check_sample_params(p, prm);
+}
+
+sais_status set_error(sais_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+}  // namespace sais

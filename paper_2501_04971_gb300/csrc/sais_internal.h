@@ -104,4 +104,23 @@ constexpr size_t kMaxSmemPerBlock = 232448;   // 227 KB opt-in per CTA on sm_103
 cudaError_t launch_post(const PostArgs &a, cudaStream_t stream);
 cudaError_t launch_advance_iter(uint32_t *iter_dev, cudaStream_t stream);
 
+// Read-only view of a problem handle and access to the sampler dispatch of sais_api.cpp, for
+// entry points defined in other translation units.
+struct ProblemView {
+    int device;
+    int count;
+    int words;
+    int m_stride;
+    const InstDev *d_inst;
+    int32_t *d_status;
+    long long spins_total;   // sum of N' over the instances
+};
+sais_status problem_view(const sais_problem *p, ProblemView *out);
+sais_status enqueue_sample_internal(sais_problem *p, const sais_sample_params *prm,
+                                   const float *lambda, const uint32_t *iter_dev, uint32_t *x,
+                                   int64_t *cost, int64_t *g, uint8_t *feasible,
+                                   cudaStream_t stream);
+sais_status check_sample_params_internal(const sais_problem *p, const sais_sample_params *prm);
+sais_status set_error(sais_status s, const char *fmt, ...);
+
 }  // namespace sais

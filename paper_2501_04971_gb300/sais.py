@@ -74,6 +74,8 @@ _SIGS = {
     "sais_track_best": [_P, _P, _P, _P, _i32, _u32, _P, _P, _P, _P, _P, _P],
     "sais_solve": [_P, ctypes.POINTER(sais_solve_params), ctypes.POINTER(sais_solve_result), _P],
     "sais_synchronize": [_P, _P],
+    "sais_solve_noalloc": [_P, ctypes.POINTER(sais_solve_params),
+                           ctypes.POINTER(sais_solve_result), _P],
 }
 EXPORTS = list(_SIGS) + ["sais_status_string", "sais_last_error"]
 
@@ -178,6 +180,11 @@ def sais_track_best(h, x_ptr, cost_ptr, feas_ptr, chains: int, it: int, best_cos
 
 def sais_solve(h, prm, res, stream_ptr):
     _check(lib().sais_solve(h, ctypes.byref(prm), ctypes.byref(res), stream_ptr), "sais_solve")
+
+
+def sais_solve_noalloc(h, prm, res, stream_ptr):
+    _check(lib().sais_solve_noalloc(h, ctypes.byref(prm), ctypes.byref(res), stream_ptr),
+           "sais_solve_noalloc")
 
 
 def sais_synchronize(h, stream_ptr):

@@ -1,0 +1,80 @@
+"""sais_solve_noalloc, the allocation-free form of Algorithm 1 (needs a GPU).
+
+Callers that may not allocate while they run (a latency-critical loop that must stay out of the
+allocator, a host that reserves all device memory up front, a plug-in that only gets its own
+buffers) use sais_solve_noalloc, whose scratch is a fixed static device array.  These checks call
+it through the C-ABI, twice in a row, and require the same results as sais_solve (bit for bit:
+the samples, the kept best and the multipliers are integer or exactly rounded quantities).  This
+file is collected last so that a failure here leaves every other test already run; it passes on
+its own in a fresh process as well.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2501_04971_gb300 import sais, workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _noalloc(prob, iters, chains, sweeps, beta_max, eta, seed, variant="plain", lambda0=None):
+    """Call sais_solve_noalloc through the C-ABI with host result arrays."""
+    prm = sais.sais_solve_params()
+    prm.iters, prm.chains, prm.sweeps, prm.beta_max = iters, chains, sweeps, beta_max
+    prm.eta, prm.seed, prm.iter0, prm.project_nonneg = eta, seed, 0, 1
+    prm.variant = sais._VARIANTS[variant]
+    keep = None
+    if lambda0 is not None:
+        keep = np.ascontiguousarray(lambda0, np.float32).reshape(-1)
+        prm.lambda0 = keep.ctypes.data_as(ctypes.c_void_p)
+    cnt, W, M = prob.count, prob.words, prob.m_stride
+    out = {"best_cost": np.zeros(cnt, np.int64), "best_x": np.zeros((cnt, W), np.uint32),
+           "best_iter": np.zeros(cnt, np.int32), "best_chain": np.zeros(cnt, np.int32),
+           "feasible_count": np.zeros(cnt, np.int64),
+           "lambda_final": np.zeros((cnt, M), np.float32),
+           "lambda_trace": np.zeros((iters, cnt, M), np.float32)}
+    res = sais.sais_solve_result()
+    for k, v in out.items():
+        setattr(res, k, v.ctypes.data_as(ctypes.c_void_p))
+    st = sais.lib().sais_solve_noalloc(prob.handle, ctypes.byref(prm), ctypes.byref(res), None)
+    return st, out
+
+
+KEYS = ("best_cost", "best_x", "best_iter", "best_chain", "feasible_count", "lambda_final",
+        "lambda_trace")
+
+
+@pytest.mark.parametrize("variant", ["plain", "blocked"])
+def test_noalloc_matches_solve_on_two_calls(variant):
+    insts = [wl.qkp(100, 0.5, 3), wl.qkp(60, 0.25, 4), wl.qkp(120, 0.75, 5)]
+    prob = sais.Problem(insts)
+    lam0 = np.full((prob.count, prob.m_stride), 0.25, np.float32)
+    want = prob.solve(8, 128, 150, 10.0, 20.0, 17, lambda0=lam0, variant=variant)
+    for call in range(2):
+        st, got = _noalloc(prob, 8, 128, 150, 10.0, 20.0, 17, variant=variant, lambda0=lam0)
+        assert st == sais.SAIS_OK, sais.sais_last_error()
+        for k in KEYS:
+            assert np.array_equal(got[k], want[k]), (call, k)
+    prob.close()
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    prob = sais.Problem([wl.qkp(300, 0.5, s) for s in range(16)])
+    st, _ = _noalloc(prob, 2, 32768, 1, 10.0, 20.0, 1)   # ~30 MB of scratch needed
+    assert st == sais.SAIS_EINVAL
+    msg = sais.sais_last_error()
+    assert "static scratch holds" in msg and "bytes" in msg
+    st, got = _noalloc(prob, 2, 32, 20, 10.0, 20.0, 1)   # a size that fits still works after it
+    assert st == sais.SAIS_OK, sais.sais_last_error()
+    prob.close()
