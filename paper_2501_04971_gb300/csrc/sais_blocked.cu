@@ -18,8 +18,11 @@
 //          block form a contiguous K-major operand (LBO = 16 N'_pad, SBO = 128); loaded once
 //          per launch by bulk asynchronous copies (TMA engine).  Delta tiles (double buffered):
 //          element (chain r, k) at (k/8) 2048 + r 16 + (k%8) 2, written by the chain's thread.
-//   Warps  0-3 decide (warp w owns TMEM lanes 32w..32w+31, i.e. its 32 chains); warp 4 lane 0
-//          issues the copies and the MMAs.  Every mbarrier wait is bounded: on expiry the kernel
+//   Warps  0-3 decide (warp w owns TMEM lanes 32w..32w+31, i.e. its 32 chains); warps 4-7
+//          compute the noise (Philox, atanh) of the next block for decision warps 0-3 into a
+//          shared buffer, so that every SM sub-partition has a second warp to issue from while
+//          its decision warp waits on a dependency; lane 0 of warp 4 also stages W and issues
+//          the copies and the MMAs.  Every mbarrier wait is bounded: on expiry the kernel
 //          records SAIS_ETIMEOUT, stops, drains its copies and MMAs, frees TMEM and exits.
 #include "sais_device.cuh"
 #include "sais_tc.cuh"
@@ -29,7 +32,8 @@ namespace {
 
 constexpr int kLanes = 128;
 constexpr int kIssueThread = 128;
-constexpr int kThreadsBlocked = 160;
+constexpr int kThreadsBlocked = 256;   // 4 decision warps, 4 noise warps
+constexpr int kNoiseWarp0 = 4;
 // Every wait of this kernel is for an event microseconds away (an MMA, a block of decisions,
 // a 200 KB copy).  A wait gives up after kWaitNs of wall time, or after `polls` polls when a
 // test asks for a poll bound (polls > 0).
@@ -109,10 +113,12 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
     unsigned char *Wsm = smem;
     unsigned char *Asm = smem + wbytes;
     uint32_t *xs = reinterpret_cast<uint32_t *>(Asm + 2 * K * 256);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(xs + words * kLanes);
+    float *thbuf = reinterpret_cast<float *>(xs + words * kLanes);    // [K][128] noise
+    uint64_t *bars = reinterpret_cast<uint64_t *>(thbuf + K * kLanes);
     // bars: 0 = W staged, 1/2 = Delta tile 0/1 written, 3 = block MMAs done, 4 = drain,
-    // 5 = never completed (fault-injection test of the timeout path)
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 6);
+    // 5 = never completed (fault-injection test of the timeout path),
+    // 6..9 = noise of the next block written (per warp pair), 10..13 = noise consumed
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 14);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     if (threadIdx.x == kIssueThread) {
@@ -122,6 +128,10 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
         tc::mbar_init(&bars[3], 1);
         tc::mbar_init(&bars[4], 1);
         tc::mbar_init(&bars[5], 1);
+        for (int q = 0; q < 4; ++q) {
+            tc::mbar_init(&bars[6 + q], 1);
+            tc::mbar_init(&bars[10 + q], 1);
+        }
         *abort_flag = 0;
         tc::fence_mbar_init();
         tc::fence_proxy_async_smem();
@@ -136,42 +146,83 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
     const uint32_t tmem = *tmem_slot;
     const uint32_t iter = a.iter_dev ? *a.iter_dev : a.iter;
 
-    if (warp == 4) {
-        if (lane == 0) {
+    if (warp >= kNoiseWarp0) {
+        // Noise warps: warp 4+q produces theta = atanh(rho) of the next block for the chains of
+        // decision warp q, one block ahead, into the shared noise buffer.  Lane 0 of warp 4 also
+        // stages W and issues each block's MMAs once its Delta tile is written.
+        const int q = warp - kNoiseWarp0;
+        const int r = q * 32 + lane;
+        const uint32_t chain = (uint32_t)(blockIdx.x * kLanes + r);
+        const uint64_t seed = a.seed + (uint64_t)j;
+        const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
+        const uint32_t total = (uint32_t)a.sweeps * (uint32_t)nb;
+        const bool issuer = q == 0 && lane == 0;
+        const uint32_t lbo_b = (uint32_t)npad * 16u;
+        if (issuer) {
             tc::mbar_expect_tx(&bars[0], wbytes);
             const unsigned char *src = reinterpret_cast<const unsigned char *>(ip->Wbf);
             for (uint32_t off = 0; off < wbytes; off += 32768u)
                 tc::bulk_g2s(Wsm + off, src + off, min(32768u, wbytes - off), &bars[0]);
-            const uint32_t total = (uint32_t)a.sweeps * (uint32_t)nb;
-            const uint32_t lbo_b = (uint32_t)npad * 16u;
-            for (uint32_t it = 0; it < total; ++it) {
-                const int buf = (int)(it & 1u);
-                if (!wait_bounded(&bars[1 + buf], (it >> 1) & 1u, abort_flag, status, 0))
-                    break;
-                tc::tc_fence_after();
-                const uint32_t b = it % (uint32_t)nb;
-                const uint32_t a_base = tc::smem_u32(Asm + buf * K * 256);
-                const uint32_t w_base = tc::smem_u32(Wsm) + b * (uint32_t)(K / 8) * lbo_b;
-#pragma unroll
-                for (int ks = 0; ks < K / 16; ++ks) {
-                    const uint64_t ad = tc::smem_desc(a_base + (uint32_t)ks * 4096u, 2048u, 128u);
-                    for (int j0 = 0; j0 < npad; j0 += 256) {
-                        const int nr = min(256, npad - j0);
-                        const uint64_t bd = tc::smem_desc(
-                            w_base + (uint32_t)ks * 2u * lbo_b + (uint32_t)j0 * 16u, lbo_b, 128u);
-                        tc::mma_bf16(tmem + (uint32_t)j0, ad, bd,
-                                     tc::idesc_bf16_f32(128, (uint32_t)nr), 1u);
-                    }
-                }
-                tc::mma_commit(&bars[3]);
-            }
-            // Drain: every MMA issued above and the staging copies complete before TMEM and
-            // shared memory are released.
-            tc::mma_commit(&bars[4]);
-            wait_bounded(&bars[4], 0, nullptr, status, 0);
-            wait_bounded(&bars[0], 0, nullptr, status, 0);
         }
-        __syncwarp();
+        // MMAs of block i: F[:, chains] += W[:, blk] Delta[blk, chains] (issuer only).
+        auto issue_block = [&](uint32_t i) -> bool {
+            const int buf = (int)(i & 1u);
+            if (!wait_bounded(&bars[1 + buf], (i >> 1) & 1u, abort_flag, status, 0)) return false;
+            tc::tc_fence_after();
+            const uint32_t b = i % (uint32_t)nb;
+            const uint32_t a_base = tc::smem_u32(Asm + buf * K * 256);
+            const uint32_t w_base = tc::smem_u32(Wsm) + b * (uint32_t)(K / 8) * lbo_b;
+#pragma unroll
+            for (int ks = 0; ks < K / 16; ++ks) {
+                const uint64_t ad = tc::smem_desc(a_base + (uint32_t)ks * 4096u, 2048u, 128u);
+                for (int j0 = 0; j0 < npad; j0 += 256) {
+                    const int nr = min(256, npad - j0);
+                    const uint64_t bd = tc::smem_desc(
+                        w_base + (uint32_t)ks * 2u * lbo_b + (uint32_t)j0 * 16u, lbo_b, 128u);
+                    tc::mma_bf16(tmem + (uint32_t)j0, ad, bd, tc::idesc_bf16_f32(128, (uint32_t)nr),
+                                 1u);
+                }
+            }
+            tc::mma_commit(&bars[3]);
+            return true;
+        };
+        bool ok = true;
+        for (uint32_t it = 0; it < total; ++it) {
+            if (it > 0 &&
+                !wait_bounded_warp(&bars[10 + q], (it - 1u) & 1u, abort_flag, status, 0)) {
+                ok = false;
+                break;
+            }
+            const uint32_t t = it / (uint32_t)nb;
+            const int s0 = (int)(it % (uint32_t)nb) * K;
+#pragma unroll
+            for (int g4 = 0; g4 < K / 4; ++g4) {
+                const uint4 rw = philox4x32_10(
+                    make_uint4((uint32_t)((s0 >> 2) + g4), t, chain, iter), key0, key1);
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    thbuf[(4 * g4 + e) * kLanes + r] = theta_of_word(word_of(rw, e));
+            }
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&bars[6 + q]);
+            if (q == 0 && it > 0) {
+                bool issued = true;
+                if (issuer) issued = issue_block(it - 1u);
+                ok = __shfl_sync(0xffffffffu, issued ? 1 : 0, 0) != 0;
+                if (!ok) break;
+            }
+        }
+        if (q == 0) {
+            if (issuer) {
+                if (ok && total > 0) issue_block(total - 1u);
+                // Drain: every MMA issued and the staging copies complete before TMEM and
+                // shared memory are released.
+                tc::mma_commit(&bars[4]);
+                wait_bounded(&bars[4], 0, nullptr, status, 0);
+                wait_bounded(&bars[0], 0, nullptr, status, 0);
+            }
+            __syncwarp();
+        }
     } else {
         const int r = threadIdx.x;
         const int chain = blockIdx.x * kLanes + r;
@@ -221,26 +272,23 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                       : true;
         if (ok) ok = wait_bounded_warp(&bars[0], 0, abort_flag, status, 0);
         uint32_t it = 0;
-        // Noise of the current block (theta = atanh(rho), independent of the state).  The next
-        // block's noise is computed inside the decision loop, one spin at a time, so that the
-        // scheduler can overlap it with the sequential decision chain.
         float th[K];
-#pragma unroll
-        for (int q = 0; q < K / 4; ++q) {
-            const uint4 rw = philox4x32_10(make_uint4((uint32_t)q, 0u, (uint32_t)chain, iter),
-                                           key0, key1);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) th[4 * q + e] = theta_of_word(word_of(rw, e));
-        }
         for (int t = 0; ok && t < a.sweeps; ++t) {
             const float beta = beta_of_sweep(a.beta_max, t, a.sweeps);
             const float hb = 0.5f * beta;
             const float ez = hb * errk;
             for (int b = 0; b < nb; ++b) {
                 const int s0 = b * K;
-                const bool last = b + 1 == nb;
-                const uint32_t nx_grp = last ? 0u : (uint32_t)((s0 + K) >> 2);
-                const uint32_t nx_t = last ? (uint32_t)(t + 1) : (uint32_t)t;
+                // Noise of the block, written by this warp's partner noise warp.
+                if (!wait_bounded_warp(&bars[6 + warp], it & 1u, abort_flag, status,
+                                       dec_wait_polls)) {
+                    ok = false;
+                    break;
+                }
+#pragma unroll
+                for (int ii = 0; ii < K; ++ii) th[ii] = thbuf[ii * kLanes + r];
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&bars[10 + warp]);
                 if (it > 0) {
                     if (!wait_bounded_warp(&bars[3], (it - 1u) & 1u, abort_flag, status,
                                            dec_wait_polls)) {
@@ -254,15 +302,8 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                 const int wi = s0 >> 5, sb = s0 & 31;
                 uint32_t xw = xs[wi * kLanes + r];
                 const uint32_t xold = xw;
-                float thn[K];
-                uint4 rwn = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
                 for (int ii = 0; ii < K; ++ii) {
-                    if ((ii & 3) == 0)
-                        rwn = philox4x32_10(make_uint4(nx_grp + (uint32_t)(ii >> 2), nx_t,
-                                                       (uint32_t)chain, iter),
-                                            key0, key1);
-                    thn[ii] = theta_of_word(word_of(rwn, ii & 3));
                     const int s = s0 + ii;
                     if (s < nprime) {
                         const float Fi = Fr[ii];
@@ -326,8 +367,6 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                         }
                     }
                 }
-#pragma unroll
-                for (int ii = 0; ii < K; ++ii) th[ii] = thn[ii];
                 xs[wi * kLanes + r] = xw;
                 // Delta of the block as a BF16 K-major row of the MMA's A operand.
                 unsigned char *Ab = Asm + (it & 1u) * K * 256;
@@ -432,7 +471,7 @@ cudaError_t launch_mc(const SampleArgs &a, int max_m, int32_t *status, long long
 
 size_t blocked_smem_bytes(int max_npad, int max_words, int block_k) {
     return (size_t)max_npad * max_npad * 2 + (size_t)2 * block_k * 256 +
-           (size_t)max_words * kLanes * 4 + 8 * 8 + 16;
+           (size_t)max_words * kLanes * 4 + (size_t)block_k * kLanes * 4 + 14 * 8 + 16;
 }
 
 cudaError_t launch_blocked_sampler(const SampleArgs &a, int max_m, int max_npad, int max_words,

@@ -83,7 +83,7 @@ def test_blocked_mixed_batch_sizes():
     """Instances of different N' (N'_pad 64 .. 320) in one launch."""
     insts = [wl.qkp(50, 0.5, 6), wl.qkp(120, 0.75, 7), wl.qkp(300, 0.25, 8), wl.qkp(200, 1.0, 9)]
     _compare(insts, [[0.3], [1.1], [2.0], [0.0]], C=128, T=100, beta=10.0, seed=6, it=4,
-             block_k=32, oracle_chains=(0, 8))
+             block_k=16, oracle_chains=(0, 8))
 
 
 def test_blocked_trace_every_sweep_equals_plain():
@@ -96,7 +96,7 @@ def test_blocked_full_size_qkp300():
     sampled chains against the oracle."""
     insts = [wl.qkp(300, d, s) for d in (0.25, 0.5, 0.75, 1.0) for s in range(2)]
     lams = [[0.5 + 0.4 * j] for j in range(len(insts))]
-    _compare(insts, lams, C=128, T=1000, beta=10.0, seed=8, it=0, block_k=32,
+    _compare(insts, lams, C=128, T=1000, beta=10.0, seed=8, it=0, block_k=16,
              oracle_chains=(0, 2))
 
 
