@@ -149,10 +149,11 @@ sais_status build_host(const sais_problem_desc *d, HostInst &h) {
     h.psg2 = (double)h.P * (double)h.sg * (double)h.sg;
     h.kappa = (float)(2.0 * h.psg2);
 
-    // Spin-major constraint columns of A_ext, D_i and sum_k a_ki.
-    h.acol.assign((size_t)nprime * std::max(m, 1), 0);
-    h.D.assign(nprime, 0.f);
-    h.asum.assign(nprime, 0.f);
+    // Spin-major constraint columns of A_ext, D_i and sum_k a_ki, zero-padded to N'_pad spins
+    // (kernels may read whole blocks of spins).
+    h.acol.assign((size_t)h.npad * std::max(m, 1), 0);
+    h.D.assign(h.npad, 0.f);
+    h.asum.assign(h.npad, 0.f);
     h.b.assign(m, 0);
     for (int32_t k = 0; k < m; ++k) {
         h.b[k] = (int32_t)d->b[k];
@@ -310,9 +311,9 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
         o.acol = cur;
         cur = align_up(cur + h.acol.size() * 4, 256);
         o.D = cur;
-        cur = align_up(cur + (size_t)h.nprime * 4, 256);
+        cur = align_up(cur + h.D.size() * 4, 256);
         o.asum = cur;
-        cur = align_up(cur + (size_t)h.nprime * 4, 256);
+        cur = align_up(cur + h.asum.size() * 4, 256);
         o.b = cur;
         cur = align_up(cur + (size_t)std::max(h.m, 1) * 4, 256);
         o.so = cur;

@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
     blocked_sampler_kernel(SampleArgs a, int32_t *status, long long dec_wait_polls,
                            uint32_t tmem_cols) {
     extern __shared__ __align__(1024) unsigned char smem[];
+    constexpr int kPreM = MC < 2 ? MC : 2;   // constraint columns preloaded per block
     const int j = blockIdx.y;
     const InstDev *__restrict__ ip = a.inst + j;
     const int m = ip->m, nprime = ip->nprime, npad = ip->npad, words = ip->words;
@@ -302,6 +303,18 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                 const int wi = s0 >> 5, sb = s0 & 31;
                 uint32_t xw = xs[wi * kLanes + r];
                 const uint32_t xold = xw;
+                // Per-spin constants of the block, loaded together before the sequential loop
+                // (spins past N' read the zero padding of the arrays).
+                float Dp[K], Sp[K];
+                int32_t Ap[K][kPreM];
+#pragma unroll
+                for (int ii = 0; ii < K; ++ii) {
+                    Dp[ii] = __ldg(Dv + s0 + ii);
+                    Sp[ii] = __ldg(asum + s0 + ii);
+#pragma unroll
+                    for (int k = 0; k < kPreM; ++k)
+                        Ap[ii][k] = k < m ? __ldg(acol + (size_t)(s0 + ii) * m + k) : 0;
+                }
 #pragma unroll
                 for (int ii = 0; ii < K; ++ii) {
                     const int s = s0 + ii;
@@ -313,15 +326,18 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                         const float tabs = fabsf(acc);
 #pragma unroll
                         for (int k = 0; k < MC; ++k) {
-                            ak[k] = (k < m) ? __ldg(acol + (size_t)s * m + k) : 0;
+                            if (k < kPreM)
+                                ak[k] = Ap[ii][k < kPreM ? k : 0];
+                            else
+                                ak[k] = (k < m) ? __ldg(acol + (size_t)s * m + k) : 0;
                             acc = fmaf(-(float)ak[k], c[k], acc);
                         }
-                        const float Di = __ldg(Dv + s);
+                        const float Di = Dp[ii];
                         acc = fmaf(xi ? 1.f : -1.f, Di, acc);
                         const float z = hb * acc;
                         const float theta = th[ii];
                         const float y = z + theta;
-                        const float bound = ez * (tabs + __ldg(asum + s) * Mmax + Di) +
+                        const float bound = ez * (tabs + Sp[ii] * Mmax + Di) +
                                             kThetaRelErr * fabsf(theta) + kThetaAbsErr;
                         int xn = y > 0.f;
                         if (!(fabsf(y) > bound)) {

@@ -32,9 +32,9 @@ struct InstDev {
     double psg2;        // P sigma_g^2 in FP64 (exact-path evaluation)
     const int16_t *W;   // npad x npad row-major pair values, zero padded (NULL if !has_w)
     const float *hF;    // npad: h_i as FP32 (exact integers), 0 for slack/padding
-    const int32_t *acol;   // nprime x m, spin-major: a_ki of A_ext
-    const float *D;        // nprime: fl(P sigma_g^2 sum_k a_ki^2)
-    const float *asum;     // nprime: sum_k a_ki (exact in FP32)
+    const int32_t *acol;   // npad x m, spin-major: a_ki of A_ext (zero past N')
+    const float *D;        // npad: fl(P sigma_g^2 sum_k a_ki^2) (zero past N')
+    const float *asum;     // npad: sum_k a_ki, exact in FP32 (zero past N')
     const int32_t *b;      // m capacities
     const int32_t *slack_off;  // m+1: first slack spin of constraint k; [m] = N'
     // BF16 copy of W for the blocked sampler in its shared-memory image: column-chunk major,
