@@ -57,7 +57,8 @@ struct HostInst {
     bool need_lo = false;                  // some |W| > 256: BF16 hi/lo split
     std::vector<int32_t> Q, slack_off;     // m, m+1
     std::vector<int32_t> acol;             // nprime x m (spin-major)
-    std::vector<float> D, asum;            // nprime
+    std::vector<float> D, asum;            // npad
+    std::vector<float> spinc;              // npad x 4: a_0 (int bits), D, sum a, a_1 (int bits)
     std::vector<int32_t> b;                // m
     std::vector<float> hF;                 // npad
     const int32_t *W = nullptr;            // borrowed from the descriptor during creation
@@ -170,6 +171,14 @@ sais_status build_host(const sais_problem_desc *d, HostInst &h) {
         }
         h.D[i] = (float)(h.psg2 * (double)s2);
         h.asum[i] = (float)s1;
+    }
+    h.spinc.assign((size_t)h.npad * 4, 0.f);
+    for (int32_t i = 0; i < nprime; ++i) {
+        int32_t a0 = m > 0 ? h.acol[(size_t)i * m] : 0, a1 = m > 1 ? h.acol[(size_t)i * m + 1] : 0;
+        std::memcpy(&h.spinc[(size_t)i * 4 + 0], &a0, 4);
+        h.spinc[(size_t)i * 4 + 1] = h.D[i];
+        h.spinc[(size_t)i * 4 + 2] = h.asum[i];
+        std::memcpy(&h.spinc[(size_t)i * 4 + 3], &a1, 4);
     }
     h.hF.assign(h.npad, 0.f);
     for (int32_t i = 0; i < n; ++i) h.hF[i] = (float)d->h[i];
@@ -285,7 +294,7 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
     // Pool layout: [InstDev x count] then per instance W, Wbf(, Wbf_lo), hF, acol, D, asum, b,
     // slack_off, each 256-byte aligned.
     struct Off {
-        size_t W, Wbf, Wlo, hF, acol, D, asum, b, so;
+        size_t W, Wbf, Wlo, hF, acol, D, asum, spinc, b, so;
     };
     std::vector<Off> off(count);
     size_t cur = align_up(sizeof(InstDev) * count, 256);
@@ -314,6 +323,8 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
         cur = align_up(cur + h.D.size() * 4, 256);
         o.asum = cur;
         cur = align_up(cur + h.asum.size() * 4, 256);
+        o.spinc = cur;
+        cur = align_up(cur + h.spinc.size() * 4, 256);
         o.b = cur;
         cur = align_up(cur + (size_t)std::max(h.m, 1) * 4, 256);
         o.so = cur;
@@ -376,12 +387,14 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
         std::memcpy(stage.data() + o.acol, h.acol.data(), h.acol.size() * 4);
         std::memcpy(stage.data() + o.D, h.D.data(), h.D.size() * 4);
         std::memcpy(stage.data() + o.asum, h.asum.data(), h.asum.size() * 4);
+        std::memcpy(stage.data() + o.spinc, h.spinc.data(), h.spinc.size() * 4);
         if (h.m) std::memcpy(stage.data() + o.b, h.b.data(), h.b.size() * 4);
         std::memcpy(stage.data() + o.so, h.slack_off.data(), h.slack_off.size() * 4);
         r.hF = reinterpret_cast<const float *>(base + o.hF);
         r.acol = reinterpret_cast<const int32_t *>(base + o.acol);
         r.D = reinterpret_cast<const float *>(base + o.D);
         r.asum = reinterpret_cast<const float *>(base + o.asum);
+        r.spinc = reinterpret_cast<const float4 *>(base + o.spinc);
         r.b = reinterpret_cast<const int32_t *>(base + o.b);
         r.slack_off = reinterpret_cast<const int32_t *>(base + o.so);
         recs[j] = r;
@@ -523,9 +536,15 @@ sais_status enqueue_sample(sais_problem *p, const sais_sample_params *prm, const
                         "blocked sampler: pair values above 256 need the BF16 hi/lo split, "
                         "not available in this build");
         if (k == 64) return fail(SAIS_EUNSUPPORTED, "blocked sampler: block_k = 64 not available");
-        if (p->max_npad > 512)
-            return fail(SAIS_EUNSUPPORTED, "blocked sampler: N'=%d exceeds 512 TMEM columns",
-                        p->max_spins);
+        if (p->max_m > kMaxBlockedConstraints)
+            return fail(SAIS_EUNSUPPORTED,
+                        "blocked sampler: m = %d constraints (at most %d; use SAIS_PLAIN)",
+                        p->max_m, kMaxBlockedConstraints);
+        if (p->max_npad + k > 512)
+            return fail(SAIS_EUNSUPPORTED,
+                        "blocked sampler: N'=%d (padded %d) plus the %d operand columns exceed "
+                        "512 TMEM columns",
+                        p->max_spins, p->max_npad, k);
         const size_t smem = blocked_smem_bytes(p->max_npad, p->words, k);
         if (smem > kMaxSmemPerBlock)
             return fail(SAIS_EUNSUPPORTED,

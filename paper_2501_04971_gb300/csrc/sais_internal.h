@@ -13,6 +13,7 @@
 namespace sais {
 
 constexpr int kMaxConstraints = 32;    // m <= 32: per-chain constraint state lives in registers
+constexpr int kMaxBlockedConstraints = 8;   // the blocked sampler keeps 8 at most in registers
 constexpr int kSpinPad = 64;           // N' is padded to a multiple of 64 spins
 constexpr int kMaxPlainSmem = 220 * 1024;
 
@@ -35,6 +36,7 @@ struct InstDev {
     const int32_t *acol;   // npad x m, spin-major: a_ki of A_ext (zero past N')
     const float *D;        // npad: fl(P sigma_g^2 sum_k a_ki^2) (zero past N')
     const float *asum;     // npad: sum_k a_ki, exact in FP32 (zero past N')
+    const float4 *spinc;   // npad: {a_0i (int bits), D_i, sum_k a_ki, a_1i (int bits)}
     const int32_t *b;      // m capacities
     const int32_t *slack_off;  // m+1: first slack spin of constraint k; [m] = N'
     // BF16 copy of W for the blocked sampler in its shared-memory image: column-chunk major,
