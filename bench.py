@@ -50,6 +50,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-gap", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--gap-instances", type=int, default=32)
+    ap.add_argument("--gap-iters", type=int, default=100)
+    ap.add_argument("--gap-eta", type=float, default=2000.0)
     return ap.parse_args()
 
 
@@ -175,6 +180,61 @@ class ClockSampler:
                 "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
                 if any(r[3].replace(".", "").isdigit() for r in rows) else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------------------
+# wall-clock to a 1 % gap (QKP N=300, d=0.5), blocked vs plain
+# ------------------------------------------------------------------------------------------
+
+def gap_measurement(a, sais, torch, variants):
+    """Best-known profit per instance = best feasible sample of blocked runs (4 seeds x
+    `gap_iters` iterations; uncertified).  Then, per variant, Algorithm 1
+    from lambda = 0 with a fresh seed, one iteration at a time through the C-ABI; the time to a
+    1 % gap of an instance is the device time (CUDA events) of the iterations until its best
+    feasible profit reaches 0.99 x best-known.  Both variants draw identical samples, so they
+    need the same number of iterations; their times differ by the per-iteration cost."""
+    from paper_2501_04971_gb300 import workloads as wl
+    insts = [wl.qkp(300, 0.5, 5000 + i) for i in range(a.gap_instances)]
+    prob = sais.Problem(insts)
+    C, T, beta, eta = a.chains, a.sweeps, a.beta_max, a.gap_eta
+    best_known = np.full(prob.count, np.iinfo(np.int64).max, np.int64)
+    ref_variant = variants[0]
+    for seed in range(4):
+        r = prob.solve(a.gap_iters, C, T, beta, eta, 777 + seed, variant=ref_variant)
+        best_known = np.minimum(best_known, r["best_cost"])
+    out = {"instances": prob.count, "workload": "QKP N=300 d=0.5, %d chains x %d sweeps per "
+           "iteration, beta_max %g, P = 2dN, eta %g (normalised units)" % (C, T, beta, eta),
+           "best_known": "best of 4 seeds x %d iterations (blocked), uncertified" % a.gap_iters}
+    stream = torch.cuda.current_stream()
+    for v in variants:
+        lam = torch.zeros(prob.count * prob.m_stride, device="cuda")
+        o = prob.alloc_outputs(C)
+        best = prob.alloc_best()
+        reached = np.full(prob.count, np.nan)
+        t_acc = 0.0
+        for k in range(a.gap_iters):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            prob.sample(lam, C, T, beta, 4242, k, variant=v, out=o, stream=stream)
+            prob.track_best(o, C, k, best, stream=stream)
+            prob.update_lambda(o["g"], C, eta, True, lam, stream=stream)
+            e1.record(stream)
+            bc = best["best_cost"].cpu().numpy()     # synchronises
+            t_acc += e0.elapsed_time(e1) / 1e3
+            # costs are negative profits: reach when -bc >= 0.99 * (-best_known)
+            hit = (bc != np.iinfo(np.int64).max) & (-bc >= 0.99 * (-best_known))
+            reached[np.isnan(reached) & hit] = t_acc
+            if not np.isnan(reached).any():
+                break
+        ok = ~np.isnan(reached)
+        out[v] = {"reached": int(ok.sum()),
+                  "median_s": float(np.median(reached[ok])) if ok.any() else None,
+                  "p90_s": float(np.percentile(reached[ok], 90)) if ok.any() else None,
+                  "iterations_run": k + 1}
+    if all(out.get(v, {}).get("median_s") for v in ("blocked", "plain")):
+        out["speedup_median"] = out["plain"]["median_s"] / out["blocked"]["median_s"]
+    prob.close()
+    return out
 
 
 # ------------------------------------------------------------------------------------------
@@ -318,6 +378,30 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "api": "sais_solve(iters=1), pinned host lambda0 and results"}
 
+    plain_cmp = None
+    if variant == "blocked" and not a.no_plain:
+        # the same workload on the plain sampler: identical samples, per-step time only
+        for k in range(1):
+            prob.sample(lam, a.chains, a.sweeps, a.beta_max, 1234, k, variant="plain", out=out,
+                        stream=stream)
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        np_steps = max(1, min(2, a.steps))
+        p0.record(stream)
+        for k in range(np_steps):
+            prob.sample(lam, a.chains, a.sweeps, a.beta_max, 1234, k, variant="plain", out=out,
+                        stream=stream)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        pms = p0.elapsed_time(p1) / np_steps
+        plain_cmp = {"value": upd_step * world / (pms / 1e3), "unit": UNIT,
+                     "sampler_ms_per_step": pms,
+                     "blocked_over_plain": (upd_step * world / (pms / 1e3)) and
+                     value / (upd_step * world / (pms / 1e3))}
+    gap = None
+    if not a.no_gap and world == 1:
+        gap = gap_measurement(a, sais, torch, ["blocked", "plain"] if variant == "blocked"
+                              else ["plain"])
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -338,7 +422,7 @@ def main():
                              f"{prob.count * 2 * 2 * 320 * 320 / 1e6:.0f} MB)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": 3 * a.steps, "clocks": clk.summary(),
-            "updates_per_step": upd_step}
+            "updates_per_step": upd_step, "plain": plain_cmp, "gap_1pct": gap}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
