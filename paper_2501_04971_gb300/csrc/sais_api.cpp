@@ -297,6 +297,11 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
         size_t W, Wbf, Wlo, hF, acol, D, asum, spinc, b, so;
     };
     std::vector<Off> off(count);
+    // In a batch with any pair value above 256 every instance gets a lo image (zero where the
+    // hi term is already exact), since one launch serves the whole batch.
+    if (p->any_lo)
+        for (HostInst &h : p->host)
+            if (h.has_w) h.need_lo = true;
     size_t cur = align_up(sizeof(InstDev) * count, 256);
     const size_t status_off = cur;
     cur = align_up(cur + 4, 256);
@@ -531,10 +536,6 @@ sais_status enqueue_sample(sais_problem *p, const sais_sample_params *prm, const
             return fail(SAIS_EUNSUPPORTED,
                         "blocked sampler: every instance needs a quadratic objective W "
                         "(linear objectives have no dense field to update; use SAIS_PLAIN)");
-        if (p->any_lo)
-            return fail(SAIS_EUNSUPPORTED,
-                        "blocked sampler: pair values above 256 need the BF16 hi/lo split, "
-                        "not available in this build");
         if (k == 64) return fail(SAIS_EUNSUPPORTED, "blocked sampler: block_k = 64 not available");
         if (p->max_m > kMaxBlockedConstraints)
             return fail(SAIS_EUNSUPPORTED,
@@ -545,13 +546,22 @@ sais_status enqueue_sample(sais_problem *p, const sais_sample_params *prm, const
                         "blocked sampler: N'=%d (padded %d) plus the %d operand columns exceed "
                         "512 TMEM columns",
                         p->max_spins, p->max_npad, k);
-        const size_t smem = blocked_smem_bytes(p->max_npad, p->words, k);
+        // W resident in shared memory when it fits and needs one BF16 term; otherwise its
+        // per-block tiles are streamed (and pair values above 256 use the hi/lo split).
+        const bool hilo = p->any_lo;
+        bool stream_w = hilo ||
+                        blocked_smem_bytes(p->max_npad, p->words, k, false, false) > kMaxSmemPerBlock;
+        if (stream_w && k != 16)
+            return fail(SAIS_EUNSUPPORTED,
+                        "blocked sampler: streamed W (N'=%d%s) runs with block_k = 16 only",
+                        p->max_spins, hilo ? ", pair values above 256" : "");
+        const size_t smem = blocked_smem_bytes(p->max_npad, p->words, k, stream_w, hilo);
         if (smem > kMaxSmemPerBlock)
             return fail(SAIS_EUNSUPPORTED,
                         "blocked sampler: N'=%d needs %zu bytes of shared memory (max %zu)",
                         p->max_spins, smem, kMaxSmemPerBlock);
-        e = launch_blocked_sampler(a, p->max_m, p->max_npad, p->words, k, p->d_status,
-                                   (long long)prm->debug_wait_polls, st);
+        e = launch_blocked_sampler(a, p->max_m, p->max_npad, p->words, k, stream_w, hilo,
+                                   p->d_status, (long long)prm->debug_wait_polls, st);
     } else {
         int cpb = 0;
         sais_status s = plain_cpb(p, prm->chains_per_cta, &cpb);

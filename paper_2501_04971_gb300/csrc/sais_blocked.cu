@@ -1,585 +1,35 @@
-// sais_blocked.cu -- blocked p-bit sampler with the rank-k field update on the tensor cores.
-//
-// The Gibbs sweep of Sec. III-B stays sequential: spins are visited in index order and each
-// decision sees every earlier flip.  What changes is how the objective field
-// F_i = h_i + sum_j W_ij x_j follows the flips.  Spins are taken in blocks of K:
-//   1. the K decisions of a block are made one after the other on CUDA cores, each flip
-//      correcting the F values of the block's later spins (W[blk, blk], k(k-1)/2 products);
-//   2. the block's flips Delta (values -1, 0, +1) then update every field at once,
-//      F[:, chains] += W[:, blk] Delta[blk, chains], a dense GEMM of N'_pad x K x 128 done by
-//      tcgen05.mma in BF16 with FP32 accumulation.  The products and partial sums are
-//      integers below 2^24, so the result is exact and equal to the per-flip updates of the
-//      plain sampler: both samplers make identical decisions.
-//
-// Layout (one CTA = 128 chains of one instance; 1 CTA per SM):
-//   TMEM   F transposed, lane = chain (MMA row M = 128), column = spin (N = N'_pad), FP32.
-//   TMEM   also the MMA's A operand Delta (double buffered, K/2 columns each after F): row =
-//          chain, two BF16 values per 32-bit column, written by the chain's thread.
-//   SMEM   W as BF16 in the no-swizzle core-matrix layout, column-chunk major:
-//          element (j, s) at ((s/8) N'_pad + j) * 16 + (s%8) * 2 bytes, so the K columns of one
-//          block form a contiguous K-major operand (LBO = 16 N'_pad, SBO = 128); loaded once
-//          per launch by bulk asynchronous copies (TMA engine).  A two-slot ring of noise.
-//   Warps  0-3 decide (warp w owns TMEM lanes 32w..32w+31, i.e. its 32 chains); the last of
-//          them to finish a block issues the block's MMAs.  Warps 4-7 compute the noise (Philox,
-//          atanh) up to two blocks ahead for decision warps 0-3, so that every SM
-//          sub-partition has a second warp to issue from while its decision warp waits on a
-//          dependency; lane 0 of warp 4 also stages W by bulk copies.  Every mbarrier wait is bounded: on expiry the kernel
-//          records SAIS_ETIMEOUT, stops, drains its copies and MMAs, frees TMEM and exits.
-#include "sais_device.cuh"
-#include "sais_tc.cuh"
+// sais_blocked.cu -- launch of the blocked p-bit sampler (kernel in sais_blocked_kernel.cuh):
+// shared-memory size, TMEM columns, and the variants with W resident in shared memory.  The
+// variants that stream W tiles are instantiated in sais_blocked_stream.cu.
+#include "sais_blocked_kernel.cuh"
 
 namespace sais {
-namespace {
 
-constexpr int kLanes = 128;
-constexpr int kIssueThread = 128;
-constexpr int kThreadsBlocked = 256;   // 4 decision warps, 4 noise warps
-constexpr int kNoiseWarp0 = 4;
-// Every wait of this kernel is for an event microseconds away (an MMA, a block of decisions,
-// a 200 KB copy).  A wait gives up after kWaitCycles SM clock cycles (about 4 s at 2 GHz;
-// longer if the clock runs slower), or after `polls` polls when a test asks for a poll bound
-// (polls > 0).  The SM cycle counter is a cheap register read, unlike the global timer.
-constexpr long long kWaitCycles = 8000000000ll;
+cudaError_t launch_blocked_stream(const SampleArgs &a, int max_m, bool hilo, int32_t *status,
+                                  long long polls, size_t smem, uint32_t cols, cudaStream_t st);
 
-__device__ __forceinline__ unsigned long long sm_cycles() {
-    return (unsigned long long)clock64();
-}
-
-__device__ __forceinline__ bool wait_expired(long long n, long long polls,
-                                             unsigned long long t0) {
-    return polls > 0 ? n >= polls : (long long)(sm_cycles() - t0) > kWaitCycles;
-}
-
-// The clock is read only once a first poll has failed: most waits find their phase complete.
-__device__ __forceinline__ bool wait_bounded(uint64_t *bar, uint32_t parity,
-                                             volatile int *abort_flag, int32_t *status,
-                                             long long polls) {
-    if (tc::mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = sm_cycles();
-    for (long long n = 0;; ++n) {
-        if (tc::mbar_try_wait(bar, parity)) return true;
-        if (abort_flag && *abort_flag) return false;
-        if (wait_expired(n, polls, t0)) {
-            if (abort_flag) *abort_flag = 1;
-            if (status) atomicExch(status, (int32_t)SAIS_ETIMEOUT);
-            return false;
-        }
-    }
-}
-
-// Warp-collective bounded wait: every lane polls and the warp leaves together, either when all
-// lanes have observed the phase or when any lane sees the abort flag or the poll limit.
-__device__ __forceinline__ bool wait_bounded_warp(uint64_t *bar, uint32_t parity,
-                                                  volatile int *abort_flag, int32_t *status,
-                                                  long long polls) {
-    if (__all_sync(0xffffffffu, tc::mbar_try_wait(bar, parity))) return true;
-    const unsigned long long t0 = sm_cycles();
-    for (long long n = 0;; ++n) {
-        const bool got = tc::mbar_try_wait(bar, parity);
-        if (__all_sync(0xffffffffu, got)) return true;
-        const bool give_up = *abort_flag != 0 || wait_expired(n, polls, t0);
-        if (__any_sync(0xffffffffu, give_up)) {
-            if ((threadIdx.x & 31) == 0 && !*abort_flag) {
-                *abort_flag = 1;
-                if (status) atomicExch(status, (int32_t)SAIS_ETIMEOUT);
-            }
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ uint32_t bf16_pm1(int d) {
-    return d > 0 ? 0x3F80u : (d < 0 ? 0xBF80u : 0u);
-}
-
-template <int K>
-__device__ __forceinline__ void load_block_fields(uint32_t taddr, float (&Fr)[K]) {
-    if constexpr (K == 32) {
-        tc::tmem_ld32(taddr, Fr);
-    } else {
-        tc::tmem_ld16(taddr, Fr);
-    }
-}
-
-template <int MC, int K>
-__global__ void __launch_bounds__(kThreadsBlocked, 1)
-    blocked_sampler_kernel(SampleArgs a, int32_t *status, long long dec_wait_polls,
-                           uint32_t tmem_cols) {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    constexpr int kPreM = MC < 2 ? MC : 2;   // constraint columns in the per-spin record
-    const int j = blockIdx.y;
-    const InstDev *__restrict__ ip = a.inst + j;
-    const int m = ip->m, nprime = ip->nprime, npad = ip->npad, words = ip->words;
-    const int nb = (nprime + K - 1) / K;
-    const uint32_t wbytes = (uint32_t)npad * (uint32_t)npad * 2u;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-    unsigned char *Wsm = smem;
-    uint32_t *xs = reinterpret_cast<uint32_t *>(smem + wbytes);
-    float *thbuf = reinterpret_cast<float *>(xs + words * kLanes);   // [2][K][128] noise ring
-    uint64_t *bars = reinterpret_cast<uint64_t *>(thbuf + 2 * K * kLanes);
-    // bars: 0 = W staged, 1 = never completed (fault-injection test of the timeout path),
-    // 2 = the block's MMAs done, 3..6 = drain of decision warp 0..3,
-    // 7..14 = noise slot written (2 q + slot), 15..22 = noise slot consumed (2 q + slot)
-    uint32_t *arrivals = reinterpret_cast<uint32_t *>(bars + 23);   // [2] decision warps done
-    uint32_t *tmem_slot = arrivals + 2;
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-
-    if (threadIdx.x == kIssueThread) {
-        for (int i = 0; i < 23; ++i) tc::mbar_init(&bars[i], 1);
-        arrivals[0] = arrivals[1] = 0u;
-        *abort_flag = 0;
-        tc::fence_mbar_init();
-        tc::fence_proxy_async_smem();
-    }
-    if (warp == 0) {
-        tc::tmem_alloc(tmem_slot, tmem_cols);
-        tc::tmem_relinquish();
-    }
-    tc::tc_fence_before();
-    __syncthreads();
-    tc::tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
-    const uint32_t iter = a.iter_dev ? *a.iter_dev : a.iter;
-
-    if (warp >= kNoiseWarp0) {
-        // Noise warps: warp 4+q produces theta = atanh(rho) for the chains of decision warp q,
-        // up to two blocks ahead, into a two-slot ring.  Lane 0 of warp 4 stages W.
-        const int q = warp - kNoiseWarp0;
-        const int r = q * 32 + lane;
-        const uint32_t chain = (uint32_t)(blockIdx.x * kLanes + r);
-        const uint64_t seed = a.seed + (uint64_t)j;
-        const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
-        const uint32_t total = (uint32_t)a.sweeps * (uint32_t)nb;
-        if (q == 0 && lane == 0) {
-            tc::mbar_expect_tx(&bars[0], wbytes);
-            const unsigned char *src = reinterpret_cast<const unsigned char *>(ip->Wbf);
-            for (uint32_t off = 0; off < wbytes; off += 32768u)
-                tc::bulk_g2s(Wsm + off, src + off, min(32768u, wbytes - off), &bars[0]);
-        }
-        for (uint32_t it = 0; it < total; ++it) {
-            const uint32_t slot = it & 1u;
-            if (it >= 2 && !wait_bounded_warp(&bars[15 + 2 * q + slot], ((it >> 1) + 1u) & 1u,
-                                              abort_flag, status, 0))
-                break;
-            const uint32_t t = it / (uint32_t)nb;
-            const int s0 = (int)(it % (uint32_t)nb) * K;
-            float *tb = thbuf + slot * K * kLanes;
-#pragma unroll
-            for (int g4 = 0; g4 < K / 4; ++g4) {
-                const uint4 rw = philox4x32_10(
-                    make_uint4((uint32_t)((s0 >> 2) + g4), t, chain, iter), key0, key1);
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    // Spins past N' (block padding) get a threshold that keeps them at 0.
-                    const bool real = s0 + 4 * g4 + e < nprime;
-                    tb[(4 * g4 + e) * kLanes + r] = real ? theta_of_word(word_of(rw, e)) : -1e30f;
-                }
-            }
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&bars[7 + 2 * q + slot]);
-        }
-        // The staging copies complete before shared memory is released.
-        if (q == 0 && lane == 0) wait_bounded(&bars[0], 0, nullptr, status, 0);
-        __syncwarp();
-    } else {
-        const int r = threadIdx.x;
-        const int chain = blockIdx.x * kLanes + r;
-        const bool valid = chain < a.chains;
-        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-        const uint64_t seed = a.seed + (uint64_t)j;
-        const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
-        const float sf = ip->sigma_f, sg = ip->sigma_g, kappa = ip->kappa;
-        const double psg2 = ip->psg2;
-        const float *__restrict__ hF = ip->hF;
-        const int32_t *__restrict__ acol = ip->acol;
-        const float *__restrict__ Dv = ip->D;
-        const float *__restrict__ asum = ip->asum;
-        const float *lam = a.lambda + (size_t)j * a.m_stride;
-
-        // x = 0 and F = h (Sec. III-B: every run starts from x = 0).
-        for (int w = 0; w < words; ++w) xs[w * kLanes + r] = 0u;
-        for (int c0 = 0; c0 < npad; c0 += 32) {
-            float v[32];
-#pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = __ldg(hF + c0 + i);
-            tc::tmem_st32(lane_addr + (uint32_t)c0, v);
-        }
-        tc::tc_fence_before();
-
-        int32_t g[MC];
-        float c[MC], cA[MC];
-        float Mmax = 0.f;
-#pragma unroll
-        for (int k = 0; k < MC; ++k) {
-            if (k < m) {
-                cA[k] = __double2float_rn((double)sg * (double)lam[k]);
-                g[k] = -ip->b[k];
-                c[k] = fmaf(kappa, (float)g[k], cA[k]);
-                Mmax = fmaxf(Mmax, fmaf(fabsf(kappa), fabsf((float)g[k]), fabsf(cA[k])));
-            } else {
-                cA[k] = 0.f;
-                g[k] = 0;
-                c[k] = 0.f;
-            }
-        }
-        const float errk = field_err_factor(m);
-        // Fault-injection test (dec_wait_polls > 0): wait on a barrier nothing completes, so the
-        // bound expires and the kernel takes its timeout path.
-        bool ok = dec_wait_polls > 0
-                      ? wait_bounded_warp(&bars[1], 0, abort_flag, status, dec_wait_polls)
-                      : true;
-        if (ok) ok = wait_bounded_warp(&bars[0], 0, abort_flag, status, 0);
-        uint32_t it = 0;
-        float th[K];
-        for (int t = 0; ok && t < a.sweeps; ++t) {
-            const float beta = beta_of_sweep(a.beta_max, t, a.sweeps);
-            const float hb = 0.5f * beta;
-            const float ez = hb * errk;
-            for (int b = 0; b < nb; ++b) {
-                const int s0 = b * K;
-                // Noise of the block, written by this warp's partner noise warp.
-                const uint32_t slot = it & 1u;
-                if (!wait_bounded_warp(&bars[7 + 2 * warp + slot], (it >> 1) & 1u, abort_flag,
-                                       status, dec_wait_polls)) {
-                    ok = false;
-                    break;
-                }
-#pragma unroll
-                for (int ii = 0; ii < K; ++ii) th[ii] = thbuf[(slot * K + ii) * kLanes + r];
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&bars[15 + 2 * warp + slot]);
-                // Per-spin constants of the block, loaded together before the sequential loop
-                // and before the wait for the previous block's MMAs, which they overlap
-                // (spins past N' read the zero padding of the arrays).
-                float Dp[K], Sp[K];
-                int32_t Ap[K][kPreM];
-#pragma unroll
-                for (int ii = 0; ii < K; ++ii) {
-                    const float4 sc = __ldg(ip->spinc + s0 + ii);
-                    Ap[ii][0] = __float_as_int(sc.x);
-                    Dp[ii] = sc.y;
-                    Sp[ii] = sc.z;
-                    if (kPreM > 1) Ap[ii][kPreM > 1 ? 1 : 0] = __float_as_int(sc.w);
-                }
-                if (it > 0) {
-                    if (!wait_bounded_warp(&bars[2], (it - 1u) & 1u, abort_flag, status,
-                                           dec_wait_polls)) {
-                        ok = false;
-                        break;
-                    }
-                    tc::tc_fence_after();
-                }
-                float Fr[K];
-                load_block_fields<K>(lane_addr + (uint32_t)s0, Fr);
-                const int wi = s0 >> 5, sb = s0 & 31;
-                uint32_t xw = xs[wi * kLanes + r];
-                const uint32_t xold = xw;
-                // Block-start chain state, kept for an exact re-run of the block.
-                int32_t g0[MC];
-                float cb[MC];
-                const float M0 = Mmax;
-#pragma unroll
-                for (int k = 0; k < MC; ++k) {
-                    g0[k] = g[k];
-                    cb[k] = c[k];
-                }
-                bool near_tie = false;
-#pragma unroll
-                for (int ii = 0; ii < K; ++ii) {
-                    const int s = s0 + ii;
-                    // Row s of the block's W columns (only the part right of spin ii is used):
-                    // loaded ahead of the decision so that it is ready if any chain flips.
-                    uint4 wrow[K / 8];
-#pragma unroll
-                    for (int cc = (ii + 1) >> 3; cc < K / 8; ++cc)
-                        wrow[cc] = *reinterpret_cast<const uint4 *>(
-                            Wsm + ((size_t)((s0 >> 3) + cc) * npad + s) * 16);
-                    {
-                        const float Fi = Fr[ii];
-                        const int xi = (xw >> (sb + ii)) & 1;
-                        int32_t ak[MC];
-                        float acc = sf * Fi;
-                        const float tabs = fabsf(acc);
-#pragma unroll
-                        for (int k = 0; k < MC; ++k) {
-                            if (k < kPreM)
-                                ak[k] = Ap[ii][k < kPreM ? k : 0];
-                            else
-                                ak[k] = (k < m) ? __ldg(acol + (size_t)s * m + k) : 0;
-                            acc = fmaf(-(float)ak[k], c[k], acc);
-                        }
-                        const float Di = Dp[ii];
-                        acc = fmaf(xi ? 1.f : -1.f, Di, acc);
-                        const float z = hb * acc;
-                        const float theta = th[ii];
-                        const float y = z + theta;
-                        const float bound = ez * (tabs + Sp[ii] * Mmax + Di) +
-                                            kThetaRelErr * fabsf(theta) + kThetaAbsErr;
-                        // A decision the FP32 bound cannot settle is only flagged here; the
-                        // warp then re-runs the block below with the FP64 path.
-                        const int xn = y > 0.f;
-                        near_tie |= !(fabsf(y) > bound);
-                        const int d = xn - xi;
-                        // Constraint state follows the flip without a branch (d = 0 leaves every
-                        // value bit-identical).
-                        xw ^= (uint32_t)(d != 0) << (sb + ii);
-                        Mmax = 0.f;
-#pragma unroll
-                        for (int k = 0; k < MC; ++k) {
-                            if (k < m) {
-                                g[k] += ak[k] * d;
-                                c[k] = fmaf(kappa, (float)g[k], cA[k]);
-                                Mmax = fmaxf(Mmax, fmaf(fabsf(kappa), fabsf((float)g[k]),
-                                                        fabsf(cA[k])));
-                            }
-                        }
-                        if (ii + 1 < K && __any_sync(0xffffffffu, d != 0)) {
-                            // In-block correction F_jj += W[s, s0+jj] d for the block's later
-                            // spins; row s of the block's W columns is contiguous per 8 columns.
-                            const float df = (float)d;
-#pragma unroll
-                            for (int cc = (ii + 1) >> 3; cc < K / 8; ++cc) {
-                                const uint4 w4 = wrow[cc];
-                                const uint32_t wv[4] = {w4.x, w4.y, w4.z, w4.w};
-#pragma unroll
-                                for (int e = 0; e < 8; ++e) {
-                                    const int jj = cc * 8 + e;
-                                    if (jj > ii) {
-                                        const uint32_t bits = (e & 1) ? (wv[e >> 1] & 0xFFFF0000u)
-                                                                      : (wv[e >> 1] << 16);
-                                        Fr[jj] = fmaf(df, __uint_as_float(bits), Fr[jj]);
-                                    }
-                                }
-                            }
-                        }
-                    }
-                }
-                if (__any_sync(0xffffffffu, near_tie)) {
-                    // Exact re-run of the block for the whole warp, from its start state: F from
-                    // TMEM (this block's MMA is not issued yet) plus the block's earlier flips, the
-                    // noise recomputed, the same FP32 evaluation, and FP64 where the bound cannot
-                    // settle the decision.  Decisions outside near-ties come out as before.
-                    xw = xold;
-                    Mmax = M0;
-#pragma unroll
-                    for (int k = 0; k < MC; ++k) {
-                        g[k] = g0[k];
-                        c[k] = cb[k];
-                    }
-#pragma unroll 1
-                    for (int ii = 0; ii < K; ++ii) {
-                        const int s = s0 + ii;
-                        uint32_t fv;
-                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
-                                     : "=r"(fv)
-                                     : "r"(lane_addr + (uint32_t)s));
-                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                        float Fi = __uint_as_float(fv);
-                        uint32_t fl = ((xw ^ xold) >> sb) & ((1u << ii) - 1u);
-                        while (fl) {
-                            const int i2 = __ffs(fl) - 1;
-                            fl &= fl - 1u;
-                            const int d2 = (int)((xw >> (sb + i2)) & 1u) -
-                                           (int)((xold >> (sb + i2)) & 1u);
-                            const int s2 = s0 + i2;
-                            const uint16_t wb = *reinterpret_cast<const uint16_t *>(
-                                Wsm + ((size_t)(s2 >> 3) * npad + s) * 16 + (s2 & 7) * 2);
-                            Fi = fmaf((float)d2, __uint_as_float((uint32_t)wb << 16), Fi);
-                        }
-                        const int xi = (xw >> (sb + ii)) & 1;
-                        int32_t ak[MC];
-                        float acc = sf * Fi;
-                        const float tabs = fabsf(acc);
-#pragma unroll
-                        for (int k = 0; k < MC; ++k) {
-                            ak[k] = (k < m) ? __ldg(acol + (size_t)s * m + k) : 0;
-                            acc = fmaf(-(float)ak[k], c[k], acc);
-                        }
-                        const float Di = __ldg(Dv + s);
-                        acc = fmaf(xi ? 1.f : -1.f, Di, acc);
-                        const float z = hb * acc;
-                        const uint4 rw = philox4x32_10(
-                            make_uint4((uint32_t)(s >> 2), (uint32_t)t, (uint32_t)chain, iter),
-                            key0, key1);
-                        const float theta =
-                            s < nprime ? theta_of_word(word_of(rw, s & 3)) : -1e30f;
-                        const float y = z + theta;
-                        const float bound = ez * (tabs + __ldg(asum + s) * Mmax + Di) +
-                                            kThetaRelErr * fabsf(theta) + kThetaAbsErr;
-                        int xn = y > 0.f;
-                        if (!(fabsf(y) > bound)) {
-                            const float rho = rho_of_word(word_of(rw, s & 3));
-                            xn = decide_exact<MC>(Fi, xi, ak, g, lam, m, sf, sg, psg2, beta, rho);
-                        }
-                        const int d = xn - xi;
-                        xw ^= (uint32_t)(d != 0) << (sb + ii);
-                        Mmax = 0.f;
-#pragma unroll
-                        for (int k = 0; k < MC; ++k) {
-                            if (k < m) {
-                                g[k] += ak[k] * d;
-                                c[k] = fmaf(kappa, (float)g[k], cA[k]);
-                                Mmax = fmaxf(Mmax, fmaf(fabsf(kappa), fabsf((float)g[k]),
-                                                        fabsf(cA[k])));
-                            }
-                        }
-                    }
-                }
-                xs[wi * kLanes + r] = xw;
-                // Delta of the block (BF16 -1, 0, +1) into this chain's TMEM row of the MMA's A
-                // operand (columns N'_pad + slot K/2 ..); the last decision warp to finish the
-                // block issues its MMAs: F[:, chains] += W[:, blk] Delta[blk, chains].
-                {
-                    const uint32_t a_col = (uint32_t)npad + (it & 1u) * (uint32_t)(K / 2);
-                    uint32_t pk[K / 2];
-#pragma unroll
-                    for (int e2 = 0; e2 < K / 2; ++e2) {
-                        const int i0 = sb + 2 * e2;
-                        const int d0 = (int)((xw >> i0) & 1u) - (int)((xold >> i0) & 1u);
-                        const int d1 = (int)((xw >> (i0 + 1)) & 1u) - (int)((xold >> (i0 + 1)) & 1u);
-                        pk[e2] = bf16_pm1(d0) | (bf16_pm1(d1) << 16);
-                    }
-#pragma unroll
-                    for (int h8 = 0; h8 < K / 16; ++h8) {
-                        uint32_t v8[8];
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) v8[e] = pk[8 * h8 + e];
-                        tc::tmem_st8(lane_addr + a_col + 8u * (uint32_t)h8, v8);
-                    }
-                    tc::tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) {
-                        __threadfence_block();
-                        const bool last = (atomicAdd(&arrivals[it & 1u], 1u) & 3u) == 3u;
-                        if (last) {
-                            __threadfence_block();
-                            tc::tc_fence_after();
-                            const uint32_t lbo_b = (uint32_t)npad * 16u;
-                            const uint32_t w_base =
-                                tc::smem_u32(Wsm) + (uint32_t)(s0 >> 3) * lbo_b;
-#pragma unroll
-                            for (int ks = 0; ks < K / 16; ++ks) {
-                                for (int j0 = 0; j0 < npad; j0 += 256) {
-                                    const int nr = min(256, npad - j0);
-                                    const uint64_t bd = tc::smem_desc(
-                                        w_base + (uint32_t)ks * 2u * lbo_b + (uint32_t)j0 * 16u,
-                                        lbo_b, 128u);
-                                    tc::mma_bf16_tmem_a(tmem + (uint32_t)j0,
-                                                        tmem + a_col + 8u * (uint32_t)ks, bd,
-                                                        tc::idesc_bf16_f32(128, (uint32_t)nr), 1u);
-                                }
-                            }
-                            tc::mma_commit(&bars[2]);
-                        }
-                    }
-                    __syncwarp();
-                }
-                ++it;
-            }
-            if (ok && a.trace && valid) {
-                uint32_t *tr = a.trace + (((size_t)j * a.chains + chain) * a.sweeps + t) * a.words;
-                for (int w = 0; w < a.words; ++w) tr[w] = w < words ? xs[w * kLanes + r] : 0u;
-            }
-        }
-        if (ok && it > 0) {
-            ok = wait_bounded_warp(&bars[2], (it - 1u) & 1u, abort_flag, status, dec_wait_polls);
-            tc::tc_fence_after();
-        }
-        if (ok) {
-            // Readout of the last sample: cost -(sum_i x_i F_i + h^T x)/2, g, feasibility.  The
-            // TMEM loads are warp-collective, so every lane takes part; only valid chains store.
-            long long sumF = 0, sumh = 0;
-            for (int c0 = 0; c0 < npad; c0 += 32) {
-                float v[32];
-                tc::tmem_ld32(lane_addr + (uint32_t)c0, v);
-                const uint32_t bits = c0 < words * 32 ? xs[(c0 >> 5) * kLanes + r] : 0u;
-#pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    if ((bits >> i) & 1u) {
-                        sumF += (long long)v[i];
-                        sumh += (long long)__ldg(hF + c0 + i);
-                    }
-                }
-            }
-            if (valid) {
-                const size_t cidx = (size_t)j * a.chains + chain;
-                for (int w = 0; w < a.words; ++w)
-                    a.x[cidx * a.words + w] = w < words ? xs[w * kLanes + r] : 0u;
-                a.cost[cidx] = -(sumF + sumh) / 2;
-                bool feas = true;
-#pragma unroll
-                for (int k = 0; k < MC; ++k) {
-                    if (k < m) {
-                        const int o0 = ip->slack_off[k], o1 = ip->slack_off[k + 1];
-                        long long sv = 0;
-                        for (int s = o0; s < o1; ++s)
-                            if ((xs[(s >> 5) * kLanes + r] >> (s & 31)) & 1u) sv += 1LL << (s - o0);
-                        if ((long long)g[k] - sv > 0) feas = false;
-                        a.g[cidx * a.m_stride + k] = g[k];
-                    }
-                }
-                for (int k = m; k < a.m_stride; ++k) a.g[cidx * a.m_stride + k] = 0;
-                if (a.feasible) a.feasible[cidx] = feas ? 1 : 0;
-            }
-        }
-    }
-    if (warp < kNoiseWarp0 && lane == 0) {
-        // Drain: MMAs this thread issued complete before TMEM is released.
-        tc::mma_commit(&bars[3 + warp]);
-        wait_bounded(&bars[3 + warp], 0, nullptr, status, 0);
-    }
-    tc::tc_fence_before();
-    __syncthreads();
-    if (warp == 0) {
-        tc::tc_fence_after();
-        tc::tmem_dealloc(tmem, tmem_cols);
-    }
-}
-
-template <int MC, int K>
-cudaError_t launch_k(const SampleArgs &a, int32_t *status, long long polls, size_t smem,
-                     uint32_t cols, cudaStream_t s) {
-    auto kern = blocked_sampler_kernel<MC, K>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid((a.chains + kLanes - 1) / kLanes, a.count);
-    kern<<<grid, kThreadsBlocked, smem, s>>>(a, status, polls, cols);
-    return cudaGetLastError();
-}
-
-template <int K>
-cudaError_t launch_mc(const SampleArgs &a, int max_m, int32_t *status, long long polls,
-                      size_t smem, uint32_t cols, cudaStream_t s) {
-    if (max_m <= 1) return launch_k<1, K>(a, status, polls, smem, cols, s);
-    if (max_m <= 2) return launch_k<2, K>(a, status, polls, smem, cols, s);
-    if (max_m <= 4) return launch_k<4, K>(a, status, polls, smem, cols, s);
-    return launch_k<8, K>(a, status, polls, smem, cols, s);   // the host admits m <= 8
-}
-
-}  // namespace
-
-size_t blocked_smem_bytes(int max_npad, int max_words, int block_k) {
-    return (size_t)max_npad * max_npad * 2 + (size_t)max_words * kLanes * 4 +
-           (size_t)2 * block_k * kLanes * 4 + 23 * 8 + 16;
+size_t blocked_smem_bytes(int max_npad, int max_words, int block_k, bool stream, bool hilo) {
+    const size_t w = stream ? (size_t)3 * (hilo ? 2 : 1) * (block_k / 8) * max_npad * 16
+                            : (size_t)max_npad * max_npad * 2;
+    return w + (size_t)max_words * kLanes * 4 + (size_t)2 * block_k * kLanes * 4 + 29 * 8 + 16;
 }
 
 cudaError_t launch_blocked_sampler(const SampleArgs &a, int max_m, int max_npad, int max_words,
-                                   int block_k, int32_t *status, long long dec_wait_polls,
-                                   cudaStream_t stream) {
-    // TMEM columns: the power of two >= N'_pad (>= 32).  At most 512 / cols CTAs may share an
-    // SM, or a CTA's allocation would wait for another CTA's release; the shared-memory request
-    // is raised so that no more CTAs than that fit on one SM (228 KB per SM).
+                                   int block_k, bool stream, bool hilo, int32_t *status,
+                                   long long dec_wait_polls, cudaStream_t st) {
+    // TMEM columns: the power of two >= N'_pad + K (F, then the A operand).  At most 512 / cols
+    // CTAs may share an SM, or a CTA's allocation would wait for another CTA's release; the
+    // shared-memory request is raised so that no more CTAs than that fit on one SM.
     uint32_t cols = 32;
-    while (cols < (uint32_t)(max_npad + block_k)) cols <<= 1;   // F, then the A operand
+    while (cols < (uint32_t)(max_npad + block_k)) cols <<= 1;
     const size_t per_sm = 228 * 1024, max_ctas = 512 / cols;
-    size_t smem = blocked_smem_bytes(max_npad, max_words, block_k);
+    size_t smem = blocked_smem_bytes(max_npad, max_words, block_k, stream, hilo);
     const size_t floor_smem = per_sm / (max_ctas + 1) + 1;
     if (smem < floor_smem) smem = floor_smem;
     const long long polls = dec_wait_polls > 0 ? dec_wait_polls : 0;
-    if (block_k == 32) return launch_mc<32>(a, max_m, status, polls, smem, cols, stream);
-    return launch_mc<16>(a, max_m, status, polls, smem, cols, stream);
+    if (block_k == 32) return launch_mc<32, false, false>(a, max_m, status, polls, smem, cols, st);
+    if (!stream) return launch_mc<16, false, false>(a, max_m, status, polls, smem, cols, st);
+    return launch_blocked_stream(a, max_m, hilo, status, polls, smem, cols, st);
 }
 
 }  // namespace sais

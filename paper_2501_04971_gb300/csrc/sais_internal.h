@@ -98,9 +98,10 @@ struct PostArgs {
 cudaError_t launch_plain_sampler(const SampleArgs &a, int max_m, int max_npad, int max_words,
                                  int chains_per_cta, cudaStream_t stream);
 cudaError_t launch_blocked_sampler(const SampleArgs &a, int max_m, int max_npad,
-                                   int max_words, int block_k, int32_t *status,
-                                   long long dec_wait_polls, cudaStream_t stream);
-size_t blocked_smem_bytes(int max_npad, int max_words, int block_k);
+                                   int max_words, int block_k, bool stream_w, bool hilo,
+                                   int32_t *status, long long dec_wait_polls,
+                                   cudaStream_t stream);
+size_t blocked_smem_bytes(int max_npad, int max_words, int block_k, bool stream_w, bool hilo);
 size_t plain_smem_bytes(int max_npad, int max_words, bool any_w, int cpb);
 constexpr size_t kMaxSmemPerBlock = 232448;   // 227 KB opt-in per CTA on sm_103
 cudaError_t launch_post(const PostArgs &a, cudaStream_t stream);

@@ -129,8 +129,28 @@ def test_blocked_timeout_path_reports_and_recovers():
     prob.close()
 
 
+@pytest.mark.parametrize("case", ["hilo_n100", "hilo_n300", "stream_n400", "hilo_stream_mixed"])
+def test_blocked_streamed_and_hilo(case):
+    """W streamed through the shared-memory tile ring, and the BF16 hi/lo split for pair
+    values above 256 (profits up to 10^4): still identical to the plain sampler and the oracle."""
+    if case == "hilo_n100":
+        _compare([wl.qkp(100, 0.5, 21, profit_max=10000)], [[0.7]], C=128, T=150, beta=10.0,
+                 seed=9, it=1, block_k=16)
+    elif case == "hilo_n300":
+        _compare([wl.qkp(300, 0.75, 22, profit_max=10000)], [[1.5]], C=128, T=200, beta=10.0,
+                 seed=10, it=0, block_k=16, oracle_chains=(0, 2))
+    elif case == "stream_n400":
+        _compare([wl.qkp(400, 0.5, 23)], [[2.0]], C=128, T=120, beta=10.0, seed=11, it=2,
+                 block_k=16, oracle_chains=(0, 2))
+    else:
+        insts = [wl.qkp(150, 0.5, 24), wl.qkp(420, 0.25, 25, profit_max=5000),
+                 wl.qkp(60, 1.0, 26, profit_max=300)]
+        _compare(insts, [[0.2], [3.0], [0.9]], C=160, T=80, beta=10.0, seed=12, it=3,
+                 block_k=16, oracle_chains=(0, 3))
+
+
 def test_blocked_unsupported_cases():
-    for inst in (wl.mkp(40, 3, 1), wl.qkp(50, 0.5, 2, profit_max=1000)):
+    for inst in (wl.mkp(40, 3, 1), wl.qkp(600, 0.5, 2)):
         prob = sais.Problem(inst)
         lam = torch.zeros(prob.count * prob.m_stride, device="cuda:0")
         with pytest.raises(sais.SaisError) as e:
