@@ -108,8 +108,25 @@ typedef struct sais_layout {
 
 typedef enum sais_variant {
     SAIS_PLAIN = 0,          /* per-spin sampler: FP32 fields, rank-1 update on every flip  */
-    SAIS_BLOCKED = 1         /* k spins per block, rank-k field update on the tensor cores  */
+    SAIS_BLOCKED = 1,        /* k spins per block, rank-k field update on the tensor cores  */
+    SAIS_AUTO = 2            /* per launch group of the batch: the blocked sampler where an
+                                instance allows it (quadratic objective, m <= 8, N' <= 496),
+                                the plain sampler otherwise, or the choices sais_autotune
+                                made; ragged work lists, most expensive instances first      */
 } sais_variant;
+
+/* What sais_autotune chose for each launch group of SAIS_AUTO (first 8 groups). */
+typedef struct sais_tuning {
+    int32_t groups;                  /* launch groups of the batch                         */
+    int32_t blocked_instances;       /* instances now run by the blocked sampler           */
+    int32_t plain_instances;         /* instances now run by the plain sampler             */
+    int32_t reserved;
+    int32_t group_variant[8];        /* sais_variant chosen per group                      */
+    int32_t group_block_k[8];        /* block size (blocked groups)                        */
+    int32_t group_chains_per_cta[8]; /* chains per CTA                                     */
+    int32_t group_size[8];           /* instances per group                                */
+    double group_ms[8];              /* measured time of the chosen configuration          */
+} sais_tuning;
 
 /* One annealing run per chain (Sec. III-B): every chain starts at x = 0 and performs `sweeps`
  * sequential sweeps, sweep t at beta_t = beta_max t / (sweeps-1) (beta_max when sweeps = 1). */
@@ -261,6 +278,21 @@ SAIS_API sais_status sais_solve(sais_problem *p, const sais_solve_params *prm,
  * Errors: as sais_solve. */
 SAIS_API sais_status sais_solve_noalloc(sais_problem *p, const sais_solve_params *prm,
                                         sais_solve_result *res, void *stream);
+
+/* Ragged batches: counts[j] >= 1 chains for instance j (host array of `count` entries, copied);
+ * NULL restores one count for all.  While set, the `chains` argument of sais_sample,
+ * sais_update_lambda, sais_track_best and sais_solve is the row stride of per-chain arrays
+ * (>= every counts[j]); instance j uses its first counts[j] rows, and the multiplier step
+ * averages over them.  Errors: SAIS_EINVAL, SAIS_ENOMEM, SAIS_ECUDA. */
+SAIS_API sais_status sais_set_instance_chains(sais_problem *p, const int32_t *counts);
+
+/* Autotuner of SAIS_AUTO: for every launch group, times one launch of `sweeps` sweeps with
+ * `chains` chains for each candidate (blocked with block_k 16 / 32 where W allows it, plain with
+ * 32 / 64 / 128 chains per CTA) and keeps the fastest for later SAIS_AUTO launches.  Allocates
+ * and frees temporary device buffers; synchronises `stream`.  Errors: SAIS_EINVAL, SAIS_ENOMEM,
+ * SAIS_ECUDA. */
+SAIS_API sais_status sais_autotune(sais_problem *p, int32_t chains, int32_t sweeps,
+                                   sais_tuning *out, void *stream);
 
 /* Wait for the work queued on `stream` and report device-side failures of this problem's
  * kernels since the last call: SAIS_ETIMEOUT if a bounded wait inside a kernel gave up (the

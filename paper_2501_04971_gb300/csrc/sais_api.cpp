@@ -54,7 +54,8 @@ struct HostInst {
     float sf = 1.f, sg = 1.f, P = 0.f;
     double d = 0.0, psg2 = 0.0;
     float kappa = 0.f;
-    bool need_lo = false;                  // some |W| > 256: BF16 hi/lo split
+    bool need_lo = false;                  // lo image allocated (BF16 hi/lo split)
+    bool lo_own = false;                   // this instance has |W| > 256
     std::vector<int32_t> Q, slack_off;     // m, m+1
     std::vector<int32_t> acol;             // nprime x m (spin-major)
     std::vector<float> D, asum;            // npad
@@ -106,6 +107,7 @@ sais_status build_host(const sais_problem_desc *d, HostInst &h) {
                         (long long)row);
     }
     h.need_lo = max_w > 256;
+    h.lo_own = h.need_lo;
     int64_t maxabs_g = 0;
     h.Q.assign(m, 0);
     h.slack_off.assign(m + 1, 0);
@@ -215,7 +217,126 @@ struct sais_problem {
     void *pool = nullptr;         // one device allocation for all instance arrays
     InstDev *d_inst = nullptr;    // device array of count records (inside pool)
     int32_t *d_status = nullptr;  // device status word written by kernels (inside pool)
+
+    // Launch groups of SAIS_AUTO: instances the blocked sampler runs, grouped by how it holds W
+    // (resident, streamed, streamed hi/lo), and the rest on the plain sampler.  Members are kept
+    // most expensive first; each group runs over a slice of a device work list of (instance,
+    // chain group) pairs, so the block scheduler starts the longest work first.
+    struct Group {
+        int variant = SAIS_PLAIN;
+        bool stream_w = false, hilo = false;
+        int block_k = 16, cpb = 32;
+        int max_m = 0, max_npad = 0, max_npad_w = 0, words = 0;
+        bool any_w = false;
+        bool blocked_ok = false;   // every member fits the blocked sampler
+        std::vector<int> members;
+        size_t work_off = 0, nwork = 0;
+        double tuned_ms = 0.0;
+    };
+    std::vector<Group> groups;
+    std::vector<int32_t> inst_chains;   // chains per instance (empty: one count for all)
+    int32_t *d_inst_chains = nullptr;   // device copy (own allocation)
+    int32_t *d_work = nullptr;          // device work list (own allocation)
+    size_t work_cap = 0;                // capacity in (instance, group) pairs
+    int work_chains = -1;               // `chains` the work list was built for
+    bool work_valid = false;
 };
+
+namespace {
+
+// SAIS_AUTO grouping (see struct sais_problem).
+void build_groups(sais_problem *p) {
+    p->groups.clear();
+    auto key_of = [&](const HostInst &h) -> int {
+        const bool eligible = h.has_w && h.m <= kMaxBlockedConstraints && h.npad + 16 <= 512;
+        if (!eligible) return 0;
+        if (h.lo_own) return 3;
+        return blocked_smem_bytes(h.npad, h.words, 16, false, false) > kMaxSmemPerBlock ? 2 : 1;
+    };
+    for (int key = 1; key <= 4; ++key) {
+        const int k = key == 4 ? 0 : key;   // blocked groups first, then the plain group
+        sais_problem::Group g;
+        for (int j = 0; j < p->count; ++j) {
+            const HostInst &h = p->host[j];
+            if (key_of(h) != k) continue;
+            g.members.push_back(j);
+            g.max_m = std::max(g.max_m, h.m);
+            g.max_npad = std::max(g.max_npad, h.npad);
+            if (h.has_w) g.max_npad_w = std::max(g.max_npad_w, h.npad);
+            g.words = std::max(g.words, h.words);
+            g.any_w = g.any_w || h.has_w;
+        }
+        if (g.members.empty()) continue;
+        g.variant = k == 0 ? SAIS_PLAIN : SAIS_BLOCKED;
+        g.blocked_ok = k != 0;
+        g.stream_w = k >= 2;
+        g.hilo = k == 3;
+        auto cost = [&](int j) {
+            const HostInst &h = p->host[j];
+            return (double)h.nprime * (h.has_w ? (double)h.npad : (double)std::max(1, h.m));
+        };
+        std::stable_sort(g.members.begin(), g.members.end(),
+                         [&](int x, int y) { return cost(x) > cost(y); });
+        p->groups.push_back(std::move(g));
+    }
+    p->work_valid = false;
+}
+
+int group_cta(const sais_problem::Group &g) { return g.variant == SAIS_BLOCKED ? 128 : g.cpb; }
+
+// Device work list for `chains` (the uniform count, or the stride when per-instance counts are
+// set).  Built on the host and copied; (re)allocated only outside stream capture.
+sais_status ensure_work(sais_problem *p, int chains, cudaStream_t st) {
+    if (p->work_valid && p->work_chains == chains) return SAIS_OK;
+    std::vector<int32_t> w;
+    for (auto &g : p->groups) {
+        g.work_off = w.size() / 2;
+        const int cta = group_cta(g);
+        for (int j : g.members) {
+            const int cj = p->inst_chains.empty() ? chains : p->inst_chains[j];
+            for (int q = 0; q < (cj + cta - 1) / cta; ++q) {
+                w.push_back(j);
+                w.push_back(q);
+            }
+        }
+        g.nwork = w.size() / 2 - g.work_off;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail(SAIS_EINVAL, "SAIS_AUTO: prepare the launch (one call with these chains) "
+                                 "before capturing a graph");
+    // Launches already queued on the stream may still read the old list.
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(SAIS_ECUDA, "work list: %s", cudaGetErrorString(e));
+    if (w.size() / 2 > p->work_cap) {
+        if (p->d_work) cudaFree(p->d_work);
+        p->d_work = nullptr;
+        p->work_cap = 0;
+        e = cudaMalloc(&p->d_work, w.size() * 4);
+        if (e != cudaSuccess) return fail(SAIS_ENOMEM, "work list: %s", cudaGetErrorString(e));
+        p->work_cap = w.size() / 2;
+    }
+    e = cudaMemcpy(p->d_work, w.data(), w.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(SAIS_ECUDA, "work list copy: %s", cudaGetErrorString(e));
+    p->work_chains = chains;
+    p->work_valid = true;
+    return SAIS_OK;
+}
+
+cudaError_t launch_group(const sais_problem *p, const sais_problem::Group &g, const SampleArgs &a,
+                         long long polls, cudaStream_t st) {
+    if (g.nwork == 0) return cudaSuccess;
+    SampleArgs ga = a;
+    ga.work = p->d_work + 2 * g.work_off;
+    ga.nwork = (int32_t)g.nwork;
+    if (g.variant == SAIS_BLOCKED)
+        return launch_blocked_sampler(ga, g.max_m, g.max_npad, g.words, g.block_k, g.stream_w,
+                                      g.hilo, p->d_status, polls, st);
+    return launch_plain_sampler(ga, g.max_m, g.max_npad_w, g.words, g.cpb, st);
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -414,6 +535,7 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
     }
     p->d_inst = reinterpret_cast<InstDev *>(p->pool);
     p->d_status = reinterpret_cast<int32_t *>(base + status_off);
+    build_groups(p);
     *out = p;
     return SAIS_OK;
 }
@@ -430,6 +552,8 @@ sais_status sais_destroy_problem(sais_problem *p) {
     cudaSetDevice(p->device);
     cudaError_t e = cudaDeviceSynchronize();
     if (p->pool) cudaFree(p->pool);
+    if (p->d_work) cudaFree(p->d_work);
+    if (p->d_inst_chains) cudaFree(p->d_inst_chains);
     cudaSetDevice(prev);
     delete p;
     if (e != cudaSuccess) return fail(SAIS_ECUDA, "synchronize before free: %s", cudaGetErrorString(e));
@@ -482,7 +606,7 @@ sais_status check_sample_params(const sais_problem *p, const sais_sample_params 
     if (prm->sweeps < 1) return fail(SAIS_EINVAL, "sweeps = %d: need >= 1", prm->sweeps);
     if (!(prm->beta_max >= 0.0f) || !std::isfinite(prm->beta_max))
         return fail(SAIS_EINVAL, "beta_max must be finite and >= 0");
-    if (prm->variant != SAIS_PLAIN && prm->variant != SAIS_BLOCKED)
+    if (prm->variant != SAIS_PLAIN && prm->variant != SAIS_BLOCKED && prm->variant != SAIS_AUTO)
         return fail(SAIS_EINVAL, "unknown variant %d", prm->variant);
     if (prm->chains_per_cta != 0 && prm->chains_per_cta != 32 && prm->chains_per_cta != 64 &&
         prm->chains_per_cta != 128)
@@ -527,9 +651,31 @@ sais_status enqueue_sample(sais_problem *p, const sais_sample_params *prm, const
     a.g = g;
     a.feasible = feasible;
     a.trace = trace;
-    a.status = nullptr;
-    cudaError_t e;
     a.status = p->d_status;
+    a.inst_chains = p->d_inst_chains;
+    if (!p->inst_chains.empty())
+        for (int j = 0; j < p->count; ++j)
+            if (p->inst_chains[j] > prm->chains)
+                return fail(SAIS_EINVAL,
+                            "instance %d has %d chains but the chains argument (the row stride) "
+                            "is %d", j, p->inst_chains[j], prm->chains);
+    cudaError_t e;
+    if (prm->variant == SAIS_AUTO) {
+        for (const auto &g : p->groups)
+            if (g.variant == SAIS_PLAIN &&
+                plain_smem_bytes(g.max_npad_w, g.words, g.any_w, g.cpb) > (size_t)kMaxPlainSmem)
+                return fail(SAIS_EUNSUPPORTED,
+                            "plain sampler group: padded N'=%d needs %zu bytes of shared memory",
+                            g.max_npad_w, plain_smem_bytes(g.max_npad_w, g.words, g.any_w, g.cpb));
+        sais_status s = ensure_work(p, prm->chains, st);
+        if (s != SAIS_OK) return s;
+        for (const auto &g : p->groups) {
+            e = launch_group(p, g, a, (long long)prm->debug_wait_polls, st);
+            if (e != cudaSuccess)
+                return fail(SAIS_ECUDA, "sampler launch (group): %s", cudaGetErrorString(e));
+        }
+        return SAIS_OK;
+    }
     if (prm->variant == SAIS_BLOCKED) {
         const int k = prm->block_k ? prm->block_k : 16;
         if (!p->all_w)
@@ -628,6 +774,7 @@ sais_status sais_update_lambda(sais_problem *p, const int64_t *g, int32_t chains
     a.project = project_nonneg ? 1 : 0;
     a.track_best = 0;
     a.do_lambda = 1;
+    a.inst_chains = p->d_inst_chains;
     a.g = g;
     a.lambda = lambda;
     cudaError_t e = launch_post(a, static_cast<cudaStream_t>(stream));
@@ -652,6 +799,7 @@ sais_status sais_track_best(sais_problem *p, const uint32_t *x, const int64_t *c
     a.m_stride = p->m_stride;
     a.track_best = 1;
     a.do_lambda = 0;
+    a.inst_chains = p->d_inst_chains;
     a.x = x;
     a.cost = cost;
     a.feasible = feasible;
@@ -737,6 +885,7 @@ sais_status sais_solve(sais_problem *p, const sais_solve_params *prm, sais_solve
     pa.project = prm->project_nonneg ? 1 : 0;
     pa.track_best = 1;
     pa.do_lambda = 1;
+    pa.inst_chains = p->d_inst_chains;
     pa.x = d_x;
     pa.cost = d_cost;
     pa.g = d_g;
@@ -771,6 +920,10 @@ sais_status sais_solve(sais_problem *p, const sais_solve_params *prm, sais_solve
         }
     } evs{ev0, ev1};
     cudaGraphExec_t exec = nullptr;
+    if (prm->variant == SAIS_AUTO) {
+        sais_status r = ensure_work(p, C, st);
+        if (r != SAIS_OK) return r;
+    }
     if (prm->use_graph) {
         cudaStream_t cap = st;
         bool own = false;
@@ -836,8 +989,154 @@ sais_status sais_solve(sais_problem *p, const sais_solve_params *prm, sais_solve
     SAIS_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
     res->elapsed_ms = ms;
     int64_t upd = 0;
-    for (const HostInst &h : p->host) upd += (int64_t)h.nprime;
-    res->spin_updates = upd * C * (int64_t)prm->sweeps * K;
+    for (int j = 0; j < count; ++j)
+        upd += (int64_t)p->host[j].nprime *
+               (p->inst_chains.empty() ? (int64_t)C : (int64_t)p->inst_chains[j]);
+    res->spin_updates = upd * (int64_t)prm->sweeps * K;
+    return SAIS_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+sais_status sais_set_instance_chains(sais_problem *p, const int32_t *counts) {
+    if (!p) return fail(SAIS_EINVAL, "NULL problem");
+    DeviceGuard dg(p->device);
+    if (!counts) {
+        p->inst_chains.clear();
+        if (p->d_inst_chains) cudaFree(p->d_inst_chains);
+        p->d_inst_chains = nullptr;
+        p->work_valid = false;
+        return SAIS_OK;
+    }
+    for (int j = 0; j < p->count; ++j)
+        if (counts[j] < 1) return fail(SAIS_EINVAL, "counts[%d] = %d: need >= 1", j, counts[j]);
+    if (!p->d_inst_chains) {
+        cudaError_t e = cudaMalloc(&p->d_inst_chains, (size_t)p->count * 4);
+        if (e != cudaSuccess) return fail(SAIS_ENOMEM, "chain counts: %s", cudaGetErrorString(e));
+    }
+    cudaError_t e = cudaMemcpy(p->d_inst_chains, counts, (size_t)p->count * 4,
+                               cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(SAIS_ECUDA, "chain counts copy: %s", cudaGetErrorString(e));
+    p->inst_chains.assign(counts, counts + p->count);
+    p->work_valid = false;
+    return SAIS_OK;
+}
+
+sais_status sais_autotune(sais_problem *p, int32_t chains, int32_t sweeps, sais_tuning *out,
+                          void *stream) {
+    if (!p || !out) return fail(SAIS_EINVAL, "NULL argument");
+    if (chains < 1 || sweeps < 1) return fail(SAIS_EINVAL, "need chains >= 1 and sweeps >= 1");
+    DeviceGuard dg(p->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t nch = (size_t)p->count * chains;
+    const size_t sz[5] = {nch * p->words * 4, nch * 8, nch * p->m_stride * 8, nch,
+                          (size_t)p->count * p->m_stride * 4};
+    size_t off[5], cur = 0;
+    for (int i = 0; i < 5; ++i) {
+        off[i] = cur;
+        cur = align_up(cur + sz[i], 256);
+    }
+    unsigned char *buf = nullptr;
+    SAIS_CUDA(cudaMalloc(&buf, cur));
+    struct Free {
+        unsigned char *q;
+        ~Free() { cudaFree(q); }
+    } fr{buf};
+    SAIS_CUDA(cudaMemsetAsync(buf, 0, cur, st));
+    cudaEvent_t e0, e1;
+    SAIS_CUDA(cudaEventCreate(&e0));
+    SAIS_CUDA(cudaEventCreate(&e1));
+    struct Ev {
+        cudaEvent_t a, b;
+        ~Ev() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } evs{e0, e1};
+    sais_sample_params sp{};
+    sp.chains = chains;
+    sp.sweeps = sweeps;
+    sp.beta_max = 10.0f;
+    sp.seed = 1;
+    SampleArgs a{};
+    a.inst = p->d_inst;
+    a.count = p->count;
+    a.chains = chains;
+    a.sweeps = sweeps;
+    a.beta_max = sp.beta_max;
+    a.seed = sp.seed;
+    a.words = p->words;
+    a.m_stride = p->m_stride;
+    a.lambda = reinterpret_cast<const float *>(buf + off[4]);
+    a.x = reinterpret_cast<uint32_t *>(buf + off[0]);
+    a.cost = reinterpret_cast<int64_t *>(buf + off[1]);
+    a.g = reinterpret_cast<int64_t *>(buf + off[2]);
+    a.feasible = buf + off[3];
+    a.status = p->d_status;
+    a.inst_chains = p->d_inst_chains;
+    std::memset(out, 0, sizeof *out);
+    for (size_t gi = 0; gi < p->groups.size(); ++gi) {
+        auto &g = p->groups[gi];
+        struct Cand {
+            int variant, k, cpb;
+        };
+        std::vector<Cand> cands;
+        if (g.blocked_ok) {
+            cands.push_back({SAIS_BLOCKED, 16, g.cpb});
+            if (!g.stream_w &&
+                blocked_smem_bytes(g.max_npad, g.words, 32, false, false) <= kMaxSmemPerBlock &&
+                g.max_npad + 32 <= 512)
+                cands.push_back({SAIS_BLOCKED, 32, g.cpb});
+        }
+        for (int cpb : {32, 64, 128})
+            if (plain_smem_bytes(g.max_npad_w, g.words, g.any_w, cpb) <= (size_t)kMaxPlainSmem)
+                cands.push_back({SAIS_PLAIN, g.block_k, cpb});
+        double best = 1e300;
+        Cand pick = cands.front();
+        for (const Cand &c : cands) {
+            g.variant = c.variant;
+            g.block_k = c.k;
+            g.cpb = c.cpb;
+            p->work_valid = false;
+            sais_status r = ensure_work(p, chains, st);
+            if (r != SAIS_OK) return r;
+            cudaError_t e = launch_group(p, g, a, 0, st);   // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+            if (e == cudaSuccess) e = launch_group(p, g, a, 0, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) return fail(SAIS_ECUDA, "autotune launch: %s", cudaGetErrorString(e));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                pick = c;
+            }
+        }
+        g.variant = pick.variant;
+        g.block_k = pick.k;
+        g.cpb = pick.cpb;
+        g.tuned_ms = best;
+        if (gi < 8) {
+            out->group_variant[gi] = g.variant;
+            out->group_block_k[gi] = g.variant == SAIS_BLOCKED ? g.block_k : 0;
+            out->group_chains_per_cta[gi] = g.variant == SAIS_PLAIN ? g.cpb : 128;
+            out->group_size[gi] = (int32_t)g.members.size();
+            out->group_ms[gi] = best;
+        }
+        (g.variant == SAIS_BLOCKED ? out->blocked_instances : out->plain_instances) +=
+            (int32_t)g.members.size();
+    }
+    out->groups = (int32_t)p->groups.size();
+    p->work_valid = false;
+    int32_t v = 0;
+    SAIS_CUDA(cudaMemcpy(&v, p->d_status, 4, cudaMemcpyDeviceToHost));
+    if (v != SAIS_OK) {
+        cudaMemset(p->d_status, 0, 4);
+        return fail((sais_status)v, "a sampler kernel reported: %s", sais_status_string((sais_status)v));
+    }
     return SAIS_OK;
 }
 
@@ -855,9 +1154,14 @@ sais_status problem_view(const sais_problem *p, ProblemView *out) {
     out->m_stride = p->m_stride;
     out->d_inst = p->d_inst;
     out->d_status = p->d_status;
-    long long tot = 0;
-    for (const HostInst &h : p->host) tot += h.nprime;
+    out->d_inst_chains = p->d_inst_chains;
+    long long tot = 0, totc = 0;
+    for (int j = 0; j < p->count; ++j) {
+        tot += p->host[j].nprime;
+        totc += (long long)p->host[j].nprime * (p->inst_chains.empty() ? 0 : p->inst_chains[j]);
+    }
     out->spins_total = tot;
+    out->spin_chains_total = totc;
     return SAIS_OK;
 }
 

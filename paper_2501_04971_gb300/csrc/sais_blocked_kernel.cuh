@@ -114,7 +114,8 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
     extern __shared__ __align__(1024) unsigned char smem[];
     constexpr int kPreM = MC < 2 ? MC : 2;   // constraint columns in the per-spin record
     constexpr uint32_t kRing = 3;
-    const int j = blockIdx.y;
+    const int j = a.work ? a.work[2 * blockIdx.x] : (int)blockIdx.y;
+    const int grp = a.work ? a.work[2 * blockIdx.x + 1] : (int)blockIdx.x;
     const InstDev *__restrict__ ip = a.inst + j;
     const int m = ip->m, nprime = ip->nprime, npad = ip->npad, words = ip->words;
     const int nb = (nprime + K - 1) / K;
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
         // up to two blocks ahead, into a two-slot ring.  Lane 0 of warp 4 stages W.
         const int q = warp - kNoiseWarp0;
         const int r = q * 32 + lane;
-        const uint32_t chain = (uint32_t)(blockIdx.x * kLanes + r);
+        const uint32_t chain = (uint32_t)(grp * kLanes + r);
         const uint64_t seed = a.seed + (uint64_t)j;
         const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
         const uint32_t total = (uint32_t)a.sweeps * (uint32_t)nb;
@@ -231,8 +232,8 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
         __syncwarp();
     } else {
         const int r = threadIdx.x;
-        const int chain = blockIdx.x * kLanes + r;
-        const bool valid = chain < a.chains;
+        const int chain = grp * kLanes + r;
+        const bool valid = chain < (a.inst_chains ? a.inst_chains[j] : a.chains);
         const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
         const uint64_t seed = a.seed + (uint64_t)j;
         const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
@@ -627,7 +628,7 @@ cudaError_t launch_k(const SampleArgs &a, int32_t *status, long long polls, size
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((a.chains + kLanes - 1) / kLanes, a.count);
+    const dim3 grid = a.work ? dim3(a.nwork, 1) : dim3((a.chains + kLanes - 1) / kLanes, a.count);
     kern<<<grid, kThreadsBlocked, smem, s>>>(a, status, polls, cols);
     return cudaGetLastError();
 }

@@ -64,6 +64,12 @@ struct SampleArgs {
     uint8_t *feasible;       // [count*chains] or NULL
     uint32_t *trace;         // [count*chains*sweeps*words] or NULL
     int32_t *status;         // device status word (SAIS_ETIMEOUT etc.), or NULL
+    // Ragged launches: work[2 i], work[2 i + 1] = (instance, chain group) of CTA i, nwork
+    // entries; NULL = the full grid (chain groups x instances).  inst_chains[j] = chains of
+    // instance j (NULL: `chains` for all); `chains` stays the stride of the outputs.
+    const int32_t *work;
+    int32_t nwork;
+    const int32_t *inst_chains;
 };
 
 // Arguments of the per-instance post-processing launch (readout reduction, best-so-far,
@@ -92,6 +98,7 @@ struct PostArgs {
     int32_t *best_iter;      // [count]
     int32_t *best_chain;     // [count]
     int64_t *feasible_count; // [count]
+    const int32_t *inst_chains;  // chains of instance j (NULL: `chains` for all)
 };
 
 // Launchers (defined in the .cu files); they only enqueue work on `stream`.
@@ -117,6 +124,8 @@ struct ProblemView {
     const InstDev *d_inst;
     int32_t *d_status;
     long long spins_total;   // sum of N' over the instances
+    const int32_t *d_inst_chains;   // per-instance chains (device), or NULL
+    long long spin_chains_total;    // sum of N' x chains when per-instance chains are set, else 0
 };
 sais_status problem_view(const sais_problem *p, ProblemView *out);
 sais_status enqueue_sample_internal(sais_problem *p, const sais_sample_params *prm,

@@ -178,6 +178,7 @@ extern "C" sais_status sais_solve_noalloc(sais_problem *p, const sais_solve_para
     pa.best_iter = d_bi;
     pa.best_chain = d_bch;
     pa.feasible_count = d_fc;
+    pa.inst_chains = v.d_inst_chains;
     for (int k = 0; k < K; ++k) {
         st = enqueue_sample_internal(p, &sp, d_lam, d_iter, d_x, d_cost, d_g, d_feas, s);
         if (st != SAIS_OK) return st;
@@ -201,7 +202,9 @@ extern "C" sais_status sais_solve_noalloc(sais_problem *p, const sais_solve_para
     }
     res->elapsed_ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    res->spin_updates = (int64_t)v.spins_total * C * (int64_t)prm->sweeps * K;
+    res->spin_updates = (v.spin_chains_total ? (int64_t)v.spin_chains_total
+                                              : (int64_t)v.spins_total * C) *
+                        (int64_t)prm->sweeps * K;
     return SAIS_OK;
 #undef NOALLOC_CUDA
 }

@@ -29,7 +29,8 @@ namespace {
 
 template <int MC>
 __global__ void __launch_bounds__(128) plain_sampler_kernel(SampleArgs a) {
-    const int j = blockIdx.y;
+    const int j = a.work ? a.work[2 * blockIdx.x] : (int)blockIdx.y;
+    const int grp = a.work ? a.work[2 * blockIdx.x + 1] : (int)blockIdx.x;
     const InstDev *__restrict__ ip = a.inst + j;
     const int m = ip->m, nprime = ip->nprime, npad = ip->npad, words = ip->words;
     const bool has_w = ip->has_w != 0;
@@ -42,8 +43,8 @@ __global__ void __launch_bounds__(128) plain_sampler_kernel(SampleArgs a) {
     const float *__restrict__ asum = ip->asum;
 
     const int cpb = blockDim.x, tid = threadIdx.x;
-    const int chain = blockIdx.x * cpb + tid;
-    const bool valid = chain < a.chains;
+    const int chain = grp * cpb + tid;
+    const bool valid = chain < (a.inst_chains ? a.inst_chains[j] : a.chains);
     const uint32_t iter = a.iter_dev ? *a.iter_dev : a.iter;
     const uint64_t seed = a.seed + (uint64_t)j;
     const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
@@ -189,7 +190,7 @@ cudaError_t launch_mc(const SampleArgs &a, int cpb, size_t smem, cudaStream_t s)
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((a.chains + cpb - 1) / cpb, a.count);
+    const dim3 grid = a.work ? dim3(a.nwork, 1) : dim3((a.chains + cpb - 1) / cpb, a.count);
     kern<<<grid, cpb, smem, s>>>(a);
     return cudaGetLastError();
 }

@@ -35,8 +35,8 @@ __device__ __forceinline__ void warp_argmin(long long &c, int &ch) {
 __global__ void __launch_bounds__(kPostThreads) post_kernel(PostArgs a) {
     const int j = blockIdx.x;
     const int m = a.inst[j].m;
-    const int C = a.chains;
-    const size_t base = (size_t)j * C;
+    const int C = a.inst_chains ? a.inst_chains[j] : a.chains;   // this instance's chains
+    const size_t base = (size_t)j * a.chains;                     // rows are strided by `chains`
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int kWarps = kPostThreads / 32;
     const uint32_t iter = a.iter_dev ? *a.iter_dev : a.iter;

@@ -22,8 +22,8 @@ _f32, _f64, _P = ctypes.c_float, ctypes.c_double, ctypes.c_void_p
 
 SAIS_OK, SAIS_EINVAL, SAIS_ENOMEM, SAIS_ECUDA, SAIS_EOVERFLOW, SAIS_ETIMEOUT, \
     SAIS_EUNSUPPORTED = range(7)
-SAIS_PLAIN, SAIS_BLOCKED = 0, 1
-_VARIANTS = {"plain": SAIS_PLAIN, "blocked": SAIS_BLOCKED}
+SAIS_PLAIN, SAIS_BLOCKED, SAIS_AUTO = 0, 1, 2
+_VARIANTS = {"plain": SAIS_PLAIN, "blocked": SAIS_BLOCKED, "auto": SAIS_AUTO}
 
 
 class sais_problem_desc(ctypes.Structure):
@@ -55,6 +55,13 @@ class sais_solve_params(ctypes.Structure):
                 ("use_graph", _i32), ("lambda0", _P)]
 
 
+class sais_tuning(ctypes.Structure):
+    _fields_ = [("groups", _i32), ("blocked_instances", _i32), ("plain_instances", _i32),
+                ("reserved", _i32), ("group_variant", _i32 * 8), ("group_block_k", _i32 * 8),
+                ("group_chains_per_cta", _i32 * 8), ("group_size", _i32 * 8),
+                ("group_ms", _f64 * 8)]
+
+
 class sais_solve_result(ctypes.Structure):
     _fields_ = [("best_cost", _P), ("best_x", _P), ("best_iter", _P), ("best_chain", _P),
                 ("feasible_count", _P), ("lambda_final", _P), ("lambda_trace", _P),
@@ -74,6 +81,8 @@ _SIGS = {
     "sais_track_best": [_P, _P, _P, _P, _i32, _u32, _P, _P, _P, _P, _P, _P],
     "sais_solve": [_P, ctypes.POINTER(sais_solve_params), ctypes.POINTER(sais_solve_result), _P],
     "sais_synchronize": [_P, _P],
+    "sais_set_instance_chains": [_P, _P],
+    "sais_autotune": [_P, _i32, _i32, ctypes.POINTER(sais_tuning), _P],
     "sais_solve_noalloc": [_P, ctypes.POINTER(sais_solve_params),
                            ctypes.POINTER(sais_solve_result), _P],
 }
@@ -187,6 +196,16 @@ def sais_solve_noalloc(h, prm, res, stream_ptr):
            "sais_solve_noalloc")
 
 
+def sais_set_instance_chains(h, counts_ptr):
+    _check(lib().sais_set_instance_chains(h, counts_ptr), "sais_set_instance_chains")
+
+
+def sais_autotune(h, chains: int, sweeps: int, stream_ptr):
+    out = sais_tuning()
+    _check(lib().sais_autotune(h, chains, sweeps, ctypes.byref(out), stream_ptr), "sais_autotune")
+    return out
+
+
 def sais_synchronize(h, stream_ptr):
     _check(lib().sais_synchronize(h, stream_ptr), "sais_synchronize")
 
@@ -267,6 +286,27 @@ class Problem:
         p.block_k, p.chains_per_cta = block_k, chains_per_cta
         p.debug_wait_polls = debug_wait_polls
         return p
+
+    def set_instance_chains(self, counts=None):
+        """sais_set_instance_chains: per-instance chain counts (None: one count for all)."""
+        if counts is None:
+            sais_set_instance_chains(self.handle, None)
+            self.inst_chains = None
+            return
+        c = np.ascontiguousarray(counts, dtype=np.int32)
+        assert c.size == self.count
+        sais_set_instance_chains(self.handle, c.ctypes.data_as(_P))
+        self.inst_chains = c
+
+    def autotune(self, chains: int, sweeps: int = 20, stream=None):
+        """sais_autotune: returns a dict of the per-group choices."""
+        t = sais_autotune(self.handle, chains, sweeps, _stream_ptr(stream))
+        g = t.groups
+        return {"groups": g, "blocked_instances": t.blocked_instances,
+                "plain_instances": t.plain_instances,
+                "variant": list(t.group_variant)[:g], "block_k": list(t.group_block_k)[:g],
+                "chains_per_cta": list(t.group_chains_per_cta)[:g],
+                "size": list(t.group_size)[:g], "ms": list(t.group_ms)[:g]}
 
     def synchronize(self, stream=None):
         """sais_synchronize: wait for the stream, raise SaisError on a device-side timeout."""
