@@ -110,22 +110,23 @@ typedef enum sais_variant {
     SAIS_PLAIN = 0,          /* per-spin sampler: FP32 fields, rank-1 update on every flip  */
     SAIS_BLOCKED = 1,        /* k spins per block, rank-k field update on the tensor cores  */
     SAIS_AUTO = 2            /* per launch group of the batch: the blocked sampler where an
-                                instance allows it (quadratic objective, m <= 8, N' <= 496),
+                                instance allows it (quadratic objective, m <= 8, N' <= 448),
                                 the plain sampler otherwise, or the choices sais_autotune
                                 made; ragged work lists, most expensive instances first      */
 } sais_variant;
 
-/* What sais_autotune chose for each launch group of SAIS_AUTO (first 8 groups). */
+/* What sais_autotune chose for each launch group of SAIS_AUTO (first 16 groups). */
 typedef struct sais_tuning {
     int32_t groups;                  /* launch groups of the batch                         */
     int32_t blocked_instances;       /* instances now run by the blocked sampler           */
     int32_t plain_instances;         /* instances now run by the plain sampler             */
     int32_t reserved;
-    int32_t group_variant[8];        /* sais_variant chosen per group                      */
-    int32_t group_block_k[8];        /* block size (blocked groups)                        */
-    int32_t group_chains_per_cta[8]; /* chains per CTA                                     */
-    int32_t group_size[8];           /* instances per group                                */
-    double group_ms[8];              /* measured time of the chosen configuration          */
+    int32_t group_variant[16];       /* sais_variant chosen per group                      */
+    int32_t group_block_k[16];       /* block size (blocked groups)                        */
+    int32_t group_chains_per_cta[16];/* chains per CTA                                     */
+    int32_t group_size[16];          /* instances per group                                */
+    double group_ms[16];             /* measured time of the chosen configuration          */
+    int64_t group_spin_updates[16];  /* spin updates of one timed launch of the group      */
 } sais_tuning;
 
 /* One annealing run per chain (Sec. III-B): every chain starts at x = 0 and performs `sweeps`

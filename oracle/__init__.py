@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "saim_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "mlp_oracle.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libsaim_oracle.so")
 _lock = threading.Lock()
@@ -31,15 +32,17 @@ CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast
           "-fopenmp", "-Wall", "-Wextra", "-Wno-unused-parameter"]
 
 
-def build(force: bool = False, src: str = _SRC, out: str = _LIB_PATH,
+def build(force: bool = False, src: Optional[str] = None, out: str = _LIB_PATH,
           extra_flags: Optional[list] = None) -> str:
-    """Compile the oracle with gcc into ``out`` (default: oracle/_build/libsaim_oracle.so)."""
+    """Compile the oracle with gcc into ``out`` (default: oracle/_build/libsaim_oracle.so).
+    ``src`` replaces saim_oracle.c (the mutation tests build altered copies of it)."""
     os.makedirs(os.path.dirname(out), exist_ok=True)
+    srcs = [src or _SRC] + _SRCS[1:]
     if (not force and os.path.exists(out)
-            and os.path.getmtime(out) >= os.path.getmtime(src)
+            and all(os.path.getmtime(out) >= os.path.getmtime(f) for f in srcs)
             and not extra_flags):
         return out
-    cmd = ["gcc", *CFLAGS, *(extra_flags or []), src, "-o", out + ".tmp", "-lm"]
+    cmd = ["gcc", *CFLAGS, *(extra_flags or []), *srcs, "-o", out + ".tmp", "-lm"]
     subprocess.run(cmd, check=True, capture_output=True, text=True)
     os.replace(out + ".tmp", out)
     return out
@@ -74,6 +77,11 @@ _SIGS = {
     "or_enumerate_lagrangian": (None, [_i32, _i32, _i32, _P, _P, _P, _P, _P, _f32, _f32, _f32,
                                        _P]),
     "or_brute_force_opt": (_i64, [_i32, _i32, _P, _P, _P, _P, _P]),
+    "or_bf16_round": (_f32, [_f32]),
+    "or_features": (None, [_i32, _i32, _P, _P, _P, _P, _f32, _f32, _f32, _P]),
+    "or_mlp_forward": (None, [_P, _P, _P, _i32, _i32, _P]),
+    "or_mlp_grad": (_f64, [_P, _P, _P, _P, _i32, _i32, _P]),
+    "or_adam_step": (None, [_i32, _P, _P, _P, _P, _i32, _f64, _f64, _f64, _f64]),
 }
 
 
@@ -295,3 +303,52 @@ def solve(p: Problem, K: int, C: int, T: int, beta_max: float, eta: float, seed:
     found = int(bc[0]) != np.iinfo(np.int64).max
     return SolveResult(int(bc[0]) if found else None, bx if found else None, int(bi[0]),
                        int(bch[0]), lt, int(fc[0]), costs, gs)
+
+
+# --------------------------------------------------------------------------------------------
+# Learned multiplier warm start (no counterpart in the paper; see mlp_oracle.c)
+# --------------------------------------------------------------------------------------------
+MLP_PARAMS, MLP_HIDDEN = 20612, 128
+MLP_OFF_W1, MLP_OFF_W2, MLP_OFF_W3, MLP_OFF_B3 = 0, 2048, 20480, 20608
+MLP_BF16, MLP_ABS = 1, 2
+
+
+def bf16_round(v: float) -> float:
+    """FP32 -> BF16, round to nearest even (returned as FP32)."""
+    return float(load().or_bf16_round(float(v)))
+
+
+def features(p: "Problem") -> np.ndarray:
+    """Per-constraint features (m x 8) of Sec. IV-A's normalised instance (mlp_oracle.c)."""
+    out = np.zeros((p.m, 8), np.float32)
+    load().or_features(p.n, p.m, _ptr(p.W), _ptr(p.h), _ptr(p.A), _ptr(p.b), p.alpha,
+                       p.density, p.penalty, _ptr(out))
+    return out
+
+
+def mlp_forward(params, norm, X, flags: int = 0) -> np.ndarray:
+    """lambda predicted for each row of X (rows x 8), FP64."""
+    params, norm, X = _c(params, np.float32), _c(norm, np.float32), _c(X, np.float32)
+    y = np.zeros(X.shape[0], np.float64)
+    load().or_mlp_forward(_ptr(params), _ptr(norm), _ptr(X), X.shape[0], flags, _ptr(y))
+    return y
+
+
+def mlp_grad(params, norm, X, t, flags: int = 0):
+    """(loss, gradient[MLP_PARAMS]) of the mean squared error on normalised targets, FP64."""
+    params, norm, X, t = (_c(params, np.float32), _c(norm, np.float32), _c(X, np.float32),
+                          _c(t, np.float32))
+    g = np.zeros(MLP_PARAMS, np.float64)
+    loss = load().or_mlp_grad(_ptr(params), _ptr(norm), _ptr(X), _ptr(t), X.shape[0], flags,
+                              _ptr(g))
+    return float(loss), g
+
+
+def adam_step(theta, mom, vel, g, t: int, lr: float, b1: float = 0.9, b2: float = 0.999,
+              eps: float = 1e-8):
+    """One Adam step in place on FP64 arrays (Kingma & Ba, Algorithm 1)."""
+    for a in (theta, mom, vel):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = _c(g, np.float64)
+    load().or_adam_step(theta.size, _ptr(theta), _ptr(mom), _ptr(vel), _ptr(g), t, lr, b1, b2,
+                        eps)

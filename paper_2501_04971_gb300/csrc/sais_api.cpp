@@ -244,21 +244,33 @@ struct sais_problem {
 
 namespace {
 
-// SAIS_AUTO grouping (see struct sais_problem).
+// SAIS_AUTO grouping (see struct sais_problem).  Keys: 1 blocked with W resident, 2 streamed,
+// 3 streamed hi/lo; plain instances split by whether they have W and by padded N' (bucket of
+// 128 spins), so each plain group sizes its shared memory for its own largest member.
 void build_groups(sais_problem *p) {
     p->groups.clear();
     auto key_of = [&](const HostInst &h) -> int {
         const bool eligible = h.has_w && h.m <= kMaxBlockedConstraints && h.npad + 16 <= 512;
-        if (!eligible) return 0;
+        if (!eligible) return 100 + (h.has_w ? 1000 : 0) + (h.npad + 127) / 128;
         if (h.lo_own) return 3;
         return blocked_smem_bytes(h.npad, h.words, 16, false, false) > kMaxSmemPerBlock ? 2 : 1;
     };
-    for (int key = 1; key <= 4; ++key) {
-        const int k = key == 4 ? 0 : key;   // blocked groups first, then the plain group
+    std::vector<int> keys;
+    for (int j = 0; j < p->count; ++j) keys.push_back(key_of(p->host[j]));
+    std::vector<int> uniq = keys;
+    std::sort(uniq.begin(), uniq.end());
+    uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+    // blocked groups first (ascending key), then plain groups, largest N' first
+    std::stable_sort(uniq.begin(), uniq.end(), [](int x, int y) {
+        const bool bx = x < 100, by = y < 100;
+        if (bx != by) return bx;
+        return bx ? x < y : x > y;
+    });
+    for (int key : uniq) {
         sais_problem::Group g;
         for (int j = 0; j < p->count; ++j) {
+            if (keys[j] != key) continue;
             const HostInst &h = p->host[j];
-            if (key_of(h) != k) continue;
             g.members.push_back(j);
             g.max_m = std::max(g.max_m, h.m);
             g.max_npad = std::max(g.max_npad, h.npad);
@@ -266,11 +278,10 @@ void build_groups(sais_problem *p) {
             g.words = std::max(g.words, h.words);
             g.any_w = g.any_w || h.has_w;
         }
-        if (g.members.empty()) continue;
-        g.variant = k == 0 ? SAIS_PLAIN : SAIS_BLOCKED;
-        g.blocked_ok = k != 0;
-        g.stream_w = k >= 2;
-        g.hilo = k == 3;
+        g.variant = key >= 100 ? SAIS_PLAIN : SAIS_BLOCKED;
+        g.blocked_ok = key < 100;
+        g.stream_w = key == 2 || key == 3;
+        g.hilo = key == 3;
         auto cost = [&](int j) {
             const HostInst &h = p->host[j];
             return (double)h.nprime * (h.has_w ? (double)h.npad : (double)std::max(1, h.m));
@@ -1119,12 +1130,17 @@ sais_status sais_autotune(sais_problem *p, int32_t chains, int32_t sweeps, sais_
         g.block_k = pick.k;
         g.cpb = pick.cpb;
         g.tuned_ms = best;
-        if (gi < 8) {
+        if (gi < 16) {
             out->group_variant[gi] = g.variant;
             out->group_block_k[gi] = g.variant == SAIS_BLOCKED ? g.block_k : 0;
             out->group_chains_per_cta[gi] = g.variant == SAIS_PLAIN ? g.cpb : 128;
             out->group_size[gi] = (int32_t)g.members.size();
             out->group_ms[gi] = best;
+            long long upd = 0;
+            for (int j : g.members)
+                upd += (long long)p->host[j].nprime *
+                       (p->inst_chains.empty() ? chains : p->inst_chains[j]);
+            out->group_spin_updates[gi] = (int64_t)upd * sweeps;
         }
         (g.variant == SAIS_BLOCKED ? out->blocked_instances : out->plain_instances) +=
             (int32_t)g.members.size();

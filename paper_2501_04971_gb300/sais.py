@@ -57,9 +57,9 @@ class sais_solve_params(ctypes.Structure):
 
 class sais_tuning(ctypes.Structure):
     _fields_ = [("groups", _i32), ("blocked_instances", _i32), ("plain_instances", _i32),
-                ("reserved", _i32), ("group_variant", _i32 * 8), ("group_block_k", _i32 * 8),
-                ("group_chains_per_cta", _i32 * 8), ("group_size", _i32 * 8),
-                ("group_ms", _f64 * 8)]
+                ("reserved", _i32), ("group_variant", _i32 * 16), ("group_block_k", _i32 * 16),
+                ("group_chains_per_cta", _i32 * 16), ("group_size", _i32 * 16),
+                ("group_ms", _f64 * 16), ("group_spin_updates", _i64 * 16)]
 
 
 class sais_solve_result(ctypes.Structure):
@@ -306,7 +306,8 @@ class Problem:
                 "plain_instances": t.plain_instances,
                 "variant": list(t.group_variant)[:g], "block_k": list(t.group_block_k)[:g],
                 "chains_per_cta": list(t.group_chains_per_cta)[:g],
-                "size": list(t.group_size)[:g], "ms": list(t.group_ms)[:g]}
+                "size": list(t.group_size)[:g], "ms": list(t.group_ms)[:g],
+                "spin_updates": list(t.group_spin_updates)[:g]}
 
     def synchronize(self, stream=None):
         """sais_synchronize: wait for the stream, raise SaisError on a device-side timeout."""
