@@ -56,6 +56,11 @@ def parse():
     ap.add_argument("--gap-iters", type=int, default=100)
     ap.add_argument("--gap-eta", type=float, default=2000.0)
     ap.add_argument("--no-ragged", action="store_true")
+    ap.add_argument("--warmstart", action="store_true",
+                    help="also run the learned warm start: labels, training, evaluation")
+    ap.add_argument("--ws-train", type=int, default=20000)
+    ap.add_argument("--ws-eval", type=int, default=64)
+    ap.add_argument("--ws-epochs", type=int, default=200)
     ap.add_argument("--ragged-iters", type=int, default=3)
     ap.add_argument("--ragged-tune-sweeps", type=int, default=50)
     return ap.parse_args()
@@ -274,6 +279,71 @@ def ragged_measurement(a, sais, torch):
     return out
 
 
+def warmstart_measurement(a, sais, torch):
+    """Learned warm start: `ws_train` seeded QKP/MKP instances (N in [100, 500]) labelled by the
+    multipliers Algorithm 1 converges to (30 iterations x 128 chains x 200 sweeps, SAIS_AUTO,
+    graph-captured), the network trained on 90 % of the instances by the project's kernels and
+    checked on the other 10 %, then samples to a 1 % gap, warm against cold, on QKP N=500 d=0.5
+    and MKP N=500 m=10 (`ws_eval` instances each).  Also the device time of the training step
+    and of inference, with their tensor-core flops against the bf16 peak."""
+    from paper_2501_04971_gb300 import warmstart as ws, workloads as wl
+    t0 = time.perf_counter()
+    insts = ws.training_instances(a.ws_train)
+    t_gen = time.perf_counter() - t0
+    bud = ws.SolveBudget(iters=30, chains=128, sweeps=200, beta_max=a.beta_max, eta=a.gap_eta)
+    X, y, t_lab, upd = ws.label(insts, bud)
+    rows = np.cumsum([0] + [i.m for i in insts])
+    cut = int(rows[int(0.9 * len(insts))])
+    net, losses, t_train = ws.train(X[:cut], y[:cut], epochs=a.ws_epochs)
+    pred = ws.predict(net, X[cut:])
+    mse_w = float(np.mean((np.maximum(pred, 0) - y[cut:]) ** 2))
+    mse_c = float(np.mean(y[cut:] ** 2))
+    # kernel timing on 4096 rows (one minibatch): training step (forward, backward, Adam
+    # update) and inference
+    B = min(4096, X.shape[0])
+    Xd, yd = torch.tensor(X[:B], device="cuda"), torch.tensor(y[:B], device="cuda")
+    out = torch.empty(B, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = {}
+    for name, fn in (("train_step", lambda: net.train_step(Xd, yd, 1e-6)),
+                     ("forward", lambda: net.forward(Xd, out=out))):
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(50):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        times[name] = e0.elapsed_time(e1) / 50
+    flops_row = {"train_step": 2 * 128 * (16 + 144 + 128 + 144 + 16), "forward": 2 * 128 * (16 + 144)}
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("bf16_tflops", 1900.0)
+    kern = {k: {"ms": v, "rows": B, "tflops": flops_row[k] * B / (v / 1e3) / 1e12,
+                "frac_of_bf16_peak": flops_row[k] * B / (v / 1e3) / 1e12 / peak}
+            for k, v in times.items()}
+    ev_res = {}
+    for name, ev in (("qkp_n500_d0.5", [wl.qkp(500, 0.5, 7000 + i) for i in range(a.ws_eval)]),
+                     ("mkp_n500_m10", [wl.mkp(500, 10, 8000 + i) for i in range(a.ws_eval)])):
+        t1 = time.perf_counter()
+        r = ws.evaluate(net, ev, bud, best_seeds=2)
+        ev_res[name] = {"cold": {k: v for k, v in r["cold"].items() if k != "per_instance"},
+                        "warm": {k: v for k, v in r["warm"].items() if k != "per_instance"},
+                        "best_known_feasible": r["best_known_feasible"],
+                        "seconds": time.perf_counter() - t1}
+    net.close()
+    return {"train_instances": len(insts), "rows": int(X.shape[0]), "label_seconds": t_lab,
+            "label_spin_updates_per_s": upd / t_lab, "generate_seconds": t_gen,
+            "label_budget": "30 iterations x 128 chains x 200 sweeps, eta %g, lambda label = "
+                            "mean of the second half" % bud.eta,
+            "epochs": a.ws_epochs, "train_device_seconds": t_train,
+            "loss_first_last": [losses[0], losses[-1]],
+            "heldout_mse_warm": mse_w, "heldout_mse_lambda0": mse_c, "kernels": kern,
+            "samples_to_1pct_gap": ev_res,
+            "samples_unit": "chains x iterations (each sample = one anneal of 200 sweeps)"}
+
+
 # ------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------
@@ -442,6 +512,9 @@ def main():
     ragged = None
     if not a.no_ragged and world == 1:
         ragged = ragged_measurement(a, sais, torch)
+    warm = None
+    if a.warmstart and world == 1:
+        warm = warmstart_measurement(a, sais, torch)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -464,6 +537,8 @@ def main():
             "gpu_launches": 3 * a.steps, "clocks": clk.summary(),
             "updates_per_step": upd_step, "plain": plain_cmp, "gap_1pct": gap,
             "ragged": ragged}
+    if warm is not None:
+        line["warmstart"] = warm
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

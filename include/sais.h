@@ -301,6 +301,71 @@ SAIS_API sais_status sais_autotune(sais_problem *p, int32_t chains, int32_t swee
  * Errors: SAIS_EINVAL, SAIS_ECUDA, SAIS_ETIMEOUT. */
 SAIS_API sais_status sais_synchronize(sais_problem *p, void *stream);
 
+/* ---- Learned multiplier warm start (the paper has no counterpart) -------------------------
+ * A 7 -> 128 -> 128 -> 1 ReLU network (BF16 weights, FP32 accumulation, tensor cores) maps the
+ * features of one constraint k of an instance to the multiplier lambda_k that Algorithm 1
+ * (Sec. III-A) converges to, so that a run can start from it instead of lambda = 0.
+ *
+ * Features (8 floats per constraint, column 7 unused), from Sec. IV-A's normalised data:
+ *   f0 = min(1, b_k / sum_i a_ki) (1 if the row sum is 0); f1, f2 = sigma_g x mean, population
+ *   std of a_ki over the items; f3, f4 = sigma_f x mean, std of the nonzero profits h_i and
+ *   W_ij (i < j); f5 = n / 1000; f6 = d, the density that entered P = alpha d N'.
+ * Parameters: SAIS_MLP_PARAMS floats, W1 [128 x 16] at 0 (column 7 = b1, columns 8..15 zero),
+ *   W2 [128 x 144] at 2048 (column 128 = b2, columns 129..143 zero), w3 [128] at 20480, b3 at
+ *   20608, three unused.  Normalisation norm[16] = {mu[7], sd[7], y_mu, y_sd}: the network sees
+ *   (f - mu) / sd and predicts lambda = y_mu + y_sd u.
+ * The handle owns its device buffers (FP32 master weights, Adam moments, BF16 images of the
+ * weights, partial gradients); one stream at a time per handle. */
+#define SAIS_MLP_PARAMS 20612
+#define SAIS_MLP_FEATURES 8
+typedef struct sais_mlp sais_mlp;
+
+/* Features of every constraint of every instance, rows in instance order then k (host array
+ * of capacity_rows x 8 floats; *rows receives sum_j m_j).  Errors: SAIS_EINVAL when NULL or
+ * the capacity is short. */
+SAIS_API sais_status sais_constraint_features(const sais_problem *p, float *out,
+                                              int32_t capacity_rows, int32_t *rows);
+
+/* New network on `device`, weights drawn from `seed` (He-uniform hidden layers, zero biases),
+ * identity normalisation.  Errors: SAIS_EINVAL, SAIS_ENOMEM, SAIS_ECUDA. */
+SAIS_API sais_status sais_mlp_create(int32_t device, uint64_t seed, sais_mlp **out);
+SAIS_API sais_status sais_mlp_destroy(sais_mlp *m);
+
+/* Host copies in and out of the parameter vector and (if not NULL) the normalisation.
+ * set_params zeroes the padding entries, resets Adam and synchronises the device. */
+SAIS_API sais_status sais_mlp_set_params(sais_mlp *m, const float *params, const float *norm);
+SAIS_API sais_status sais_mlp_get_params(const sais_mlp *m, float *params, float *norm);
+
+/* Normalisation from a training set on the host: per-feature mean and population std of X
+ * (rows x 8) and of the targets y (std < 1e-6 is replaced by 1). */
+SAIS_API sais_status sais_mlp_fit_normalization(sais_mlp *m, const float *X, const float *y,
+                                                int32_t rows);
+
+/* lambda predicted for each row of X (device, rows x 8) into y (device, rows), not clamped. */
+SAIS_API sais_status sais_mlp_forward(const sais_mlp *m, const float *X, int32_t rows, float *y,
+                                      void *stream);
+
+/* Gradient of the mean squared error (1/rows) sum (u - t')^2 on normalised targets
+ * t' = (t - y_mu) / y_sd, into grad (device, SAIS_MLP_PARAMS floats), and the loss into *loss
+ * (device, may be NULL).  X, t on the device. */
+SAIS_API sais_status sais_mlp_gradient(sais_mlp *m, const float *X, const float *t, int32_t rows,
+                                       float *grad, float *loss, void *stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8 as FP32 values; bias corrections from those
+ * values) of that loss over all `rows` rows. */
+SAIS_API sais_status sais_mlp_train_step(sais_mlp *m, const float *X, const float *t,
+                                         int32_t rows, float lr, float *loss, void *stream);
+
+/* Device-side failures of the handle's kernels since the last call (SAIS_ETIMEOUT if a bounded
+ * wait gave up); resets the status word.  Synchronises the device. */
+SAIS_API sais_status sais_mlp_status(sais_mlp *m);
+
+/* Warm start: lambda[j m_stride + k] = max(0, network(features of constraint k of instance j))
+ * for every k < m_j (device array of count x m_stride floats; other entries untouched).
+ * Errors: SAIS_EINVAL (NULL, other device), SAIS_ECUDA. */
+SAIS_API sais_status sais_warm_start(sais_problem *p, const sais_mlp *m, float *lambda,
+                                     void *stream);
+
 /* Static text for a status code. */
 SAIS_API const char *sais_status_string(sais_status s);
 

@@ -62,6 +62,7 @@ struct HostInst {
     std::vector<float> spinc;              // npad x 4: a_0 (int bits), D, sum a, a_1 (int bits)
     std::vector<int32_t> b;                // m
     std::vector<float> hF;                 // npad
+    std::vector<float> feat;               // m x 8 features of the warm-start network
     const int32_t *W = nullptr;            // borrowed from the descriptor during creation
 };
 
@@ -184,6 +185,47 @@ sais_status build_host(const sais_problem_desc *d, HostInst &h) {
     }
     h.hF.assign(h.npad, 0.f);
     for (int32_t i = 0; i < n; ++i) h.hF[i] = (float)d->h[i];
+
+    // Features of the warm-start network (one row per constraint): capacity ratio, weight
+    // statistics in sigma_g units, profit statistics in sigma_f units, size and density.
+    double psum = 0.0, psq = 0.0, pcnt = 0.0;
+    for (int32_t i = 0; i < n; ++i) {
+        const double hv = (double)d->h[i];
+        if (hv != 0.0) {
+            psum += hv;
+            psq += hv * hv;
+            pcnt += 1.0;
+        }
+        if (h.has_w)
+            for (int32_t j = i + 1; j < n; ++j) {
+                const double wv = (double)d->W[(size_t)i * n + j];
+                if (wv != 0.0) {
+                    psum += wv;
+                    psq += wv * wv;
+                    pcnt += 1.0;
+                }
+            }
+    }
+    const double pmu = pcnt > 0.0 ? psum / pcnt : 0.0;
+    const double pvar = pcnt > 0.0 ? psq / pcnt - pmu * pmu : 0.0;
+    h.feat.assign((size_t)m * 8, 0.f);
+    for (int32_t k = 0; k < m; ++k) {
+        double as = 0.0, asq = 0.0;
+        for (int32_t i = 0; i < n; ++i) {
+            const double av = (double)d->A[(size_t)k * n + i];
+            as += av;
+            asq += av * av;
+        }
+        const double amu = as / n, avar = asq / n - amu * amu;
+        float *f = &h.feat[(size_t)k * 8];
+        f[0] = (float)(as > 0.0 ? std::min(1.0, (double)d->b[k] / as) : 1.0);
+        f[1] = (float)((double)h.sg * amu);
+        f[2] = (float)((double)h.sg * std::sqrt(std::max(avar, 0.0)));
+        f[3] = (float)((double)h.sf * pmu);
+        f[4] = (float)((double)h.sf * std::sqrt(std::max(pvar, 0.0)));
+        f[5] = (float)(n / 1000.0);
+        f[6] = (float)h.d;
+    }
     return SAIS_OK;
 }
 
@@ -217,6 +259,9 @@ struct sais_problem {
     void *pool = nullptr;         // one device allocation for all instance arrays
     InstDev *d_inst = nullptr;    // device array of count records (inside pool)
     int32_t *d_status = nullptr;  // device status word written by kernels (inside pool)
+    int32_t feat_rows = 0;        // sum of m over the instances
+    float *d_feat = nullptr;      // feat_rows x 8 warm-start features (inside pool)
+    int32_t *d_feat_dst = nullptr;   // row -> j m_stride + k (inside pool)
 
     // Launch groups of SAIS_AUTO: instances the blocked sampler runs, grouped by how it holds W
     // (resident, streamed, streamed hi/lo), and the rest on the plain sampler.  Members are kept
@@ -428,6 +473,8 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
     struct Off {
         size_t W, Wbf, Wlo, hF, acol, D, asum, spinc, b, so;
     };
+    int32_t feat_rows = 0;
+    for (const HostInst &h : p->host) feat_rows += h.m;
     std::vector<Off> off(count);
     // In a batch with any pair value above 256 every instance gets a lo image (zero where the
     // hi term is already exact), since one launch serves the whole batch.
@@ -467,6 +514,10 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
         o.so = cur;
         cur = align_up(cur + (size_t)(h.m + 1) * 4, 256);
     }
+    const size_t feat_off = cur;
+    cur = align_up(cur + (size_t)std::max(feat_rows, 1) * 8 * 4, 256);
+    const size_t dst_off = cur;
+    cur = align_up(cur + (size_t)std::max(feat_rows, 1) * 4, 256);
     std::vector<unsigned char> stage;
     try {
         stage.assign(cur, 0);
@@ -537,6 +588,19 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
         recs[j] = r;
         h.W = nullptr;
     }
+    {
+        float *F = reinterpret_cast<float *>(stage.data() + feat_off);
+        int32_t *Dst = reinterpret_cast<int32_t *>(stage.data() + dst_off);
+        int32_t r = 0;
+        for (int32_t j = 0; j < count; ++j)
+            for (int32_t k = 0; k < p->host[j].m; ++k, ++r) {
+                std::memcpy(F + (size_t)r * 8, &p->host[j].feat[(size_t)k * 8], 8 * 4);
+                Dst[r] = j * p->m_stride + k;
+            }
+    }
+    p->feat_rows = feat_rows;
+    p->d_feat = reinterpret_cast<float *>(base + feat_off);
+    p->d_feat_dst = reinterpret_cast<int32_t *>(base + dst_off);
     ce = cudaMemcpy(p->pool, stage.data(), cur, cudaMemcpyHostToDevice);
     cudaSetDevice(prev);
     if (ce != cudaSuccess) {
@@ -1154,6 +1218,30 @@ sais_status sais_autotune(sais_problem *p, int32_t chains, int32_t sweeps, sais_
         return fail((sais_status)v, "a sampler kernel reported: %s", sais_status_string((sais_status)v));
     }
     return SAIS_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+sais_status sais_constraint_features(const sais_problem *p, float *out, int32_t capacity_rows,
+                                     int32_t *rows) {
+    if (!p || !out || !rows) return fail(SAIS_EINVAL, "NULL argument");
+    *rows = p->feat_rows;
+    if (capacity_rows < p->feat_rows)
+        return fail(SAIS_EINVAL, "capacity of %d rows, %d needed", capacity_rows, p->feat_rows);
+    size_t r = 0;
+    for (const HostInst &h : p->host)
+        for (int32_t k = 0; k < h.m; ++k, ++r)
+            std::memcpy(out + r * 8, &h.feat[(size_t)k * 8], 8 * 4);
+    return SAIS_OK;
+}
+
+sais_status sais_warm_start(sais_problem *p, const sais_mlp *m, float *lambda, void *stream) {
+    if (!p || !m || !lambda) return fail(SAIS_EINVAL, "NULL argument");
+    DeviceGuard dg(p->device);
+    return mlp_warm_start_launch(m, p->d_feat, p->d_feat_dst, p->feat_rows, lambda, p->device,
+                                 static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -134,5 +134,8 @@ sais_status enqueue_sample_internal(sais_problem *p, const sais_sample_params *p
                                    cudaStream_t stream);
 sais_status check_sample_params_internal(const sais_problem *p, const sais_sample_params *prm);
 sais_status set_error(sais_status s, const char *fmt, ...);
+// Inference launch of the warm-start network: lambda[dst[r]] = max(0, y(feat row r)).
+sais_status mlp_warm_start_launch(const sais_mlp *m, const float *feat, const int32_t *dst,
+                                  int32_t rows, float *lambda, int device, cudaStream_t st);
 
 }  // namespace sais

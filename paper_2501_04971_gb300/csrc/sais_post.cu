@@ -44,7 +44,6 @@ __global__ void __launch_bounds__(kPostThreads) post_kernel(PostArgs a) {
     __shared__ long long red[kWarps];
     __shared__ int redi[kWarps];
     __shared__ long long gsum[kMaxConstraints];
-    __shared__ long long s_best;
     __shared__ int s_best_chain;
     __shared__ int s_copy;
 
@@ -101,7 +100,6 @@ __global__ void __launch_bounds__(kPostThreads) post_kernel(PostArgs a) {
                 a.best_cost[j] = b;
                 a.best_iter[j] = (int)iter;
                 a.best_chain[j] = bi;
-                s_best = b;
                 s_best_chain = bi;
                 s_copy = 1;
             }

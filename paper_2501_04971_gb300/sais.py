@@ -85,7 +85,19 @@ _SIGS = {
     "sais_autotune": [_P, _i32, _i32, ctypes.POINTER(sais_tuning), _P],
     "sais_solve_noalloc": [_P, ctypes.POINTER(sais_solve_params),
                            ctypes.POINTER(sais_solve_result), _P],
+    "sais_constraint_features": [_P, _P, _i32, ctypes.POINTER(_i32)],
+    "sais_mlp_create": [_i32, _u64, ctypes.POINTER(_P)],
+    "sais_mlp_destroy": [_P],
+    "sais_mlp_set_params": [_P, _P, _P],
+    "sais_mlp_get_params": [_P, _P, _P],
+    "sais_mlp_fit_normalization": [_P, _P, _P, _i32],
+    "sais_mlp_forward": [_P, _P, _i32, _P, _P],
+    "sais_mlp_gradient": [_P, _P, _P, _i32, _P, _P, _P],
+    "sais_mlp_train_step": [_P, _P, _P, _i32, _f32, _P, _P],
+    "sais_mlp_status": [_P],
+    "sais_warm_start": [_P, _P, _P, _P],
 }
+MLP_PARAMS, MLP_FEATURES = 20612, 8
 EXPORTS = list(_SIGS) + ["sais_status_string", "sais_last_error"]
 
 _lib = None
@@ -206,6 +218,18 @@ def sais_autotune(h, chains: int, sweeps: int, stream_ptr):
     return out
 
 
+def sais_constraint_features(h, rows_cap: int) -> np.ndarray:
+    out = np.zeros((max(rows_cap, 1), MLP_FEATURES), np.float32)
+    rows = _i32(0)
+    _check(lib().sais_constraint_features(h, out.ctypes.data_as(_P), rows_cap,
+                                          ctypes.byref(rows)), "sais_constraint_features")
+    return out[:rows.value]
+
+
+def sais_warm_start(h, mlp_h, lam_ptr, stream_ptr):
+    _check(lib().sais_warm_start(h, mlp_h, lam_ptr, stream_ptr), "sais_warm_start")
+
+
 def sais_synchronize(h, stream_ptr):
     _check(lib().sais_synchronize(h, stream_ptr), "sais_synchronize")
 
@@ -309,6 +333,18 @@ class Problem:
                 "size": list(t.group_size)[:g], "ms": list(t.group_ms)[:g],
                 "spin_updates": list(t.group_spin_updates)[:g]}
 
+    @property
+    def feature_rows(self) -> int:
+        return int(sum(s.m for s in self.scalars))
+
+    def features(self) -> np.ndarray:
+        """sais_constraint_features: (sum_j m_j) x 8 host array."""
+        return sais_constraint_features(self.handle, self.feature_rows)
+
+    def warm_start(self, mlp: "MLP", lam, stream=None):
+        """sais_warm_start: lam[j*m_stride + k] = max(0, network prediction)."""
+        sais_warm_start(self.handle, mlp.handle, _P(lam.data_ptr()), _stream_ptr(stream))
+
     def synchronize(self, stream=None):
         """sais_synchronize: wait for the stream, raise SaisError on a device-side timeout."""
         sais_synchronize(self.handle, _stream_ptr(stream))
@@ -410,3 +446,72 @@ def unpack_bits(words: np.ndarray, nspins: int) -> np.ndarray:
     w = np.ascontiguousarray(words).view(np.uint32)
     bits = (w[..., :, None] >> np.arange(32, dtype=np.uint32)) & 1
     return bits.reshape(*w.shape[:-1], -1)[..., :nspins].astype(np.uint8)
+
+
+class MLP:
+    """The warm-start network (sais_mlp_*): device-resident BF16/FP32 parameters, Adam state."""
+
+    def __init__(self, seed: int = 0, device: int = 0):
+        h = _P()
+        _check(lib().sais_mlp_create(device, seed, ctypes.byref(h)), "sais_mlp_create")
+        self.handle, self.device = h, device
+
+    def close(self):
+        if self.handle:
+            lib().sais_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        p = np.zeros(MLP_PARAMS, np.float32)
+        n = np.zeros(16, np.float32)
+        _check(lib().sais_mlp_get_params(self.handle, p.ctypes.data_as(_P), n.ctypes.data_as(_P)),
+               "sais_mlp_get_params")
+        return p, n
+
+    def set_params(self, params, norm=None):
+        p = np.ascontiguousarray(params, np.float32)
+        assert p.size == MLP_PARAMS
+        n = None if norm is None else np.ascontiguousarray(norm, np.float32)
+        _check(lib().sais_mlp_set_params(self.handle, p.ctypes.data_as(_P),
+                                         None if n is None else n.ctypes.data_as(_P)),
+               "sais_mlp_set_params")
+
+    def fit_normalization(self, X, y):
+        X = np.ascontiguousarray(X, np.float32)
+        y = np.ascontiguousarray(y, np.float32)
+        _check(lib().sais_mlp_fit_normalization(self.handle, X.ctypes.data_as(_P),
+                                                y.ctypes.data_as(_P), X.shape[0]),
+               "sais_mlp_fit_normalization")
+
+    def forward(self, X, out=None, stream=None):
+        """X: device float32 tensor (rows x 8); returns the device predictions (rows)."""
+        import torch
+        y = out if out is not None else torch.empty(X.shape[0], dtype=torch.float32,
+                                                    device=X.device)
+        _check(lib().sais_mlp_forward(self.handle, _P(X.data_ptr()), X.shape[0],
+                                      _P(y.data_ptr()), _stream_ptr(stream)), "sais_mlp_forward")
+        return y
+
+    def gradient(self, X, t, stream=None):
+        import torch
+        g = torch.empty(MLP_PARAMS, dtype=torch.float32, device=X.device)
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        _check(lib().sais_mlp_gradient(self.handle, _P(X.data_ptr()), _P(t.data_ptr()),
+                                       X.shape[0], _P(g.data_ptr()), _P(loss.data_ptr()),
+                                       _stream_ptr(stream)), "sais_mlp_gradient")
+        return g, loss
+
+    def train_step(self, X, t, lr: float, loss=None, stream=None):
+        _check(lib().sais_mlp_train_step(self.handle, _P(X.data_ptr()), _P(t.data_ptr()),
+                                         X.shape[0], lr,
+                                         None if loss is None else _P(loss.data_ptr()),
+                                         _stream_ptr(stream)), "sais_mlp_train_step")
+
+    def status(self):
+        _check(lib().sais_mlp_status(self.handle), "sais_mlp_status")
