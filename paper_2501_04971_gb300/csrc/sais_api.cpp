@@ -252,6 +252,7 @@ struct sais_problem {
     int device = 0;
     int count = 0;
     int max_spins = 0, max_npad = 0, max_npad_w = 0, words = 0, m_stride = 1, max_m = 0;
+    int max_n = 0;
     bool any_w = false;
     std::vector<HostInst> host;   // host copies (W pointer cleared after creation)
     bool any_lo = false;          // some instance needs the BF16 hi/lo split
@@ -271,9 +272,10 @@ struct sais_problem {
         int variant = SAIS_PLAIN;
         bool stream_w = false, hilo = false;
         int block_k = 16, cpb = 32;
-        int max_m = 0, max_npad = 0, max_npad_w = 0, words = 0;
+        int max_m = 0, max_npad = 0, max_npad_w = 0, words = 0, max_n = 0;
         bool any_w = false;
         bool blocked_ok = false;   // every member fits the blocked sampler
+        bool pair = false;         // blocked sampler on CTA pairs (items beyond one SM's TMEM)
         std::vector<int> members;
         size_t work_off = 0, nwork = 0;
         double tuned_ms = 0.0;
@@ -290,12 +292,14 @@ struct sais_problem {
 namespace {
 
 // SAIS_AUTO grouping (see struct sais_problem).  Keys: 1 blocked with W resident, 2 streamed,
-// 3 streamed hi/lo; plain instances split by whether they have W and by padded N' (bucket of
-// 128 spins), so each plain group sizes its shared memory for its own largest member.
+// 3 streamed hi/lo, 4 CTA-pair blocked, 5 CTA-pair hi/lo; plain instances split by whether they
+// have W and by padded N' (bucket of 128 spins), so each plain group sizes its shared memory for
+// its own largest member.
 void build_groups(sais_problem *p) {
     p->groups.clear();
     auto key_of = [&](const HostInst &h) -> int {
         const bool eligible = h.has_w && h.m <= kMaxBlockedConstraints && h.npad + 16 <= 512;
+        if (!eligible && pair_eligible(h.n, h.m, h.has_w)) return h.lo_own ? 5 : 4;
         if (!eligible) return 100 + (h.has_w ? 1000 : 0) + (h.npad + 127) / 128;
         if (h.lo_own) return 3;
         return blocked_smem_bytes(h.npad, h.words, 16, false, false) > kMaxSmemPerBlock ? 2 : 1;
@@ -319,14 +323,16 @@ void build_groups(sais_problem *p) {
             g.members.push_back(j);
             g.max_m = std::max(g.max_m, h.m);
             g.max_npad = std::max(g.max_npad, h.npad);
+            g.max_n = std::max(g.max_n, h.n);
             if (h.has_w) g.max_npad_w = std::max(g.max_npad_w, h.npad);
             g.words = std::max(g.words, h.words);
             g.any_w = g.any_w || h.has_w;
         }
         g.variant = key >= 100 ? SAIS_PLAIN : SAIS_BLOCKED;
         g.blocked_ok = key < 100;
-        g.stream_w = key == 2 || key == 3;
-        g.hilo = key == 3;
+        g.pair = key == 4 || key == 5;
+        g.stream_w = key >= 2 && key <= 5;
+        g.hilo = key == 3 || key == 5;
         auto cost = [&](int j) {
             const HostInst &h = p->host[j];
             return (double)h.nprime * (h.has_w ? (double)h.npad : (double)std::max(1, h.m));
@@ -386,6 +392,8 @@ cudaError_t launch_group(const sais_problem *p, const sais_problem::Group &g, co
     SampleArgs ga = a;
     ga.work = p->d_work + 2 * g.work_off;
     ga.nwork = (int32_t)g.nwork;
+    if (g.variant == SAIS_BLOCKED && g.pair)
+        return launch_pair_sampler(ga, g.max_m, g.max_n, g.words, g.hilo, p->d_status, polls, st);
     if (g.variant == SAIS_BLOCKED)
         return launch_blocked_sampler(ga, g.max_m, g.max_npad, g.words, g.block_k, g.stream_w,
                                       g.hilo, p->d_status, polls, st);
@@ -459,6 +467,7 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
         const HostInst &h = p->host[j];
         p->max_spins = std::max(p->max_spins, h.nprime);
         p->max_npad = std::max(p->max_npad, h.npad);
+        p->max_n = std::max(p->max_n, h.n);
         if (h.has_w) p->max_npad_w = std::max(p->max_npad_w, h.npad);
         p->max_m = std::max(p->max_m, h.m);
         p->any_w = p->any_w || h.has_w;
@@ -762,11 +771,24 @@ sais_status enqueue_sample(sais_problem *p, const sais_sample_params *prm, const
             return fail(SAIS_EUNSUPPORTED,
                         "blocked sampler: m = %d constraints (at most %d; use SAIS_PLAIN)",
                         p->max_m, kMaxBlockedConstraints);
-        if (p->max_npad + k > 512)
-            return fail(SAIS_EUNSUPPORTED,
-                        "blocked sampler: N'=%d (padded %d) plus the %d operand columns exceed "
-                        "512 TMEM columns",
-                        p->max_spins, p->max_npad, k);
+        if (p->max_npad + k > 512) {
+            // Fields split over a CTA pair (thread-block cluster of two).
+            for (int jj = 0; jj < p->count; ++jj) {
+                const HostInst &h = p->host[jj];
+                if (!pair_eligible(h.n, h.m, h.has_w))
+                    return fail(SAIS_EUNSUPPORTED,
+                                "blocked sampler: N'=%d exceeds one SM's 512 TMEM columns and "
+                                "instance %d (n=%d) is outside the CTA-pair range "
+                                "(128 <= n rounded up to 64 <= 1024)",
+                                p->max_spins, jj, h.n);
+            }
+            if (k != 16)
+                return fail(SAIS_EUNSUPPORTED, "blocked sampler on CTA pairs: block_k = 16 only");
+            e = launch_pair_sampler(a, p->max_m, p->max_n, p->words, p->any_lo, p->d_status,
+                                    (long long)prm->debug_wait_polls, st);
+            if (e != cudaSuccess) return fail(SAIS_ECUDA, "sampler launch: %s", cudaGetErrorString(e));
+            return SAIS_OK;
+        }
         // W resident in shared memory when it fits and needs one BF16 term; otherwise its
         // per-block tiles are streamed (and pair values above 256 use the hi/lo split).
         const bool hilo = p->any_lo;

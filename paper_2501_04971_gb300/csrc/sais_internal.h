@@ -110,6 +110,12 @@ cudaError_t launch_blocked_sampler(const SampleArgs &a, int max_m, int max_npad,
                                    cudaStream_t stream);
 size_t blocked_smem_bytes(int max_npad, int max_words, int block_k, bool stream_w, bool hilo);
 size_t plain_smem_bytes(int max_npad, int max_words, bool any_w, int cpb);
+// Blocked sampler on a CTA pair (thread-block cluster of two) for instances whose items do not
+// fit one SM's TMEM: W present, m <= 8, 128 <= n rounded up to 64 <= 1024.
+bool pair_eligible(int n, int m, bool has_w);
+size_t pair_smem_bytes(int max_n, int max_words, bool hilo);
+cudaError_t launch_pair_sampler(const SampleArgs &a, int max_m, int max_n, int max_words, bool hilo,
+                                int32_t *status, long long dec_wait_polls, cudaStream_t st);
 constexpr size_t kMaxSmemPerBlock = 232448;   // 227 KB opt-in per CTA on sm_103
 cudaError_t launch_post(const PostArgs &a, cudaStream_t stream);
 cudaError_t launch_advance_iter(uint32_t *iter_dev, cudaStream_t stream);

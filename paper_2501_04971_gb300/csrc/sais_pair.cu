@@ -1,0 +1,730 @@
+// sais_pair.cu -- the blocked p-bit sampler on a pair of CTAs (a thread-block cluster of two), for
+// instances whose objective field does not fit one SM's tensor memory.
+//
+// The blocked sampler keeps F (objective field, FP32 exact integers) for 128 chains in TMEM with
+// one column per spin, so one CTA holds at most 512 spins.  Here the item columns are split in
+// two halves, [0, h) in CTA 0 and [h, n_pad) in CTA 1 of the cluster; both CTAs run the same 128
+// chains.  The Gibbs sweep of Sec. III-B stays sequential, spin by spin:
+//   * a block of K = 16 spins inside CTA p's half is decided by CTA p (it holds their fields);
+//     its flips Delta (BF16 -1/0/+1, the MMA's A operand, 128 x 16) are written into both
+//     CTAs' shared memory (the peer's through distributed shared memory) and the peer is
+//     signalled with remote mbarrier arrivals;
+//   * both CTAs then apply the rank-16 update to their own half of F with tcgen05.mma,
+//     F[:, half] += W[half, blk] Delta[blk, :], W streamed per block through a tile ring; each
+//     CTA's MMA completion is multicast to both CTAs' "slot free" barrier, which gates the
+//     reuse of the Delta slot two blocks later;
+//   * the CTA that does not decide a block only follows the chains' state: it applies the
+//     block's flips to its copy of x and of the constraint values;
+//   * blocks of slack spins (past the items; W is zero there, F = 0) are decided by both CTAs
+//     identically (same state, same noise), with no exchange and no MMA.
+// So the two CTAs always hold identical chain states, and the decisions are those of the plain
+// sampler bit for bit.  At the end CTA 1 sends its part of sum_i x_i F_i to CTA 0 through
+// distributed shared memory and CTA 0 writes the outputs.
+//
+// Warps 0-3 decide or follow (warp w owns chains 32w..32w+31 = TMEM lanes); warps 4-7 produce
+// the noise two blocks ahead, and lane 0 of warp 4 streams the W tiles.  Every wait is bounded
+// (on expiry: SAIS_ETIMEOUT, stop, drain, free TMEM); every thread of both CTAs reaches the two
+// cluster barriers (after initialisation, before the final readout).
+#include "sais_device.cuh"
+#include "sais_tc.cuh"
+
+namespace sais {
+namespace {
+
+constexpr int kPK = 16;                 // spins per block
+constexpr int kPLanes = 128;            // chains per CTA pair
+constexpr int kPThreads = 256;
+constexpr int kPNoiseWarp0 = 4;
+constexpr uint32_t kPRing = 3;          // W tile slots
+constexpr long long kPWaitCycles = 8000000000ll;
+constexpr uint32_t kASlotBytes = kPLanes * kPK * 2;   // 4096
+
+// bars: 0 never completed (timeout test), 1 own MMAs done (one phase per item block),
+// 2..3 Delta slot free (2 arrivals: both CTAs' MMAs), 4..5 Delta slot filled by the peer
+// (4 arrivals: its decision warps), 6..9 drain, 10..17 noise full (2 q + slot),
+// 18..25 noise consumed, 26..28 tile full, 29..31 tile free.
+constexpr int kBars = 32;
+
+__device__ __forceinline__ bool p_expired(long long n, long long polls, unsigned long long t0) {
+    return polls > 0 ? n >= polls : (long long)(clock64() - t0) > kPWaitCycles;
+}
+
+template <bool kCluster>
+__device__ __forceinline__ bool p_wait_warp(uint64_t *bar, uint32_t parity,
+                                            volatile int *abort_flag, int32_t *status,
+                                            long long polls) {
+    auto tw = [&]() {
+        return kCluster ? tc::mbar_try_wait_cluster(bar, parity) : tc::mbar_try_wait(bar, parity);
+    };
+    if (__all_sync(0xffffffffu, tw())) return true;
+    const unsigned long long t0 = clock64();
+    for (long long n = 0;; ++n) {
+        if (__all_sync(0xffffffffu, tw())) return true;
+        const bool give_up = *abort_flag != 0 || p_expired(n, polls, t0);
+        if (__any_sync(0xffffffffu, give_up)) {
+            if ((threadIdx.x & 31) == 0 && !*abort_flag) {
+                *abort_flag = 1;
+                if (status) atomicExch(status, (int32_t)SAIS_ETIMEOUT);
+            }
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ bool p_wait_one(uint64_t *bar, uint32_t parity,
+                                           volatile int *abort_flag, int32_t *status) {
+    if (tc::mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = clock64();
+    for (;;) {
+        if (tc::mbar_try_wait(bar, parity)) return true;
+        if (abort_flag && *abort_flag) return false;
+        if ((long long)(clock64() - t0) > kPWaitCycles) {
+            if (abort_flag) *abort_flag = 1;
+            if (status) atomicExch(status, (int32_t)SAIS_ETIMEOUT);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t p_bf16_pm1(int d) {
+    return d > 0 ? 0x3F80u : (d < 0 ? 0xBF80u : 0u);
+}
+// Flip of a BF16 -1/0/+1 code.
+__device__ __forceinline__ int p_code(uint32_t h) { return h == 0x3F80u ? 1 : (h == 0xBF80u ? -1 : 0); }
+
+// Item columns of the pair: n_pad = n rounded up to 64, CTA 0 holds [0, h), CTA 1 [h, n_pad).
+__host__ __device__ inline int pair_npad(int n) { return (n + 63) / 64 * 64; }
+__host__ __device__ inline int pair_half(int npi) { return ((npi / 2) + 63) / 64 * 64; }
+
+template <int MC, bool kHiLo>
+__global__ void __launch_bounds__(kPThreads, 1)
+    pair_sampler_kernel(SampleArgs a, int32_t *status, long long polls, uint32_t tmem_cols,
+                        uint32_t slot_cap) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    constexpr int kPreM = MC < 2 ? MC : 2;
+    const uint32_t rank = tc::cluster_ctarank(), peer = rank ^ 1u;
+    const int pair_id = blockIdx.x >> 1;
+    const int j = a.work ? a.work[2 * pair_id] : (int)blockIdx.y;
+    const int grp = a.work ? a.work[2 * pair_id + 1] : pair_id;
+    const InstDev *__restrict__ ip = a.inst + j;
+    const int m = ip->m, nprime = ip->nprime, npad = ip->npad, words = ip->words;
+    const int npi = pair_npad(ip->n), h = pair_half(npi);
+    const int col0 = rank == 0 ? 0 : h, ncol = rank == 0 ? h : npi - h;
+    const int nb = (nprime + kPK - 1) / kPK;      // blocks per sweep
+    const int nbi = min(npi / kPK, nb);           // item blocks per sweep (they come first)
+    const int split_b = h / kPK;                  // item blocks [0, split_b) belong to CTA 0
+    const uint32_t tile_bytes = 2u * (uint32_t)ncol * 16u;   // one term: 2 chunks x ncol rows
+    const uint32_t slot_bytes = tile_bytes * (kHiLo ? 2u : 1u);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    unsigned char *ring = smem;                                       // kPRing x slot_cap
+    unsigned char *aslot = smem + kPRing * slot_cap;                  // 2 x 4096
+    uint32_t *xs = reinterpret_cast<uint32_t *>(aslot + 2 * kASlotBytes);
+    float *thbuf = reinterpret_cast<float *>(xs + words * kPLanes);   // [2][K][128]
+    long long *part = reinterpret_cast<long long *>(thbuf + 2 * kPK * kPLanes);   // [2][128]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(part + 2 * kPLanes);
+    uint32_t *arrivals = reinterpret_cast<uint32_t *>(bars + kBars);
+    uint32_t *tmem_slot = arrivals + 2;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    if (threadIdx.x == kPLanes) {
+        for (int i = 0; i < kBars; ++i) {
+            const uint32_t cnt = (i == 2 || i == 3) ? 2u : ((i == 4 || i == 5) ? 4u : 1u);
+            tc::mbar_init(&bars[i], cnt);
+        }
+        arrivals[0] = arrivals[1] = 0u;
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+        tc::fence_proxy_async_smem();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tmem_slot, tmem_cols);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    // Both CTAs' barriers exist before either signals the other.
+    tc::cluster_sync();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t iter = a.iter_dev ? *a.iter_dev : a.iter;
+
+    if (warp >= kPNoiseWarp0) {
+        const int q = warp - kPNoiseWarp0;
+        const int r = q * 32 + lane;
+        const uint32_t chain = (uint32_t)(grp * kPLanes + r);
+        const uint64_t seed = a.seed + (uint64_t)j;
+        const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
+        const uint32_t total = (uint32_t)a.sweeps * (uint32_t)nb;
+        uint32_t tiles = 0;   // item blocks whose tile was issued
+        for (uint32_t it = 0; it < total; ++it) {
+            const uint32_t slot = it & 1u;
+            if (it >= 2 && !p_wait_warp<false>(&bars[18 + 2 * q + slot], ((it >> 1) + 1u) & 1u,
+                                               abort_flag, status, 0))
+                break;
+            const uint32_t t = it / (uint32_t)nb;
+            const int b = (int)(it % (uint32_t)nb);
+            const int s0 = b * kPK;
+            if (q == 0 && b < nbi) {
+                // W tile of this item block: rows [col0, col0 + ncol) of the block's two column
+                // chunks (and of the lo image), into ring slot ib % 3 once its previous use is
+                // done (this CTA's MMAs of item block ib - 3).
+                bool okt = true;
+                const uint32_t ib = t * (uint32_t)nbi + (uint32_t)b;
+                if (lane == 0) {
+                    const uint32_t ts = ib % kPRing;
+                    if (ib >= kPRing)
+                        okt = p_wait_one(&bars[29 + ts], ((ib / kPRing) - 1u) & 1u, abort_flag,
+                                         status);
+                    if (okt) {
+                        unsigned char *dst = ring + ts * slot_cap;
+                        tc::mbar_expect_tx(&bars[26 + ts], slot_bytes);
+#pragma unroll
+                        for (int term = 0; term < (kHiLo ? 2 : 1); ++term) {
+                            const unsigned char *src = reinterpret_cast<const unsigned char *>(
+                                term ? ip->Wbf_lo : ip->Wbf);
+#pragma unroll
+                            for (int c = 0; c < 2; ++c)
+                                tc::bulk_g2s(dst + term * tile_bytes + (uint32_t)c * ncol * 16u,
+                                             src + ((size_t)((s0 >> 3) + c) * npad + col0) * 16,
+                                             (uint32_t)ncol * 16u, &bars[26 + ts]);
+                        }
+                        ++tiles;
+                    }
+                }
+                if (__shfl_sync(0xffffffffu, okt ? 1 : 0, 0) == 0) break;
+            }
+            float *tb = thbuf + slot * kPK * kPLanes;
+#pragma unroll
+            for (int g4 = 0; g4 < kPK / 4; ++g4) {
+                const uint4 rw = philox4x32_10(
+                    make_uint4((uint32_t)((s0 >> 2) + g4), t, chain, iter), key0, key1);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const bool real = s0 + 4 * g4 + e < nprime;
+                    tb[(4 * g4 + e) * kPLanes + r] = real ? theta_of_word(word_of(rw, e)) : -1e30f;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&bars[10 + 2 * q + slot]);
+        }
+        if (q == 0 && lane == 0) {
+            for (uint32_t ts = 0; ts < kPRing && ts < tiles; ++ts) {
+                const uint32_t uses = (tiles - ts + kPRing - 1u) / kPRing;
+                p_wait_one(&bars[26 + ts], (uses - 1u) & 1u, nullptr, status);
+            }
+        }
+        __syncwarp();
+    } else {
+        const int r = threadIdx.x;
+        const int chain = grp * kPLanes + r;
+        const bool valid = chain < (a.inst_chains ? a.inst_chains[j] : a.chains);
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        const uint64_t seed = a.seed + (uint64_t)j;
+        const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
+        const float sf = ip->sigma_f, sg = ip->sigma_g, kappa = ip->kappa;
+        const double psg2 = ip->psg2;
+        const float *__restrict__ hF = ip->hF;
+        const int32_t *__restrict__ acol = ip->acol;
+        const float *__restrict__ Dv = ip->D;
+        const float *__restrict__ asum = ip->asum;
+        const float *lam = a.lambda + (size_t)j * a.m_stride;
+        const uint32_t a_own = tc::smem_u32(aslot);
+        const uint32_t a_peer = tc::mapa(a_own, peer);
+        const uint32_t rowoff = (uint32_t)((r >> 3) * 128 + (r & 7) * 16);   // K-major A row
+
+        for (int w = 0; w < words; ++w) xs[w * kPLanes + r] = 0u;
+        for (int c0 = 0; c0 < ncol; c0 += 32) {
+            float v[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = __ldg(hF + col0 + c0 + i);
+            tc::tmem_st32(lane_addr + (uint32_t)c0, v);
+        }
+        tc::tc_fence_before();
+
+        int32_t g[MC];
+        float c[MC], cA[MC];
+        float Mmax = 0.f;
+#pragma unroll
+        for (int k = 0; k < MC; ++k) {
+            if (k < m) {
+                cA[k] = __double2float_rn((double)sg * (double)lam[k]);
+                g[k] = -ip->b[k];
+                c[k] = fmaf(kappa, (float)g[k], cA[k]);
+                Mmax = fmaxf(Mmax, fmaf(fabsf(kappa), fabsf((float)g[k]), fabsf(cA[k])));
+            } else {
+                cA[k] = 0.f;
+                g[k] = 0;
+                c[k] = 0.f;
+            }
+        }
+        const float errk = field_err_factor(m);
+        bool ok = polls > 0 ? p_wait_warp<false>(&bars[0], 0, abort_flag, status, polls) : true;
+        uint32_t it = 0, ib = 0, cons0 = 0u, cons1 = 0u;   // Delta slots consumed, per slot
+        float th[kPK];
+        for (int t = 0; ok && t < a.sweeps; ++t) {
+            const float beta = beta_of_sweep(a.beta_max, t, a.sweeps);
+            const float hb = 0.5f * beta;
+            const float ez = hb * errk;
+            for (int b = 0; b < nb; ++b) {
+                const int s0 = b * kPK;
+                const bool item = b < nbi;
+                const int owner = !item ? 2 : (b < split_b ? 0 : 1);
+                const bool decide = owner == 2 || owner == (int)rank;
+                const uint32_t slot = it & 1u;
+                if (!p_wait_warp<false>(&bars[10 + 2 * warp + slot], (it >> 1) & 1u, abort_flag,
+                                        status, polls)) {
+                    ok = false;
+                    break;
+                }
+                if (decide) {
+#pragma unroll
+                    for (int ii = 0; ii < kPK; ++ii) th[ii] = thbuf[(slot * kPK + ii) * kPLanes + r];
+                }
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&bars[18 + 2 * warp + slot]);
+                const uint32_t ts = ib % kPRing;
+                const unsigned char *wblk = ring + ts * slot_cap;
+                if (item && !p_wait_warp<false>(&bars[26 + ts], (ib / kPRing) & 1u, abort_flag,
+                                                status, polls)) {
+                    ok = false;
+                    break;
+                }
+                const int wi = s0 >> 5, sb = s0 & 31;
+                uint32_t xw = xs[wi * kPLanes + r];
+                const uint32_t xold = xw;
+                const uint32_t as = ib & 1u;   // Delta slot of this item block
+                // Both CTAs wait, at every item block, for the slot's previous use (block ib - 2)
+                // to be done by both CTAs' MMAs: the owner before overwriting it, the follower so
+                // that it observes every phase of the barrier in order.
+                if (item && ib >= 2 && !p_wait_warp<true>(&bars[2 + as], ((ib - 2u) >> 1) & 1u,
+                                                          abort_flag, status, polls)) {
+                    ok = false;
+                    break;
+                }
+                if (decide) {
+                    float Dp[kPK], Sp[kPK];
+                    int32_t Ap[kPK][kPreM];
+#pragma unroll
+                    for (int ii = 0; ii < kPK; ++ii) {
+                        const float4 sc = __ldg(ip->spinc + s0 + ii);
+                        Ap[ii][0] = __float_as_int(sc.x);
+                        Dp[ii] = sc.y;
+                        Sp[ii] = sc.z;
+                        if (kPreM > 1) Ap[ii][kPreM > 1 ? 1 : 0] = __float_as_int(sc.w);
+                    }
+                    float Fr[kPK];
+                    if (item) {
+                        if (ib > 0) {
+                            if (!p_wait_warp<false>(&bars[1], (ib - 1u) & 1u, abort_flag, status,
+                                                    polls)) {
+                                ok = false;
+                                break;
+                            }
+                            tc::tc_fence_after();
+                        }
+                        tc::tmem_ld16(lane_addr + (uint32_t)(s0 - col0), Fr);
+                    } else {
+#pragma unroll
+                        for (int ii = 0; ii < kPK; ++ii) Fr[ii] = 0.f;   // slack spins: F = 0
+                    }
+                    int32_t g0[MC];
+                    float cb[MC];
+                    const float M0 = Mmax;
+#pragma unroll
+                    for (int k = 0; k < MC; ++k) {
+                        g0[k] = g[k];
+                        cb[k] = c[k];
+                    }
+                    bool near_tie = false;
+#pragma unroll
+                    for (int ii = 0; ii < kPK; ++ii) {
+                        const int s = s0 + ii;
+                        uint4 wrow[2], wrlo[2];
+                        if (item) {
+#pragma unroll
+                            for (int cc = (ii + 1) >> 3; cc < 2; ++cc) {
+                                const size_t off = ((size_t)cc * ncol + (s - col0)) * 16;
+                                wrow[cc] = *reinterpret_cast<const uint4 *>(wblk + off);
+                                if (kHiLo)
+                                    wrlo[cc] = *reinterpret_cast<const uint4 *>(wblk + tile_bytes + off);
+                            }
+                        }
+                        const float Fi = Fr[ii];
+                        const int xi = (xw >> (sb + ii)) & 1;
+                        int32_t ak[MC];
+                        float acc = sf * Fi;
+                        const float tabs = fabsf(acc);
+#pragma unroll
+                        for (int k = 0; k < MC; ++k) {
+                            if (k < kPreM)
+                                ak[k] = Ap[ii][k < kPreM ? k : 0];
+                            else
+                                ak[k] = (k < m) ? __ldg(acol + (size_t)s * m + k) : 0;
+                            acc = fmaf(-(float)ak[k], c[k], acc);
+                        }
+                        const float Di = Dp[ii];
+                        acc = fmaf(xi ? 1.f : -1.f, Di, acc);
+                        const float z = hb * acc;
+                        const float theta = th[ii];
+                        const float y = z + theta;
+                        const float bound = ez * (tabs + Sp[ii] * Mmax + Di) +
+                                            kThetaRelErr * fabsf(theta) + kThetaAbsErr;
+                        const int xn = y > 0.f;
+                        near_tie |= !(fabsf(y) > bound);
+                        const int d = xn - xi;
+                        xw ^= (uint32_t)(d != 0) << (sb + ii);
+                        Mmax = 0.f;
+#pragma unroll
+                        for (int k = 0; k < MC; ++k) {
+                            if (k < m) {
+                                g[k] += ak[k] * d;
+                                c[k] = fmaf(kappa, (float)g[k], cA[k]);
+                                Mmax = fmaxf(Mmax, fmaf(fabsf(kappa), fabsf((float)g[k]),
+                                                        fabsf(cA[k])));
+                            }
+                        }
+                        if (item && ii + 1 < kPK && __any_sync(0xffffffffu, d != 0)) {
+                            const float df = (float)d;
+#pragma unroll
+                            for (int cc = (ii + 1) >> 3; cc < 2; ++cc) {
+                                const uint32_t wv[4] = {wrow[cc].x, wrow[cc].y, wrow[cc].z,
+                                                        wrow[cc].w};
+                                uint32_t wl[4] = {0u, 0u, 0u, 0u};
+                                if (kHiLo) {
+                                    wl[0] = wrlo[cc].x;
+                                    wl[1] = wrlo[cc].y;
+                                    wl[2] = wrlo[cc].z;
+                                    wl[3] = wrlo[cc].w;
+                                }
+#pragma unroll
+                                for (int e = 0; e < 8; ++e) {
+                                    const int jj = cc * 8 + e;
+                                    if (jj > ii) {
+                                        const uint32_t bits = (e & 1) ? (wv[e >> 1] & 0xFFFF0000u)
+                                                                      : (wv[e >> 1] << 16);
+                                        float w = __uint_as_float(bits);
+                                        if (kHiLo) {
+                                            const uint32_t lb = (e & 1) ? (wl[e >> 1] & 0xFFFF0000u)
+                                                                        : (wl[e >> 1] << 16);
+                                            w += __uint_as_float(lb);
+                                        }
+                                        Fr[jj] = fmaf(df, w, Fr[jj]);
+                                    }
+                                }
+                            }
+                        }
+                    }
+                    if (__any_sync(0xffffffffu, near_tie)) {
+                        // Exact re-run of the block from its start state (see the single-CTA
+                        // sampler): F from TMEM plus the block's earlier flips, FP64 where the
+                        // FP32 bound cannot settle the decision.
+                        xw = xold;
+                        Mmax = M0;
+#pragma unroll
+                        for (int k = 0; k < MC; ++k) {
+                            g[k] = g0[k];
+                            c[k] = cb[k];
+                        }
+#pragma unroll 1
+                        for (int ii = 0; ii < kPK; ++ii) {
+                            const int s = s0 + ii;
+                            float Fi = 0.f;
+                            if (item) {
+                                uint32_t fv;
+                                asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
+                                             : "=r"(fv)
+                                             : "r"(lane_addr + (uint32_t)(s - col0)));
+                                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                                Fi = __uint_as_float(fv);
+                                uint32_t fl = ((xw ^ xold) >> sb) & ((1u << ii) - 1u);
+                                while (fl) {
+                                    const int i2 = __ffs(fl) - 1;
+                                    fl &= fl - 1u;
+                                    const int d2 = (int)((xw >> (sb + i2)) & 1u) -
+                                                   (int)((xold >> (sb + i2)) & 1u);
+                                    const size_t off =
+                                        ((size_t)(i2 >> 3) * ncol + (s - col0)) * 16 + (i2 & 7) * 2;
+                                    float w = __uint_as_float(
+                                        (uint32_t)*reinterpret_cast<const uint16_t *>(wblk + off) << 16);
+                                    if (kHiLo)
+                                        w += __uint_as_float(
+                                            (uint32_t)*reinterpret_cast<const uint16_t *>(
+                                                wblk + tile_bytes + off)
+                                            << 16);
+                                    Fi = fmaf((float)d2, w, Fi);
+                                }
+                            }
+                            const int xi = (xw >> (sb + ii)) & 1;
+                            int32_t ak[MC];
+                            float acc = sf * Fi;
+                            const float tabs = fabsf(acc);
+#pragma unroll
+                            for (int k = 0; k < MC; ++k) {
+                                ak[k] = (k < m) ? __ldg(acol + (size_t)s * m + k) : 0;
+                                acc = fmaf(-(float)ak[k], c[k], acc);
+                            }
+                            const float Di = __ldg(Dv + s);
+                            acc = fmaf(xi ? 1.f : -1.f, Di, acc);
+                            const float z = hb * acc;
+                            const uint4 rw = philox4x32_10(
+                                make_uint4((uint32_t)(s >> 2), (uint32_t)t, (uint32_t)chain, iter),
+                                key0, key1);
+                            const float theta = s < nprime ? theta_of_word(word_of(rw, s & 3)) : -1e30f;
+                            const float y = z + theta;
+                            const float bound = ez * (tabs + __ldg(asum + s) * Mmax + Di) +
+                                                kThetaRelErr * fabsf(theta) + kThetaAbsErr;
+                            int xn = y > 0.f;
+                            if (!(fabsf(y) > bound)) {
+                                const float rho = rho_of_word(word_of(rw, s & 3));
+                                xn = decide_exact<MC>(Fi, xi, ak, g, lam, m, sf, sg, psg2, beta, rho);
+                            }
+                            const int d = xn - xi;
+                            xw ^= (uint32_t)(d != 0) << (sb + ii);
+                            Mmax = 0.f;
+#pragma unroll
+                            for (int k = 0; k < MC; ++k) {
+                                if (k < m) {
+                                    g[k] += ak[k] * d;
+                                    c[k] = fmaf(kappa, (float)g[k], cA[k]);
+                                    Mmax = fmaxf(Mmax, fmaf(fabsf(kappa), fabsf((float)g[k]),
+                                                            fabsf(cA[k])));
+                                }
+                            }
+                        }
+                    }
+                    xs[wi * kPLanes + r] = xw;
+                    if (item) {
+                        // Delta into this CTA's slot and the peer's (distributed shared memory).
+                        uint32_t pk[8];
+#pragma unroll
+                        for (int e2 = 0; e2 < 8; ++e2) {
+                            const int i0 = sb + 2 * e2;
+                            const int d0 = (int)((xw >> i0) & 1u) - (int)((xold >> i0) & 1u);
+                            const int d1 = (int)((xw >> (i0 + 1)) & 1u) - (int)((xold >> (i0 + 1)) & 1u);
+                            pk[e2] = p_bf16_pm1(d0) | (p_bf16_pm1(d1) << 16);
+                        }
+                        const uint4 lo4 = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        const uint4 hi4 = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                        const uint32_t off = as * kASlotBytes + rowoff;
+                        *reinterpret_cast<uint4 *>(aslot + off) = lo4;
+                        *reinterpret_cast<uint4 *>(aslot + off + 2048) = hi4;
+                        tc::st_cluster_v4(a_peer + off, lo4);
+                        tc::st_cluster_v4(a_peer + off + 2048, hi4);
+                        tc::fence_proxy_async_smem();
+                        __syncwarp();
+                        if (lane == 0) {
+                            tc::fence_acq_rel_cluster();
+                            tc::mbar_arrive_remote(tc::mapa(tc::smem_u32(&bars[4 + as]), peer));
+                        }
+                    }
+                } else {
+                    // The peer decides this block: take its flips from the Delta slot.
+                    const uint32_t ph = (as ? cons1 : cons0) & 1u;
+                    if (!p_wait_warp<true>(&bars[4 + as], ph, abort_flag, status, polls)) {
+                        ok = false;
+                        break;
+                    }
+                    if (as) ++cons1;
+                    else ++cons0;
+                    const uint32_t off = as * kASlotBytes + rowoff;
+                    const uint4 lo4 = *reinterpret_cast<const uint4 *>(aslot + off);
+                    const uint4 hi4 = *reinterpret_cast<const uint4 *>(aslot + off + 2048);
+                    const uint32_t pk[8] = {lo4.x, lo4.y, lo4.z, lo4.w, hi4.x, hi4.y, hi4.z, hi4.w};
+#pragma unroll
+                    for (int ii = 0; ii < kPK; ++ii) {
+                        const int d = p_code((pk[ii >> 1] >> ((ii & 1) * 16)) & 0xFFFFu);
+                        xw ^= (uint32_t)(d != 0) << (sb + ii);
+                        if (d != 0) {
+#pragma unroll
+                            for (int k = 0; k < MC; ++k)
+                                if (k < m) g[k] += __ldg(acol + (size_t)(s0 + ii) * m + k) * d;
+                        }
+                    }
+                    Mmax = 0.f;
+#pragma unroll
+                    for (int k = 0; k < MC; ++k) {
+                        if (k < m) {
+                            c[k] = fmaf(kappa, (float)g[k], cA[k]);
+                            Mmax = fmaxf(Mmax, fmaf(fabsf(kappa), fabsf((float)g[k]), fabsf(cA[k])));
+                        }
+                    }
+                    xs[wi * kPLanes + r] = xw;
+                    tc::fence_proxy_async_smem();
+                    __syncwarp();
+                }
+                if (item) {
+                    // The last of the four decision warps issues this CTA's MMAs for the block:
+                    // F[:, half] += W[half, blk] Delta[blk, :], A = the Delta slot (K-major,
+                    // LBO 2048, SBO 128), B = the W tile (LBO 16 ncol, SBO 128).
+                    if (lane == 0) {
+                        __threadfence_block();
+                        const bool last = (atomicAdd(&arrivals[as], 1u) & 3u) == 3u;
+                        if (last) {
+                            __threadfence_block();
+                            tc::fence_proxy_async_smem();
+                            tc::tc_fence_after();
+                            const uint32_t lbo_b = (uint32_t)ncol * 16u;
+                            const uint32_t w_base = tc::smem_u32(wblk);
+                            const uint64_t adesc = tc::smem_desc(a_own + as * kASlotBytes, 2048u, 128u);
+#pragma unroll
+                            for (int term = 0; term < (kHiLo ? 2 : 1); ++term) {
+                                for (int j0 = 0; j0 < ncol; j0 += 256) {
+                                    const int nr = min(256, ncol - j0);
+                                    const uint64_t bd = tc::smem_desc(
+                                        w_base + (uint32_t)term * tile_bytes + (uint32_t)j0 * 16u,
+                                        lbo_b, 128u);
+                                    tc::mma_bf16(tmem + (uint32_t)j0, adesc, bd,
+                                                 tc::idesc_bf16_f32(128, (uint32_t)nr), 1u);
+                                }
+                            }
+                            tc::mma_commit(&bars[1]);
+                            tc::mma_commit(&bars[29 + ts]);
+                            tc::mma_commit_multicast(&bars[2 + as], (uint16_t)0x3u);
+                        }
+                    }
+                    __syncwarp();
+                    ++ib;
+                }
+                ++it;
+            }
+            if (ok && a.trace && valid && rank == 0) {
+                uint32_t *tr = a.trace + (((size_t)j * a.chains + chain) * a.sweeps + t) * a.words;
+                for (int w = 0; w < a.words; ++w) tr[w] = w < words ? xs[w * kPLanes + r] : 0u;
+            }
+        }
+        if (ok && ib > 0) {
+            ok = p_wait_warp<false>(&bars[1], (ib - 1u) & 1u, abort_flag, status, polls);
+            tc::tc_fence_after();
+        }
+        // This CTA's part of sum_i x_i F_i over its item columns, into CTA 0's part[rank][r].
+        long long sumF = 0;
+        if (ok) {
+            for (int c0 = 0; c0 < ncol; c0 += 32) {
+                float v[32];
+                tc::tmem_ld32(lane_addr + (uint32_t)c0, v);
+                const int s = col0 + c0;
+                const uint32_t bits = s < words * 32 ? xs[(s >> 5) * kPLanes + r] : 0u;
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                    if ((bits >> i) & 1u) sumF += (long long)v[i];
+            }
+        }
+        if (rank == 1)
+            tc::st_cluster_s64(tc::mapa(tc::smem_u32(part + kPLanes + r), 0u), sumF);
+        else
+            part[r] = sumF;
+        // Drain: this thread's MMAs complete before the cluster barrier and TMEM release.
+        if (lane == 0) {
+            tc::mma_commit(&bars[6 + warp]);
+            p_wait_one(&bars[6 + warp], 0, nullptr, status);
+        }
+        __syncwarp();
+        tc::cluster_sync();
+        // Readout of the last sample by CTA 0: cost -(sum_i x_i F_i + h^T x)/2, g, feasibility.
+        if (rank == 0 && ok && !*abort_flag && valid) {
+            long long sumh = 0;
+            for (int w = 0; w < words; ++w) {
+                uint32_t bits = xs[w * kPLanes + r];
+                while (bits) {
+                    const int i = w * 32 + __ffs(bits) - 1;
+                    bits &= bits - 1u;
+                    sumh += (long long)__ldg(hF + i);
+                }
+            }
+            const long long total = part[r] + part[kPLanes + r];
+            const size_t cidx = (size_t)j * a.chains + chain;
+            for (int w = 0; w < a.words; ++w)
+                a.x[cidx * a.words + w] = w < words ? xs[w * kPLanes + r] : 0u;
+            a.cost[cidx] = -(total + sumh) / 2;
+            bool feas = true;
+#pragma unroll
+            for (int k = 0; k < MC; ++k) {
+                if (k < m) {
+                    const int o0 = ip->slack_off[k], o1 = ip->slack_off[k + 1];
+                    long long sv = 0;
+                    for (int s = o0; s < o1; ++s)
+                        if ((xs[(s >> 5) * kPLanes + r] >> (s & 31)) & 1u) sv += 1LL << (s - o0);
+                    if ((long long)g[k] - sv > 0) feas = false;
+                    a.g[cidx * a.m_stride + k] = g[k];
+                }
+            }
+            for (int k = m; k < a.m_stride; ++k) a.g[cidx * a.m_stride + k] = 0;
+            if (a.feasible) a.feasible[cidx] = feas ? 1 : 0;
+        }
+    }
+    if (warp >= kPNoiseWarp0) tc::cluster_sync();
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, tmem_cols);
+    }
+}
+
+}  // namespace
+}  // namespace sais
+
+namespace sais {
+
+bool pair_eligible(int n, int m, bool has_w) {
+    const int npi = pair_npad(n);
+    return has_w && m <= kMaxBlockedConstraints && npi >= 128 && npi <= 1024;
+}
+
+size_t pair_smem_bytes(int max_n, int max_words, bool hilo) {
+    const size_t half = (size_t)pair_half(pair_npad(max_n));
+    const size_t slot = 2 * half * 16 * (hilo ? 2 : 1);
+    return kPRing * slot + 2 * kASlotBytes + (size_t)max_words * kPLanes * 4 +
+           (size_t)2 * kPK * kPLanes * 4 + (size_t)2 * kPLanes * 8 + kBars * 8 + 16;
+}
+
+namespace {
+template <int MC, bool H>
+cudaError_t pair_launch(const SampleArgs &a, int32_t *status, long long polls, size_t smem,
+                        uint32_t cols, uint32_t slot_cap, cudaStream_t st) {
+    auto kern = pair_sampler_kernel<MC, H>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = a.work ? dim3(2 * a.nwork, 1) : dim3(2 * ((a.chains + kPLanes - 1) / kPLanes), a.count);
+    cfg.blockDim = dim3(kPThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, kern, a, status, polls, cols, slot_cap);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+template <bool H>
+cudaError_t pair_mc(const SampleArgs &a, int max_m, int32_t *status, long long polls, size_t smem,
+                    uint32_t cols, uint32_t slot_cap, cudaStream_t st) {
+    if (max_m <= 1) return pair_launch<1, H>(a, status, polls, smem, cols, slot_cap, st);
+    if (max_m <= 2) return pair_launch<2, H>(a, status, polls, smem, cols, slot_cap, st);
+    if (max_m <= 4) return pair_launch<4, H>(a, status, polls, smem, cols, slot_cap, st);
+    return pair_launch<8, H>(a, status, polls, smem, cols, slot_cap, st);
+}
+}  // namespace
+
+cudaError_t launch_pair_sampler(const SampleArgs &a, int max_m, int max_n, int max_words, bool hilo,
+                                int32_t *status, long long dec_wait_polls, cudaStream_t st) {
+    const int half = pair_half(pair_npad(max_n));
+    uint32_t cols = 32;
+    while (cols < (uint32_t)half) cols <<= 1;
+    const uint32_t slot_cap = (uint32_t)(2 * half * 16 * (hilo ? 2 : 1));
+    // one CTA per SM (its TMEM allocation may take all 512 columns)
+    size_t smem = pair_smem_bytes(max_n, max_words, hilo);
+    const size_t floor_smem = 228 * 1024 / 2 + 1;
+    if (smem < floor_smem) smem = floor_smem;
+    const long long polls = dec_wait_polls > 0 ? dec_wait_polls : 0;
+    if (hilo) return pair_mc<true>(a, max_m, status, polls, smem, cols, slot_cap, st);
+    return pair_mc<false>(a, max_m, status, polls, smem, cols, slot_cap, st);
+}
+
+}  // namespace sais

@@ -149,9 +149,45 @@ def test_blocked_streamed_and_hilo(case):
                  block_k=16, oracle_chains=(0, 3))
 
 
+@pytest.mark.parametrize("case", ["n500", "n1000_hilo", "mixed_ragged", "n640_trace"])
+def test_pair_sampler_equals_plain_and_oracle(case):
+    """Items beyond one SM's TMEM: the fields split over a CTA pair (cluster of two), flips
+    exchanged through distributed shared memory; identical to the plain sampler and the
+    oracle."""
+    if case == "n500":
+        _compare([wl.qkp(500, 0.5, 31)], [[1.0]], C=128, T=60, beta=10.0, seed=13, it=1,
+                 block_k=16, oracle_chains=(0, 2))
+    elif case == "n1000_hilo":
+        _compare([wl.qkp(1000, 0.25, 32, profit_max=10000)], [[2.0]], C=128, T=24, beta=10.0,
+                 seed=14, it=0, block_k=16, oracle_chains=(0, 1))
+    elif case == "mixed_ragged":
+        insts = [wl.qkp(700, 0.5, 33), wl.qkp(200, 0.75, 34), wl.qkp(960, 1.0, 35)]
+        _compare(insts, [[0.5], [1.5], [3.0]], C=160, T=30, beta=10.0, seed=15, it=2,
+                 block_k=16, oracle_chains=(0, 1))
+    else:
+        _compare([wl.qkp(640, 0.5, 36)], [[0.8]], C=128, T=20, beta=10.0, seed=16, it=3,
+                 block_k=16, trace=True, oracle_chains=(0, 1))
+
+
+def test_pair_timeout_path_reports_and_recovers():
+    inst = wl.qkp(600, 0.5, 37)
+    prob = sais.Problem(inst)
+    lam = _lam(prob, [[0.5]])
+    prob.sample(lam, 128, 10, 10.0, 1, 0, variant="blocked", debug_wait_polls=1)
+    with pytest.raises(sais.SaisError) as e:
+        prob.synchronize()
+    assert e.value.status == sais.SAIS_ETIMEOUT
+    prob.synchronize()
+    p = _run(prob, lam, 128, 10, 10.0, 1, 0, "plain")
+    b = _run(prob, lam, 128, 10, 10.0, 1, 0, "blocked")
+    assert np.array_equal(p["x"], b["x"]) and np.array_equal(p["cost"], b["cost"])
+    prob.close()
+
+
 def test_blocked_unsupported_cases():
-    for inst in (wl.mkp(40, 3, 1), wl.qkp(600, 0.5, 2)):
-        prob = sais.Problem(inst)
+    cases = ([wl.mkp(40, 3, 1)], [wl.qkp(1100, 0.25, 2)], [wl.qkp(600, 0.5, 3), wl.qkp(40, 0.5, 4)])
+    for insts in cases:
+        prob = sais.Problem(insts)
         lam = torch.zeros(prob.count * prob.m_stride, device="cuda:0")
         with pytest.raises(sais.SaisError) as e:
             prob.sample(lam, 128, 10, 10.0, 1, 0, variant="blocked")
