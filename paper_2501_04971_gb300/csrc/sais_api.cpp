@@ -246,6 +246,15 @@ float bf16_value(uint16_t b) {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+struct DeviceGuard {
+    int prev = 0;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        cudaSetDevice(dev);
+    }
+    ~DeviceGuard() { cudaSetDevice(prev); }
+};
+
 }  // namespace
 
 struct sais_problem {
@@ -284,6 +293,11 @@ struct sais_problem {
     std::vector<int32_t> inst_chains;   // chains per instance (empty: one count for all)
     int32_t *d_inst_chains = nullptr;   // device copy (own allocation)
     int32_t *d_work = nullptr;          // device work list (own allocation)
+    // Launch groups run concurrently: fork from the caller's stream, one side stream per group
+    // (CTA-pair groups share side[0], so two cluster kernels never run at once), join back.
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
     size_t work_cap = 0;                // capacity in (instance, group) pairs
     int work_chains = -1;               // `chains` the work list was built for
     bool work_valid = false;
@@ -342,6 +356,16 @@ void build_groups(sais_problem *p) {
         p->groups.push_back(std::move(g));
     }
     p->work_valid = false;
+    if (p->groups.size() > 1) {
+        const size_t ns = p->groups.size() + 1;
+        p->side.assign(ns, nullptr);
+        p->join.assign(ns, nullptr);
+        for (size_t i = 0; i < ns; ++i) {
+            cudaStreamCreateWithFlags(&p->side[i], cudaStreamNonBlocking);
+            cudaEventCreateWithFlags(&p->join[i], cudaEventDisableTiming);
+        }
+        cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
+    }
 }
 
 int group_cta(const sais_problem::Group &g) { return g.variant == SAIS_BLOCKED ? 128 : g.cpb; }
@@ -619,7 +643,10 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
     }
     p->d_inst = reinterpret_cast<InstDev *>(p->pool);
     p->d_status = reinterpret_cast<int32_t *>(base + status_off);
-    build_groups(p);
+    {
+        DeviceGuard dg(device);   // the groups' side streams belong to the problem's device
+        build_groups(p);
+    }
     *out = p;
     return SAIS_OK;
 }
@@ -638,6 +665,11 @@ sais_status sais_destroy_problem(sais_problem *p) {
     if (p->pool) cudaFree(p->pool);
     if (p->d_work) cudaFree(p->d_work);
     if (p->d_inst_chains) cudaFree(p->d_inst_chains);
+    for (cudaStream_t x : p->side)
+        if (x) cudaStreamDestroy(x);
+    for (cudaEvent_t x : p->join)
+        if (x) cudaEventDestroy(x);
+    if (p->fork) cudaEventDestroy(p->fork);
     cudaSetDevice(prev);
     delete p;
     if (e != cudaSuccess) return fail(SAIS_ECUDA, "synchronize before free: %s", cudaGetErrorString(e));
@@ -674,15 +706,6 @@ sais_status sais_instance_scalars(const sais_problem *p, int32_t index, sais_pro
 }  // extern "C"
 
 namespace {
-
-struct DeviceGuard {
-    int prev = 0;
-    explicit DeviceGuard(int dev) {
-        cudaGetDevice(&prev);
-        cudaSetDevice(dev);
-    }
-    ~DeviceGuard() { cudaSetDevice(prev); }
-};
 
 sais_status check_sample_params(const sais_problem *p, const sais_sample_params *prm) {
     if (!p || !prm) return fail(SAIS_EINVAL, "NULL problem or params");
@@ -753,11 +776,30 @@ sais_status enqueue_sample(sais_problem *p, const sais_sample_params *prm, const
                             g.max_npad_w, plain_smem_bytes(g.max_npad_w, g.words, g.any_w, g.cpb));
         sais_status s = ensure_work(p, prm->chains, st);
         if (s != SAIS_OK) return s;
-        for (const auto &g : p->groups) {
-            e = launch_group(p, g, a, (long long)prm->debug_wait_polls, st);
+        if (p->groups.size() == 1) {
+            e = launch_group(p, p->groups[0], a, (long long)prm->debug_wait_polls, st);
             if (e != cudaSuccess)
                 return fail(SAIS_ECUDA, "sampler launch (group): %s", cudaGetErrorString(e));
+            return SAIS_OK;
         }
+        e = cudaEventRecord(p->fork, st);
+        std::vector<char> used(p->side.size(), 0);
+        for (size_t gi = 0; e == cudaSuccess && gi < p->groups.size(); ++gi) {
+            const auto &g = p->groups[gi];
+            if (g.nwork == 0) continue;
+            const size_t si = g.pair ? 0 : gi + 1;
+            if (!used[si]) e = cudaStreamWaitEvent(p->side[si], p->fork, 0);
+            used[si] = 1;
+            if (e == cudaSuccess)
+                e = launch_group(p, g, a, (long long)prm->debug_wait_polls, p->side[si]);
+        }
+        for (size_t si = 0; e == cudaSuccess && si < p->side.size(); ++si) {
+            if (!used[si]) continue;
+            e = cudaEventRecord(p->join[si], p->side[si]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->join[si], 0);
+        }
+        if (e != cudaSuccess)
+            return fail(SAIS_ECUDA, "sampler launch (groups): %s", cudaGetErrorString(e));
         return SAIS_OK;
     }
     if (prm->variant == SAIS_BLOCKED) {

@@ -122,10 +122,12 @@ __global__ void __launch_bounds__(kPThreads, 1)
     uint32_t *xs = reinterpret_cast<uint32_t *>(aslot + 2 * kASlotBytes);
     float *thbuf = reinterpret_cast<float *>(xs + words * kPLanes);   // [2][K][128]
     long long *part = reinterpret_cast<long long *>(thbuf + 2 * kPK * kPLanes);   // [2][128]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(part + 2 * kPLanes);
+    int32_t *gout = reinterpret_cast<int32_t *>(part + 2 * kPLanes);            // [128][8]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(gout + kPLanes * kMaxBlockedConstraints);
     uint32_t *arrivals = reinterpret_cast<uint32_t *>(bars + kBars);
     uint32_t *tmem_slot = arrivals + 2;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    int *warp_ok = const_cast<int *>(abort_flag) + 1;                             // [4]
 
     if (threadIdx.x == kPLanes) {
         for (int i = 0; i < kBars; ++i) {
@@ -137,6 +139,11 @@ __global__ void __launch_bounds__(kPThreads, 1)
         tc::fence_mbar_init();
         tc::fence_proxy_async_smem();
     }
+    __syncthreads();
+    // Both CTAs' barriers exist before either signals the other.  TMEM is taken only after
+    // this barrier and given back before the final one, so a CTA never holds TMEM while it
+    // waits for its peer at a cluster barrier.
+    tc::cluster_sync();
     if (warp == 0) {
         tc::tmem_alloc(tmem_slot, tmem_cols);
         tc::tmem_relinquish();
@@ -144,8 +151,6 @@ __global__ void __launch_bounds__(kPThreads, 1)
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
-    // Both CTAs' barriers exist before either signals the other.
-    tc::cluster_sync();
     const uint32_t tmem = *tmem_slot;
     const uint32_t iter = a.iter_dev ? *a.iter_dev : a.iter;
 
@@ -614,22 +619,36 @@ __global__ void __launch_bounds__(kPThreads, 1)
             tc::st_cluster_s64(tc::mapa(tc::smem_u32(part + kPLanes + r), 0u), sumF);
         else
             part[r] = sumF;
-        // Drain: this thread's MMAs complete before the cluster barrier and TMEM release.
+#pragma unroll
+        for (int k = 0; k < MC; ++k) gout[r * kMaxBlockedConstraints + k] = g[k];
+        if (lane == 0) warp_ok[warp] = ok ? 1 : 0;
+        // Drain: this thread's MMAs complete before TMEM is released.
         if (lane == 0) {
             tc::mma_commit(&bars[6 + warp]);
             p_wait_one(&bars[6 + warp], 0, nullptr, status);
         }
         __syncwarp();
-        tc::cluster_sync();
-        // Readout of the last sample by CTA 0: cost -(sum_i x_i F_i + h^T x)/2, g, feasibility.
-        if (rank == 0 && ok && !*abort_flag && valid) {
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, tmem_cols);
+    }
+    // CTA 1's partial sums have landed in CTA 0; no remote access follows this barrier.
+    tc::cluster_sync();
+    // Readout of the last sample by CTA 0: cost -(sum_i x_i F_i + h^T x)/2, g, feasibility.
+    if (rank == 0 && warp < kPNoiseWarp0 && warp_ok[warp] && !*abort_flag) {
+        const int r = threadIdx.x;
+        const int chain = grp * kPLanes + r;
+        if (chain < (a.inst_chains ? a.inst_chains[j] : a.chains)) {
             long long sumh = 0;
             for (int w = 0; w < words; ++w) {
                 uint32_t bits = xs[w * kPLanes + r];
                 while (bits) {
                     const int i = w * 32 + __ffs(bits) - 1;
                     bits &= bits - 1u;
-                    sumh += (long long)__ldg(hF + i);
+                    sumh += (long long)__ldg(ip->hF + i);
                 }
             }
             const long long total = part[r] + part[kPLanes + r];
@@ -638,27 +657,18 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 a.x[cidx * a.words + w] = w < words ? xs[w * kPLanes + r] : 0u;
             a.cost[cidx] = -(total + sumh) / 2;
             bool feas = true;
-#pragma unroll
-            for (int k = 0; k < MC; ++k) {
-                if (k < m) {
-                    const int o0 = ip->slack_off[k], o1 = ip->slack_off[k + 1];
-                    long long sv = 0;
-                    for (int s = o0; s < o1; ++s)
-                        if ((xs[(s >> 5) * kPLanes + r] >> (s & 31)) & 1u) sv += 1LL << (s - o0);
-                    if ((long long)g[k] - sv > 0) feas = false;
-                    a.g[cidx * a.m_stride + k] = g[k];
-                }
+            for (int k = 0; k < m; ++k) {
+                const int o0 = ip->slack_off[k], o1 = ip->slack_off[k + 1];
+                long long sv = 0;
+                for (int s = o0; s < o1; ++s)
+                    if ((xs[(s >> 5) * kPLanes + r] >> (s & 31)) & 1u) sv += 1LL << (s - o0);
+                const int32_t gk = gout[r * kMaxBlockedConstraints + k];
+                if ((long long)gk - sv > 0) feas = false;
+                a.g[cidx * a.m_stride + k] = gk;
             }
             for (int k = m; k < a.m_stride; ++k) a.g[cidx * a.m_stride + k] = 0;
             if (a.feasible) a.feasible[cidx] = feas ? 1 : 0;
         }
-    }
-    if (warp >= kPNoiseWarp0) tc::cluster_sync();
-    tc::tc_fence_before();
-    __syncthreads();
-    if (warp == 0) {
-        tc::tc_fence_after();
-        tc::tmem_dealloc(tmem, tmem_cols);
     }
 }
 
@@ -676,7 +686,8 @@ size_t pair_smem_bytes(int max_n, int max_words, bool hilo) {
     const size_t half = (size_t)pair_half(pair_npad(max_n));
     const size_t slot = 2 * half * 16 * (hilo ? 2 : 1);
     return kPRing * slot + 2 * kASlotBytes + (size_t)max_words * kPLanes * 4 +
-           (size_t)2 * kPK * kPLanes * 4 + (size_t)2 * kPLanes * 8 + kBars * 8 + 16;
+           (size_t)2 * kPK * kPLanes * 4 + (size_t)2 * kPLanes * 8 +
+           (size_t)kPLanes * kMaxBlockedConstraints * 4 + kBars * 8 + 32;
 }
 
 namespace {
