@@ -11,7 +11,7 @@ cudaError_t launch_blocked_stream(const SampleArgs &a, int max_m, bool hilo, int
 size_t blocked_smem_bytes(int max_npad, int max_words, int block_k, bool stream, bool hilo) {
     const size_t w = stream ? (size_t)3 * (hilo ? 2 : 1) * (block_k / 8) * max_npad * 16
                             : (size_t)max_npad * max_npad * 2;
-    return w + (size_t)max_words * kLanes * 4 + (size_t)2 * block_k * kLanes * 4 + 29 * 8 + 16;
+    return w + (size_t)max_words * kLanes * 4 + (size_t)2 * block_k * kLanes * 4 + 30 * 8 + 32;
 }
 
 cudaError_t launch_blocked_sampler(const SampleArgs &a, int max_m, int max_npad, int max_words,

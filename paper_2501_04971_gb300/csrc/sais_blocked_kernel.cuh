@@ -130,15 +130,16 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
     float *thbuf = reinterpret_cast<float *>(xs + words * kLanes);   // [2][K][128] noise ring
     uint64_t *bars = reinterpret_cast<uint64_t *>(thbuf + 2 * K * kLanes);
     // bars: 0 = W staged, 1 = never completed (fault-injection test of the timeout path),
-    // 2 = the block's MMAs done, 3..6 = drain of decision warp 0..3,
+    // 2 = unused, 3..6 = drain of decision warp 0..3,
     // 7..14 = noise slot written (2 q + slot), 15..22 = noise slot consumed (2 q + slot),
-    // 23..25 = W tile slot filled, 26..28 = W tile slot free again (its block's MMAs done)
-    uint32_t *arrivals = reinterpret_cast<uint32_t *>(bars + 29);   // [2] decision warps done
+    // 23..25 = W tile slot filled, 26..28 = W tile slot free again (its block's MMAs done),
+    // 29 = the block's MMAs done
+    uint32_t *arrivals = reinterpret_cast<uint32_t *>(bars + 30);   // [2] decision warps done
     uint32_t *tmem_slot = arrivals + 2;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     if (threadIdx.x == kIssueThread) {
-        for (int i = 0; i < 29; ++i) tc::mbar_init(&bars[i], 1);
+        for (int i = 0; i < 30; ++i) tc::mbar_init(&bars[i], 1);
         arrivals[0] = arrivals[1] = 0u;
         *abort_flag = 0;
         tc::fence_mbar_init();
@@ -320,7 +321,10 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                     if (kPreM > 1) Ap[ii][kPreM > 1 ? 1 : 0] = __float_as_int(sc.w);
                 }
                 if (it > 0) {
-                    if (!wait_bounded_warp(&bars[2], (it - 1u) & 1u, abort_flag, status,
+                    // This block's fields: the previous block's MMAs are done (MMAs complete in
+                    // issue order, so those of every earlier block too, which also frees this
+                    // block's Delta slot, last used two blocks ago).
+                    if (!wait_bounded_warp(&bars[29], (it - 1u) & 1u, abort_flag, status,
                                            dec_wait_polls)) {
                         ok = false;
                         break;
@@ -395,36 +399,32 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                                                         fabsf(cA[k])));
                             }
                         }
-                        if (ii + 1 < K && __any_sync(0xffffffffu, d != 0)) {
+                        if (ii + 1 < K) {
                             // In-block correction F_jj += W[s, s0+jj] d for the block's later
-                            // spins; row s of the block's W columns is contiguous per 8 columns.
+                            // spins (row s of the block's W columns is contiguous per 8 columns).
+                            // The next spin's field is on the dependency chain: corrected
+                            // unconditionally (d = 0 adds an exact zero); the others only when a
+                            // chain of the warp flipped.
                             const float df = (float)d;
-#pragma unroll
-                            for (int cc = (ii + 1) >> 3; cc < K / 8; ++cc) {
-                                const uint4 w4 = wrow[cc];
-                                const uint32_t wv[4] = {w4.x, w4.y, w4.z, w4.w};
-                                uint32_t wl[4] = {0u, 0u, 0u, 0u};
+                            auto wcol = [&](int jj) -> float {
+                                const int cc = jj >> 3, e = jj & 7;
+                                const uint32_t wv[4] = {wrow[cc].x, wrow[cc].y, wrow[cc].z,
+                                                        wrow[cc].w};
+                                float w = __uint_as_float((e & 1) ? (wv[e >> 1] & 0xFFFF0000u)
+                                                                  : (wv[e >> 1] << 16));
                                 if (kHiLo) {
-                                    wl[0] = wrlo[cc].x;
-                                    wl[1] = wrlo[cc].y;
-                                    wl[2] = wrlo[cc].z;
-                                    wl[3] = wrlo[cc].w;
+                                    const uint32_t wl[4] = {wrlo[cc].x, wrlo[cc].y, wrlo[cc].z,
+                                                            wrlo[cc].w};
+                                    w += __uint_as_float((e & 1) ? (wl[e >> 1] & 0xFFFF0000u)
+                                                                 : (wl[e >> 1] << 16));   // exact
                                 }
+                                return w;
+                            };
+                            Fr[ii + 1] = fmaf(df, wcol(ii + 1), Fr[ii + 1]);
+                            if (ii + 2 < K && __any_sync(0xffffffffu, d != 0)) {
 #pragma unroll
-                                for (int e = 0; e < 8; ++e) {
-                                    const int jj = cc * 8 + e;
-                                    if (jj > ii) {
-                                        const uint32_t bits = (e & 1) ? (wv[e >> 1] & 0xFFFF0000u)
-                                                                      : (wv[e >> 1] << 16);
-                                        float w = __uint_as_float(bits);
-                                        if (kHiLo) {
-                                            const uint32_t lb = (e & 1) ? (wl[e >> 1] & 0xFFFF0000u)
-                                                                        : (wl[e >> 1] << 16);
-                                            w += __uint_as_float(lb);   // exact: both integers
-                                        }
-                                        Fr[jj] = fmaf(df, w, Fr[jj]);
-                                    }
-                                }
+                                for (int jj = ii + 2; jj < K; ++jj)
+                                    Fr[jj] = fmaf(df, wcol(jj), Fr[jj]);
                             }
                         }
                     }
@@ -536,24 +536,30 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                             tc::tc_fence_after();
                             const uint32_t lbo_b = (uint32_t)npad * 16u;
                             const uint32_t w_base = tc::smem_u32(wblk);
+                            // Columns [c0, c1) of F += W[., blk] Delta, in MMAs of <= 256 columns.
+                            auto mma_cols = [&](int c0, int c1) {
 #pragma unroll
-                            for (int term = 0; term < (kHiLo ? 2 : 1); ++term) {
+                                for (int term = 0; term < (kHiLo ? 2 : 1); ++term) {
 #pragma unroll
-                                for (int ks = 0; ks < K / 16; ++ks) {
-                                    for (int j0 = 0; j0 < npad; j0 += 256) {
-                                        const int nr = min(256, npad - j0);
-                                        const uint64_t bd = tc::smem_desc(
-                                            w_base + (uint32_t)term * tile_bytes +
-                                                (uint32_t)ks * 2u * lbo_b + (uint32_t)j0 * 16u,
-                                            lbo_b, 128u);
-                                        tc::mma_bf16_tmem_a(tmem + (uint32_t)j0,
-                                                            tmem + a_col + 8u * (uint32_t)ks, bd,
-                                                            tc::idesc_bf16_f32(128, (uint32_t)nr),
-                                                            1u);
+                                    for (int ks = 0; ks < K / 16; ++ks) {
+                                        for (int j0 = c0; j0 < c1; j0 += 256) {
+                                            const int nr = min(256, c1 - j0);
+                                            const uint64_t bd = tc::smem_desc(
+                                                w_base + (uint32_t)term * tile_bytes +
+                                                    (uint32_t)ks * 2u * lbo_b + (uint32_t)j0 * 16u,
+                                                lbo_b, 128u);
+                                            tc::mma_bf16_tmem_a(
+                                                tmem + (uint32_t)j0, tmem + a_col + 8u * (uint32_t)ks,
+                                                bd, tc::idesc_bf16_f32(128, (uint32_t)nr), 1u);
+                                        }
                                     }
                                 }
-                            }
-                            tc::mma_commit(&bars[2]);
+                            };
+                            // All columns in one go.  (Issuing the next block's columns first, so
+                            // that its decisions wait for a narrow MMA only, measured slower: the
+                            // extra MMAs and commits cost more than the wait they save.)
+                            mma_cols(0, npad);
+                            tc::mma_commit(&bars[29]);
                             if (kStream) tc::mma_commit(&bars[26 + it % kRing]);
                         }
                     }
@@ -566,11 +572,18 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                 for (int w = 0; w < a.words; ++w) tr[w] = w < words ? xs[w * kLanes + r] : 0u;
             }
         }
-        if (ok && it > 0) {
-            ok = wait_bounded_warp(&bars[2], (it - 1u) & 1u, abort_flag, status, dec_wait_polls);
-            tc::tc_fence_after();
-        }
-        if (ok) {
+        // Drain: every MMA of the CTA completes before the readout and the TMEM release.  Each
+        // decision warp's lane 0 commits the MMAs it issued (any of them may have issued some);
+        // every warp waits for all four, bounded but not cut short by an abort.
+        if (lane == 0) tc::mma_commit(&bars[3 + warp]);
+        __syncwarp();
+        bool drained = true;
+        if (lane == 0)
+            for (int w = 0; w < 4; ++w)
+                drained = wait_bounded(&bars[3 + w], 0, nullptr, status, 0) && drained;
+        drained = __shfl_sync(0xffffffffu, drained ? 1 : 0, 0) != 0;
+        tc::tc_fence_after();
+        if (ok && drained) {
             // Readout of the last sample: cost -(sum_i x_i F_i + h^T x)/2, g, feasibility.  The
             // TMEM loads are warp-collective, so every lane takes part; only valid chains store.
             long long sumF = 0, sumh = 0;
@@ -607,11 +620,6 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                 if (a.feasible) a.feasible[cidx] = feas ? 1 : 0;
             }
         }
-    }
-    if (warp < kNoiseWarp0 && lane == 0) {
-        // Drain: MMAs this thread issued complete before TMEM is released.
-        tc::mma_commit(&bars[3 + warp]);
-        wait_bounded(&bars[3 + warp], 0, nullptr, status, 0);
     }
     tc::tc_fence_before();
     __syncthreads();

@@ -39,11 +39,12 @@ constexpr uint32_t kPRing = 3;          // W tile slots
 constexpr long long kPWaitCycles = 8000000000ll;
 constexpr uint32_t kASlotBytes = kPLanes * kPK * 2;   // 4096
 
-// bars: 0 never completed (timeout test), 1 own MMAs done (one phase per item block),
+// bars: 0 never completed (timeout test), 1 unused,
 // 2..3 Delta slot free (2 arrivals: both CTAs' MMAs), 4..5 Delta slot filled by the peer
 // (4 arrivals: its decision warps), 6..9 drain, 10..17 noise full (2 q + slot),
-// 18..25 noise consumed, 26..28 tile full, 29..31 tile free.
-constexpr int kBars = 32;
+// 18..25 noise consumed, 26..28 tile full, 29..31 tile free, 32 own MMAs done (one phase per
+// item block).
+constexpr int kBars = 33;
 
 __device__ __forceinline__ bool p_expired(long long n, long long polls, unsigned long long t0) {
     return polls > 0 ? n >= polls : (long long)(clock64() - t0) > kPWaitCycles;
@@ -299,11 +300,15 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 uint32_t xw = xs[wi * kPLanes + r];
                 const uint32_t xold = xw;
                 const uint32_t as = ib & 1u;   // Delta slot of this item block
-                // Both CTAs wait, at every item block, for the slot's previous use (block ib - 2)
-                // to be done by both CTAs' MMAs: the owner before overwriting it, the follower so
-                // that it observes every phase of the barrier in order.
-                if (item && ib >= 2 && !p_wait_warp<true>(&bars[2 + as], ((ib - 2u) >> 1) & 1u,
-                                                          abort_flag, status, polls)) {
+                // At every item block both CTAs wait for (a) their own MMAs of block ib - 1 (MMAs
+                // complete in issue order, so all earlier ones too) and (b) the Delta slot's
+                // previous use (block ib - 2) done by both CTAs' MMAs: the owner before
+                // overwriting it, the follower so that it observes every phase of both barriers
+                // in order (a parity wait needs that).
+                if (item && ib >= 1 &&
+                    (!p_wait_warp<false>(&bars[32], (ib - 1u) & 1u, abort_flag, status, polls) ||
+                     (ib >= 2 && !p_wait_warp<true>(&bars[2 + as], ((ib - 2u) >> 1) & 1u,
+                                                    abort_flag, status, polls)))) {
                     ok = false;
                     break;
                 }
@@ -320,14 +325,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
                     }
                     float Fr[kPK];
                     if (item) {
-                        if (ib > 0) {
-                            if (!p_wait_warp<false>(&bars[1], (ib - 1u) & 1u, abort_flag, status,
-                                                    polls)) {
-                                ok = false;
-                                break;
-                            }
-                            tc::tc_fence_after();
-                        }
+                        if (ib > 0) tc::tc_fence_after();
                         tc::tmem_ld16(lane_addr + (uint32_t)(s0 - col0), Fr);
                     } else {
 #pragma unroll
@@ -389,34 +387,32 @@ __global__ void __launch_bounds__(kPThreads, 1)
                                                         fabsf(cA[k])));
                             }
                         }
-                        if (item && ii + 1 < kPK && __any_sync(0xffffffffu, d != 0)) {
+                        if (item && ii + 1 < kPK) {
+                            // In-block correction F_jj += W[s, s0+jj] d for the block's later
+                            // spins (row s of the block's W columns is contiguous per 8 columns).
+                            // The next spin's field is on the dependency chain: corrected
+                            // unconditionally (d = 0 adds an exact zero); the others only when a
+                            // chain of the warp flipped.
                             const float df = (float)d;
-#pragma unroll
-                            for (int cc = (ii + 1) >> 3; cc < 2; ++cc) {
+                            auto wcol = [&](int jj) -> float {
+                                const int cc = jj >> 3, e = jj & 7;
                                 const uint32_t wv[4] = {wrow[cc].x, wrow[cc].y, wrow[cc].z,
                                                         wrow[cc].w};
-                                uint32_t wl[4] = {0u, 0u, 0u, 0u};
+                                float w = __uint_as_float((e & 1) ? (wv[e >> 1] & 0xFFFF0000u)
+                                                                  : (wv[e >> 1] << 16));
                                 if (kHiLo) {
-                                    wl[0] = wrlo[cc].x;
-                                    wl[1] = wrlo[cc].y;
-                                    wl[2] = wrlo[cc].z;
-                                    wl[3] = wrlo[cc].w;
+                                    const uint32_t wl[4] = {wrlo[cc].x, wrlo[cc].y, wrlo[cc].z,
+                                                            wrlo[cc].w};
+                                    w += __uint_as_float((e & 1) ? (wl[e >> 1] & 0xFFFF0000u)
+                                                                 : (wl[e >> 1] << 16));   // exact
                                 }
+                                return w;
+                            };
+                            Fr[ii + 1] = fmaf(df, wcol(ii + 1), Fr[ii + 1]);
+                            if (ii + 2 < kPK && __any_sync(0xffffffffu, d != 0)) {
 #pragma unroll
-                                for (int e = 0; e < 8; ++e) {
-                                    const int jj = cc * 8 + e;
-                                    if (jj > ii) {
-                                        const uint32_t bits = (e & 1) ? (wv[e >> 1] & 0xFFFF0000u)
-                                                                      : (wv[e >> 1] << 16);
-                                        float w = __uint_as_float(bits);
-                                        if (kHiLo) {
-                                            const uint32_t lb = (e & 1) ? (wl[e >> 1] & 0xFFFF0000u)
-                                                                        : (wl[e >> 1] << 16);
-                                            w += __uint_as_float(lb);
-                                        }
-                                        Fr[jj] = fmaf(df, w, Fr[jj]);
-                                    }
-                                }
+                                for (int jj = ii + 2; jj < kPK; ++jj)
+                                    Fr[jj] = fmaf(df, wcol(jj), Fr[jj]);
                             }
                         }
                     }
@@ -572,18 +568,21 @@ __global__ void __launch_bounds__(kPThreads, 1)
                             const uint32_t lbo_b = (uint32_t)ncol * 16u;
                             const uint32_t w_base = tc::smem_u32(wblk);
                             const uint64_t adesc = tc::smem_desc(a_own + as * kASlotBytes, 2048u, 128u);
+                            auto mma_cols = [&](int c0, int c1) {
 #pragma unroll
-                            for (int term = 0; term < (kHiLo ? 2 : 1); ++term) {
-                                for (int j0 = 0; j0 < ncol; j0 += 256) {
-                                    const int nr = min(256, ncol - j0);
-                                    const uint64_t bd = tc::smem_desc(
-                                        w_base + (uint32_t)term * tile_bytes + (uint32_t)j0 * 16u,
-                                        lbo_b, 128u);
-                                    tc::mma_bf16(tmem + (uint32_t)j0, adesc, bd,
-                                                 tc::idesc_bf16_f32(128, (uint32_t)nr), 1u);
+                                for (int term = 0; term < (kHiLo ? 2 : 1); ++term) {
+                                    for (int j0 = c0; j0 < c1; j0 += 256) {
+                                        const int nr = min(256, c1 - j0);
+                                        const uint64_t bd = tc::smem_desc(
+                                            w_base + (uint32_t)term * tile_bytes + (uint32_t)j0 * 16u,
+                                            lbo_b, 128u);
+                                        tc::mma_bf16(tmem + (uint32_t)j0, adesc, bd,
+                                                     tc::idesc_bf16_f32(128, (uint32_t)nr), 1u);
+                                    }
                                 }
-                            }
-                            tc::mma_commit(&bars[1]);
+                            };
+                            mma_cols(0, ncol);
+                            tc::mma_commit(&bars[32]);
                             tc::mma_commit(&bars[29 + ts]);
                             tc::mma_commit_multicast(&bars[2 + as], (uint16_t)0x3u);
                         }
@@ -598,10 +597,18 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 for (int w = 0; w < a.words; ++w) tr[w] = w < words ? xs[w * kPLanes + r] : 0u;
             }
         }
-        if (ok && ib > 0) {
-            ok = p_wait_warp<false>(&bars[1], (ib - 1u) & 1u, abort_flag, status, polls);
-            tc::tc_fence_after();
-        }
+        // Drain: every MMA of this CTA completes before the readout and the TMEM release; each
+        // decision warp's lane 0 commits what it issued, every warp waits for all four (bounded,
+        // not cut short by an abort).
+        if (lane == 0) tc::mma_commit(&bars[6 + warp]);
+        __syncwarp();
+        bool drained = true;
+        if (lane == 0)
+            for (int w = 0; w < 4; ++w)
+                drained = p_wait_one(&bars[6 + w], 0, nullptr, status) && drained;
+        drained = __shfl_sync(0xffffffffu, drained ? 1 : 0, 0) != 0;
+        ok = ok && drained;
+        tc::tc_fence_after();
         // This CTA's part of sum_i x_i F_i over its item columns, into CTA 0's part[rank][r].
         long long sumF = 0;
         if (ok) {
@@ -622,11 +629,6 @@ __global__ void __launch_bounds__(kPThreads, 1)
 #pragma unroll
         for (int k = 0; k < MC; ++k) gout[r * kMaxBlockedConstraints + k] = g[k];
         if (lane == 0) warp_ok[warp] = ok ? 1 : 0;
-        // Drain: this thread's MMAs complete before TMEM is released.
-        if (lane == 0) {
-            tc::mma_commit(&bars[6 + warp]);
-            p_wait_one(&bars[6 + warp], 0, nullptr, status);
-        }
         __syncwarp();
     }
     tc::tc_fence_before();
@@ -687,7 +689,7 @@ size_t pair_smem_bytes(int max_n, int max_words, bool hilo) {
     const size_t slot = 2 * half * 16 * (hilo ? 2 : 1);
     return kPRing * slot + 2 * kASlotBytes + (size_t)max_words * kPLanes * 4 +
            (size_t)2 * kPK * kPLanes * 4 + (size_t)2 * kPLanes * 8 +
-           (size_t)kPLanes * kMaxBlockedConstraints * 4 + kBars * 8 + 32;
+           (size_t)kPLanes * kMaxBlockedConstraints * 4 + kBars * 8 + 48;
 }
 
 namespace {
