@@ -394,18 +394,17 @@ __global__ void __launch_bounds__(kPThreads, 1)
                             // unconditionally (d = 0 adds an exact zero); the others only when a
                             // chain of the warp flipped.
                             const float df = (float)d;
+                            // BF16 value of column jj of the row (jj is a compile-time
+                            // constant after unrolling; no local arrays, so nothing goes to the
+                            // stack)
+                            auto half = [](const uint4 &v, int e) -> float {
+                                const int q = e >> 1;
+                                const uint32_t u = q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
+                                return __uint_as_float((e & 1) ? (u & 0xFFFF0000u) : (u << 16));
+                            };
                             auto wcol = [&](int jj) -> float {
-                                const int cc = jj >> 3, e = jj & 7;
-                                const uint32_t wv[4] = {wrow[cc].x, wrow[cc].y, wrow[cc].z,
-                                                        wrow[cc].w};
-                                float w = __uint_as_float((e & 1) ? (wv[e >> 1] & 0xFFFF0000u)
-                                                                  : (wv[e >> 1] << 16));
-                                if (kHiLo) {
-                                    const uint32_t wl[4] = {wrlo[cc].x, wrlo[cc].y, wrlo[cc].z,
-                                                            wrlo[cc].w};
-                                    w += __uint_as_float((e & 1) ? (wl[e >> 1] & 0xFFFF0000u)
-                                                                 : (wl[e >> 1] << 16));   // exact
-                                }
+                                float w = half(wrow[jj >> 3], jj & 7);
+                                if (kHiLo) w += half(wrlo[jj >> 3], jj & 7);   // exact: integers
                                 return w;
                             };
                             Fr[ii + 1] = fmaf(df, wcol(ii + 1), Fr[ii + 1]);
