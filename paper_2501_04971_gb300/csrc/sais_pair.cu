@@ -38,13 +38,16 @@ constexpr int kPNoiseWarp0 = 4;
 constexpr uint32_t kPRing = 3;          // W tile slots
 constexpr long long kPWaitCycles = 8000000000ll;
 constexpr uint32_t kASlotBytes = kPLanes * kPK * 2;   // 4096
+constexpr uint32_t kASlots = 4;                       // Delta ring: a decider runs 3 blocks ahead
 
-// bars: 0 never completed (timeout test), 1 unused,
-// 2..3 Delta slot free (2 arrivals: both CTAs' MMAs), 4..5 Delta slot filled by the peer
-// (4 arrivals: its decision warps), 6..9 drain, 10..17 noise full (2 q + slot),
-// 18..25 noise consumed, 26..28 tile full, 29..31 tile free, 32 own MMAs done (one phase per
-// item block).
-constexpr int kBars = 33;
+// bars: 0 never completed (timeout test), 1 own MMAs done (one phase per item block),
+// 2..5 Delta slot free (2 arrivals: both CTAs' MMAs), 6..9 Delta slot filled by the peer
+// (this CTA arms it with the expected 4096 bytes; the peer's asynchronous stores complete
+// them), 10..13 drain, 14..21 noise full (2 q + slot),
+// 22..29 noise consumed, 30..32 tile full, 33..35 tile free.
+constexpr int kBars = 36;
+constexpr int kBarMma = 1, kBarFree = 2, kBarFull = 6, kBarDrain = 10, kBarNoise = 14,
+              kBarNoiseFree = 22, kBarTile = 30, kBarTileFree = 33;
 
 __device__ __forceinline__ bool p_expired(long long n, long long polls, unsigned long long t0) {
     return polls > 0 ? n >= polls : (long long)(clock64() - t0) > kPWaitCycles;
@@ -119,23 +122,23 @@ __global__ void __launch_bounds__(kPThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     unsigned char *ring = smem;                                       // kPRing x slot_cap
-    unsigned char *aslot = smem + kPRing * slot_cap;                  // 2 x 4096
-    uint32_t *xs = reinterpret_cast<uint32_t *>(aslot + 2 * kASlotBytes);
+    unsigned char *aslot = smem + kPRing * slot_cap;                  // kASlots x 4096
+    uint32_t *xs = reinterpret_cast<uint32_t *>(aslot + kASlots * kASlotBytes);
     float *thbuf = reinterpret_cast<float *>(xs + words * kPLanes);   // [2][K][128]
     long long *part = reinterpret_cast<long long *>(thbuf + 2 * kPK * kPLanes);   // [2][128]
     int32_t *gout = reinterpret_cast<int32_t *>(part + 2 * kPLanes);            // [128][8]
     uint64_t *bars = reinterpret_cast<uint64_t *>(gout + kPLanes * kMaxBlockedConstraints);
     uint32_t *arrivals = reinterpret_cast<uint32_t *>(bars + kBars);
-    uint32_t *tmem_slot = arrivals + 2;
+    uint32_t *tmem_slot = arrivals + kASlots;   // arrivals: [kASlots] decision warps done
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     int *warp_ok = const_cast<int *>(abort_flag) + 1;                             // [4]
 
     if (threadIdx.x == kPLanes) {
         for (int i = 0; i < kBars; ++i) {
-            const uint32_t cnt = (i == 2 || i == 3) ? 2u : ((i == 4 || i == 5) ? 4u : 1u);
+            const uint32_t cnt = (i >= kBarFree && i < kBarFree + (int)kASlots) ? 2u : 1u;
             tc::mbar_init(&bars[i], cnt);
         }
-        arrivals[0] = arrivals[1] = 0u;
+        for (uint32_t i = 0; i < kASlots; ++i) arrivals[i] = 0u;
         *abort_flag = 0;
         tc::fence_mbar_init();
         tc::fence_proxy_async_smem();
@@ -165,7 +168,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
         uint32_t tiles = 0;   // item blocks whose tile was issued
         for (uint32_t it = 0; it < total; ++it) {
             const uint32_t slot = it & 1u;
-            if (it >= 2 && !p_wait_warp<false>(&bars[18 + 2 * q + slot], ((it >> 1) + 1u) & 1u,
+            if (it >= 2 && !p_wait_warp<false>(&bars[kBarNoiseFree + 2 * q + slot], ((it >> 1) + 1u) & 1u,
                                                abort_flag, status, 0))
                 break;
             const uint32_t t = it / (uint32_t)nb;
@@ -180,11 +183,11 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 if (lane == 0) {
                     const uint32_t ts = ib % kPRing;
                     if (ib >= kPRing)
-                        okt = p_wait_one(&bars[29 + ts], ((ib / kPRing) - 1u) & 1u, abort_flag,
+                        okt = p_wait_one(&bars[kBarTileFree + ts], ((ib / kPRing) - 1u) & 1u, abort_flag,
                                          status);
                     if (okt) {
                         unsigned char *dst = ring + ts * slot_cap;
-                        tc::mbar_expect_tx(&bars[26 + ts], slot_bytes);
+                        tc::mbar_expect_tx(&bars[kBarTile + ts], slot_bytes);
 #pragma unroll
                         for (int term = 0; term < (kHiLo ? 2 : 1); ++term) {
                             const unsigned char *src = reinterpret_cast<const unsigned char *>(
@@ -193,7 +196,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
                             for (int c = 0; c < 2; ++c)
                                 tc::bulk_g2s(dst + term * tile_bytes + (uint32_t)c * ncol * 16u,
                                              src + ((size_t)((s0 >> 3) + c) * npad + col0) * 16,
-                                             (uint32_t)ncol * 16u, &bars[26 + ts]);
+                                             (uint32_t)ncol * 16u, &bars[kBarTile + ts]);
                         }
                         ++tiles;
                     }
@@ -212,12 +215,12 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 }
             }
             __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&bars[10 + 2 * q + slot]);
+            if (lane == 0) tc::mbar_arrive(&bars[kBarNoise + 2 * q + slot]);
         }
         if (q == 0 && lane == 0) {
             for (uint32_t ts = 0; ts < kPRing && ts < tiles; ++ts) {
                 const uint32_t uses = (tiles - ts + kPRing - 1u) / kPRing;
-                p_wait_one(&bars[26 + ts], (uses - 1u) & 1u, nullptr, status);
+                p_wait_one(&bars[kBarTile + ts], (uses - 1u) & 1u, nullptr, status);
             }
         }
         __syncwarp();
@@ -266,7 +269,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
         }
         const float errk = field_err_factor(m);
         bool ok = polls > 0 ? p_wait_warp<false>(&bars[0], 0, abort_flag, status, polls) : true;
-        uint32_t it = 0, ib = 0, cons0 = 0u, cons1 = 0u;   // Delta slots consumed, per slot
+        uint32_t it = 0, ib = 0, cons_par = 0u;   // bit s: parity of Delta slot s's next fill
         float th[kPK];
         for (int t = 0; ok && t < a.sweeps; ++t) {
             const float beta = beta_of_sweep(a.beta_max, t, a.sweeps);
@@ -278,7 +281,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 const int owner = !item ? 2 : (b < split_b ? 0 : 1);
                 const bool decide = owner == 2 || owner == (int)rank;
                 const uint32_t slot = it & 1u;
-                if (!p_wait_warp<false>(&bars[10 + 2 * warp + slot], (it >> 1) & 1u, abort_flag,
+                if (!p_wait_warp<false>(&bars[kBarNoise + 2 * warp + slot], (it >> 1) & 1u, abort_flag,
                                         status, polls)) {
                     ok = false;
                     break;
@@ -288,10 +291,10 @@ __global__ void __launch_bounds__(kPThreads, 1)
                     for (int ii = 0; ii < kPK; ++ii) th[ii] = thbuf[(slot * kPK + ii) * kPLanes + r];
                 }
                 __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&bars[18 + 2 * warp + slot]);
+                if (lane == 0) tc::mbar_arrive(&bars[kBarNoiseFree + 2 * warp + slot]);
                 const uint32_t ts = ib % kPRing;
                 const unsigned char *wblk = ring + ts * slot_cap;
-                if (item && !p_wait_warp<false>(&bars[26 + ts], (ib / kPRing) & 1u, abort_flag,
+                if (item && !p_wait_warp<false>(&bars[kBarTile + ts], (ib / kPRing) & 1u, abort_flag,
                                                 status, polls)) {
                     ok = false;
                     break;
@@ -299,19 +302,22 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 const int wi = s0 >> 5, sb = s0 & 31;
                 uint32_t xw = xs[wi * kPLanes + r];
                 const uint32_t xold = xw;
-                const uint32_t as = ib & 1u;   // Delta slot of this item block
+                const uint32_t as = ib % kASlots;   // Delta slot of this item block
                 // At every item block both CTAs wait for (a) their own MMAs of block ib - 1 (MMAs
                 // complete in issue order, so all earlier ones too) and (b) the Delta slot's
-                // previous use (block ib - 2) done by both CTAs' MMAs: the owner before
+                // previous use (block ib - 4) done by both CTAs' MMAs: the owner before
                 // overwriting it, the follower so that it observes every phase of both barriers
                 // in order (a parity wait needs that).
                 if (item && ib >= 1 &&
-                    (!p_wait_warp<false>(&bars[32], (ib - 1u) & 1u, abort_flag, status, polls) ||
-                     (ib >= 2 && !p_wait_warp<true>(&bars[2 + as], ((ib - 2u) >> 1) & 1u,
-                                                    abort_flag, status, polls)))) {
+                    (!p_wait_warp<false>(&bars[kBarMma], (ib - 1u) & 1u, abort_flag, status, polls) ||
+                     (ib >= kASlots &&
+                      !p_wait_warp<true>(&bars[kBarFree + as], ((ib - kASlots) / kASlots) & 1u,
+                                         abort_flag, status, polls)))) {
                     ok = false;
                     break;
                 }
+                uint4 dlo = make_uint4(0u, 0u, 0u, 0u), dhi = dlo;
+                bool send = false;
                 if (decide) {
                     float Dp[kPK], Sp[kPK];
                     int32_t Ap[kPK][kPreM];
@@ -509,24 +515,21 @@ __global__ void __launch_bounds__(kPThreads, 1)
                         const uint32_t off = as * kASlotBytes + rowoff;
                         *reinterpret_cast<uint4 *>(aslot + off) = lo4;
                         *reinterpret_cast<uint4 *>(aslot + off + 2048) = hi4;
-                        tc::st_cluster_v4(a_peer + off, lo4);
-                        tc::st_cluster_v4(a_peer + off + 2048, hi4);
                         tc::fence_proxy_async_smem();
-                        __syncwarp();
-                        if (lane == 0) {
-                            tc::fence_acq_rel_cluster();
-                            tc::mbar_arrive_remote(tc::mapa(tc::smem_u32(&bars[4 + as]), peer));
-                        }
+                        // the peer's copy goes out after this CTA's MMAs are issued (below)
+                        dlo = lo4;
+                        dhi = hi4;
+                        send = true;
                     }
                 } else {
                     // The peer decides this block: take its flips from the Delta slot.
-                    const uint32_t ph = (as ? cons1 : cons0) & 1u;
-                    if (!p_wait_warp<true>(&bars[4 + as], ph, abort_flag, status, polls)) {
+                    const uint32_t ph = (cons_par >> as) & 1u;
+                    if (warp == 0 && lane == 0) tc::mbar_expect_tx(&bars[kBarFull + as], kASlotBytes);
+                    if (!p_wait_warp<true>(&bars[kBarFull + as], ph, abort_flag, status, polls)) {
                         ok = false;
                         break;
                     }
-                    if (as) ++cons1;
-                    else ++cons0;
+                    cons_par ^= 1u << as;
                     const uint32_t off = as * kASlotBytes + rowoff;
                     const uint4 lo4 = *reinterpret_cast<const uint4 *>(aslot + off);
                     const uint4 hi4 = *reinterpret_cast<const uint4 *>(aslot + off + 2048);
@@ -550,7 +553,6 @@ __global__ void __launch_bounds__(kPThreads, 1)
                         }
                     }
                     xs[wi * kPLanes + r] = xw;
-                    tc::fence_proxy_async_smem();
                     __syncwarp();
                 }
                 if (item) {
@@ -581,12 +583,21 @@ __global__ void __launch_bounds__(kPThreads, 1)
                                 }
                             };
                             mma_cols(0, ncol);
-                            tc::mma_commit(&bars[32]);
-                            tc::mma_commit(&bars[29 + ts]);
-                            tc::mma_commit_multicast(&bars[2 + as], (uint16_t)0x3u);
+                            tc::mma_commit(&bars[kBarMma]);
+                            tc::mma_commit(&bars[kBarTileFree + ts]);
+                            tc::mma_commit_multicast(&bars[kBarFree + as], (uint16_t)0x3u);
                         }
                     }
                     __syncwarp();
+                    if (send) {
+                        // Delta into the peer's slot (distributed shared memory) by asynchronous
+                        // stores whose bytes complete the peer's slot-filled barrier; after this
+                        // CTA's MMAs are issued, and without a fence on this CTA's path.
+                        const uint32_t off = as * kASlotBytes + rowoff;
+                        const uint32_t pbar = tc::mapa(tc::smem_u32(&bars[kBarFull + as]), peer);
+                        tc::st_async_v4(a_peer + off, dlo, pbar);
+                        tc::st_async_v4(a_peer + off + 2048, dhi, pbar);
+                    }
                     ++ib;
                 }
                 ++it;
@@ -599,12 +610,12 @@ __global__ void __launch_bounds__(kPThreads, 1)
         // Drain: every MMA of this CTA completes before the readout and the TMEM release; each
         // decision warp's lane 0 commits what it issued, every warp waits for all four (bounded,
         // not cut short by an abort).
-        if (lane == 0) tc::mma_commit(&bars[6 + warp]);
+        if (lane == 0) tc::mma_commit(&bars[kBarDrain + warp]);
         __syncwarp();
         bool drained = true;
         if (lane == 0)
             for (int w = 0; w < 4; ++w)
-                drained = p_wait_one(&bars[6 + w], 0, nullptr, status) && drained;
+                drained = p_wait_one(&bars[kBarDrain + w], 0, nullptr, status) && drained;
         drained = __shfl_sync(0xffffffffu, drained ? 1 : 0, 0) != 0;
         ok = ok && drained;
         tc::tc_fence_after();
@@ -686,9 +697,9 @@ bool pair_eligible(int n, int m, bool has_w) {
 size_t pair_smem_bytes(int max_n, int max_words, bool hilo) {
     const size_t half = (size_t)pair_half(pair_npad(max_n));
     const size_t slot = 2 * half * 16 * (hilo ? 2 : 1);
-    return kPRing * slot + 2 * kASlotBytes + (size_t)max_words * kPLanes * 4 +
+    return kPRing * slot + kASlots * kASlotBytes + (size_t)max_words * kPLanes * 4 +
            (size_t)2 * kPK * kPLanes * 4 + (size_t)2 * kPLanes * 8 +
-           (size_t)kPLanes * kMaxBlockedConstraints * 4 + kBars * 8 + 48;
+           (size_t)kPLanes * kMaxBlockedConstraints * 4 + kBars * 8 + 64;
 }
 
 namespace {

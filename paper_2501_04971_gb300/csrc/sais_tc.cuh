@@ -201,6 +201,14 @@ __device__ __forceinline__ void st_cluster_v4(uint32_t caddr, uint4 v) {
 __device__ __forceinline__ void st_cluster_s64(uint32_t caddr, long long v) {
     asm volatile("st.shared::cluster.s64 [%0], %1;" ::"r"(caddr), "l"(v) : "memory");
 }
+// Asynchronous 16-byte store into another CTA's shared memory; its bytes complete a
+// transaction on that CTA's mbarrier `cbar` (both shared::cluster addresses in that CTA).
+__device__ __forceinline__ void st_async_v4(uint32_t caddr, uint4 v, uint32_t cbar) {
+    asm volatile(
+        "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];"
+        ::"r"(caddr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"(cbar)
+        : "memory");
+}
 __device__ __forceinline__ void fence_acq_rel_cluster() {
     asm volatile("fence.acq_rel.cluster;" ::: "memory");
 }
