@@ -318,17 +318,19 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 }
                 uint4 dlo = make_uint4(0u, 0u, 0u, 0u), dhi = dlo;
                 bool send = false;
-                if (decide) {
-                    float Dp[kPK], Sp[kPK];
-                    int32_t Ap[kPK][kPreM];
+                // Per-spin constants of the block, loaded together (independent loads) for the
+                // decisions or for following the peer's flips.
+                float Dp[kPK], Sp[kPK];
+                int32_t Ap[kPK][kPreM];
 #pragma unroll
-                    for (int ii = 0; ii < kPK; ++ii) {
-                        const float4 sc = __ldg(ip->spinc + s0 + ii);
-                        Ap[ii][0] = __float_as_int(sc.x);
-                        Dp[ii] = sc.y;
-                        Sp[ii] = sc.z;
-                        if (kPreM > 1) Ap[ii][kPreM > 1 ? 1 : 0] = __float_as_int(sc.w);
-                    }
+                for (int ii = 0; ii < kPK; ++ii) {
+                    const float4 sc = __ldg(ip->spinc + s0 + ii);
+                    Ap[ii][0] = __float_as_int(sc.x);
+                    Dp[ii] = sc.y;
+                    Sp[ii] = sc.z;
+                    if (kPreM > 1) Ap[ii][kPreM > 1 ? 1 : 0] = __float_as_int(sc.w);
+                }
+                if (decide) {
                     float Fr[kPK];
                     if (item) {
                         if (ib > 0) tc::tc_fence_after();
@@ -538,10 +540,12 @@ __global__ void __launch_bounds__(kPThreads, 1)
                     for (int ii = 0; ii < kPK; ++ii) {
                         const int d = p_code((pk[ii >> 1] >> ((ii & 1) * 16)) & 0xFFFFu);
                         xw ^= (uint32_t)(d != 0) << (sb + ii);
-                        if (d != 0) {
 #pragma unroll
-                            for (int k = 0; k < MC; ++k)
-                                if (k < m) g[k] += __ldg(acol + (size_t)(s0 + ii) * m + k) * d;
+                        for (int k = 0; k < MC; ++k) {
+                            if (k < kPreM)
+                                g[k] += Ap[ii][k < kPreM ? k : 0] * d;
+                            else if (k < m && d != 0)
+                                g[k] += __ldg(acol + (size_t)(s0 + ii) * m + k) * d;
                         }
                     }
                     Mmax = 0.f;
