@@ -427,11 +427,15 @@ def main():
     if variant == "blocked":
         npad = ((nspins + 63) // 64) * 64
         flops = float((2 * npad * nspins).sum()) * a.chains * a.sweeps
+        # DRAM bytes (read + write) per instance of one launch of this kernel, measured with ncu
+        # on a 640-instance, 10-sweep launch (W is read once per CTA, so traffic scales with
+        # instances, not sweeps)
+        traffic = 219330.0 * prob.count if (a.chains == 128 and a.block_k in (0, 16)) else None
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
             if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
         peak = peaks.get("bf16_tflops", 1900.0) * 1e12
         roof = {"bound": "tensor", "achieved": flops / kmean / 1e12, "peak": peak / 1e12,
-                "unit": "TFLOP/s", "frac": flops / kmean / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": flops / kmean / peak, "traffic": traffic,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)" if peaks else
                 "fallback 1.9 PFLOP/s"}
     else:
