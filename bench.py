@@ -71,6 +71,17 @@ def workload(per_density: int, rank: int):
     return [wl.qkp(300, d, rank * per_density + s) for d in DENSITIES for s in range(per_density)]
 
 
+def over_ranks(x: float, dist, device, op: str = "max") -> float:
+    """Max (timings) or sum (work units) of a per-rank scalar over all ranks; the value itself
+    without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def workload_name(a) -> str:
     return (f"QKP N=300, d in {{0.25,0.5,0.75,1}} x {a.per_density} instances, "
             f"{a.chains} chains, {a.sweeps} sweeps (beta 0->{a.beta_max:g}) per step")
@@ -416,11 +427,10 @@ def main():
         dist.barrier()
     ms = t_start.elapsed_time(t_end)
     kern_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = upd_step * a.steps * world / (ms / 1e3)
+    ms = over_ranks(ms, dist, "cuda", "max")
+    # each rank's instances have their own N' (slack bits depend on the capacities)
+    upd_all = over_ranks(upd_step, dist, "cuda", "sum")
+    value = upd_all * a.steps / (ms / 1e3)
 
     # roofline of the dominant kernel (the sampler), per launch
     kmean = statistics.mean(kern_ms) / 1e3
@@ -479,13 +489,10 @@ def main():
             sais.sais_solve(prob.handle, prm, res, sp)
             lam_h.copy_(pinned["lambda_final"])
         dt = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = over_ranks(dt, dist, "cuda", "max")
         h2d = cnt * M * 4 + cnt * (8 + 4 + 4) + 4
         d2h = cnt * (8 + Wd * 4 + 4 + 4 + 8 + M * 4 + M * 4)
-        e2e = {"value": upd_step * a.steps * world / dt, "unit": UNIT,
+        e2e = {"value": upd_all * a.steps / dt, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "api": "sais_solve(iters=1), pinned host lambda0 and results"}
 
@@ -504,11 +511,10 @@ def main():
                         stream=stream)
         p1.record(stream)
         torch.cuda.synchronize()
-        pms = p0.elapsed_time(p1) / np_steps
-        plain_cmp = {"value": upd_step * world / (pms / 1e3), "unit": UNIT,
-                     "sampler_ms_per_step": pms,
-                     "blocked_over_plain": (upd_step * world / (pms / 1e3)) and
-                     value / (upd_step * world / (pms / 1e3))}
+        pms = over_ranks(p0.elapsed_time(p1) / np_steps, dist, "cuda", "max")
+        pval = upd_all / (pms / 1e3)
+        plain_cmp = {"value": pval, "unit": UNIT, "sampler_ms_per_step": pms,
+                     "blocked_over_plain": value / pval}
     gap = None
     if not a.no_gap and world == 1:
         gap = gap_measurement(a, sais, torch, ["blocked", "plain"] if variant == "blocked"
