@@ -306,14 +306,16 @@ struct sais_problem {
 namespace {
 
 // SAIS_AUTO grouping (see struct sais_problem).  Keys: 1 blocked with W resident, 2 streamed,
-// 3 streamed hi/lo, 4 CTA-pair blocked, 5 CTA-pair hi/lo; plain instances split by whether they
+// 3 streamed hi/lo, 4 CTA-pair blocked, 5 CTA-pair hi/lo (6, 7: the same with n > 992, whose
+// pair kernels take the A operand from shared memory); plain instances split by whether they
 // have W and by padded N' (bucket of 128 spins), so each plain group sizes its shared memory for
 // its own largest member.
 void build_groups(sais_problem *p) {
     p->groups.clear();
     auto key_of = [&](const HostInst &h) -> int {
         const bool eligible = h.has_w && h.m <= kMaxBlockedConstraints && h.npad + 16 <= 512;
-        if (!eligible && pair_eligible(h.n, h.m, h.has_w)) return h.lo_own ? 5 : 4;
+        if (!eligible && pair_eligible(h.n, h.m, h.has_w))
+            return (h.lo_own ? 5 : 4) + (pair_a_tmem(h.n) ? 0 : 2);
         if (!eligible) return 100 + (h.has_w ? 1000 : 0) + (h.npad + 127) / 128;
         if (h.lo_own) return 3;
         return blocked_smem_bytes(h.npad, h.words, 16, false, false) > kMaxSmemPerBlock ? 2 : 1;
@@ -344,9 +346,9 @@ void build_groups(sais_problem *p) {
         }
         g.variant = key >= 100 ? SAIS_PLAIN : SAIS_BLOCKED;
         g.blocked_ok = key < 100;
-        g.pair = key == 4 || key == 5;
-        g.stream_w = key >= 2 && key <= 5;
-        g.hilo = key == 3 || key == 5;
+        g.pair = key >= 4 && key <= 7;
+        g.stream_w = key >= 2 && key <= 7;
+        g.hilo = key == 3 || key == 5 || key == 7;
         auto cost = [&](int j) {
             const HostInst &h = p->host[j];
             return (double)h.nprime * (h.has_w ? (double)h.npad : (double)std::max(1, h.m));

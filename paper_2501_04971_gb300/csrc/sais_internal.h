@@ -113,6 +113,7 @@ size_t plain_smem_bytes(int max_npad, int max_words, bool any_w, int cpb);
 // Blocked sampler on a CTA pair (thread-block cluster of two) for instances whose items do not
 // fit one SM's TMEM: W present, m <= 8, 128 <= n rounded up to 64 <= 1024.
 bool pair_eligible(int n, int m, bool has_w);
+bool pair_a_tmem(int n);   // the own MMAs' A operand fits in TMEM beside F (n <= 992)
 size_t pair_smem_bytes(int max_n, int max_words, bool hilo);
 cudaError_t launch_pair_sampler(const SampleArgs &a, int max_m, int max_n, int max_words, bool hilo,
                                 int32_t *status, long long dec_wait_polls, cudaStream_t st);

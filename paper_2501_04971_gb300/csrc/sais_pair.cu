@@ -96,14 +96,19 @@ __device__ __forceinline__ uint32_t p_bf16_pm1(int d) {
 // Flip of a BF16 -1/0/+1 code.
 __device__ __forceinline__ int p_code(uint32_t h) { return h == 0x3F80u ? 1 : (h == 0xBF80u ? -1 : 0); }
 
-// Item columns of the pair: n_pad = n rounded up to 64, CTA 0 holds [0, h), CTA 1 [h, n_pad).
-__host__ __device__ inline int pair_npad(int n) { return (n + 63) / 64 * 64; }
-__host__ __device__ inline int pair_half(int npi) { return ((npi / 2) + 63) / 64 * 64; }
+// Item columns of the pair: n_pad = n rounded up to 16, CTA 0 holds [0, h), CTA 1 [h, n_pad),
+// h = n_pad / 2 rounded up to 16 (so every MMA's N is a multiple of 16).  When h + 8 <= 512
+// columns (n <= 992) each CTA's TMEM also holds 8 columns for the A operand of its own MMAs (the
+// flips of a block it decides, two BF16 per column); above that the A operand of those MMAs is
+// the shared-memory Delta slot, written by generic stores behind a proxy fence.
+__host__ __device__ inline int pair_npad(int n) { return (n + 15) / 16 * 16; }
+__host__ __device__ inline int pair_half(int npi) { return ((npi / 2) + 15) / 16 * 16; }
+__host__ __device__ inline bool pair_a_in_tmem(int max_n) { return pair_half(pair_npad(max_n)) + 8 <= 512; }
 
 template <int MC, bool kHiLo>
 __global__ void __launch_bounds__(kPThreads, 1)
     pair_sampler_kernel(SampleArgs a, int32_t *status, long long polls, uint32_t tmem_cols,
-                        uint32_t slot_cap) {
+                        uint32_t slot_cap, int a_tmem) {
     extern __shared__ __align__(1024) unsigned char smem[];
     constexpr int kPreM = MC < 2 ? MC : 2;
     const uint32_t rank = tc::cluster_ctarank(), peer = rank ^ 1u;
@@ -244,10 +249,20 @@ __global__ void __launch_bounds__(kPThreads, 1)
 
         for (int w = 0; w < words; ++w) xs[w * kPLanes + r] = 0u;
         for (int c0 = 0; c0 < ncol; c0 += 32) {
-            float v[32];
+            if (c0 + 32 <= ncol) {
+                float v[32];
 #pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = __ldg(hF + col0 + c0 + i);
-            tc::tmem_st32(lane_addr + (uint32_t)c0, v);
+                for (int i = 0; i < 32; ++i) v[i] = __ldg(hF + col0 + c0 + i);
+                tc::tmem_st32(lane_addr + (uint32_t)c0, v);
+            } else {   // a 16-column tail
+#pragma unroll
+                for (int h8 = 0; h8 < 2; ++h8) {
+                    uint32_t v8[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) v8[i] = __float_as_uint(__ldg(hF + col0 + c0 + 8 * h8 + i));
+                    tc::tmem_st8(lane_addr + (uint32_t)(c0 + 8 * h8), v8);
+                }
+            }
         }
         tc::tc_fence_before();
 
@@ -308,18 +323,9 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 // previous use (block ib - 4) done by both CTAs' MMAs: the owner before
                 // overwriting it, the follower so that it observes every phase of both barriers
                 // in order (a parity wait needs that).
-                if (item && ib >= 1 &&
-                    (!p_wait_warp<false>(&bars[kBarMma], (ib - 1u) & 1u, abort_flag, status, polls) ||
-                     (ib >= kASlots &&
-                      !p_wait_warp<true>(&bars[kBarFree + as], ((ib - kASlots) / kASlots) & 1u,
-                                         abort_flag, status, polls)))) {
-                    ok = false;
-                    break;
-                }
-                uint4 dlo = make_uint4(0u, 0u, 0u, 0u), dhi = dlo;
-                bool send = false;
-                // Per-spin constants of the block, loaded together (independent loads) for the
-                // decisions or for following the peer's flips.
+                // Per-spin constants of the block, loaded together (independent loads, ahead of
+                // the waits below, which they overlap) for the decisions or for following the
+                // peer's flips.
                 float Dp[kPK], Sp[kPK];
                 int32_t Ap[kPK][kPreM];
 #pragma unroll
@@ -330,6 +336,16 @@ __global__ void __launch_bounds__(kPThreads, 1)
                     Sp[ii] = sc.z;
                     if (kPreM > 1) Ap[ii][kPreM > 1 ? 1 : 0] = __float_as_int(sc.w);
                 }
+                if (item && ib >= 1 &&
+                    (!p_wait_warp<false>(&bars[kBarMma], (ib - 1u) & 1u, abort_flag, status, polls) ||
+                     (ib >= kASlots &&
+                      !p_wait_warp<true>(&bars[kBarFree + as], ((ib - kASlots) / kASlots) & 1u,
+                                         abort_flag, status, polls)))) {
+                    ok = false;
+                    break;
+                }
+                uint4 dlo = make_uint4(0u, 0u, 0u, 0u), dhi = dlo;
+                bool send = false;
                 if (decide) {
                     float Fr[kPK];
                     if (item) {
@@ -514,11 +530,20 @@ __global__ void __launch_bounds__(kPThreads, 1)
                         }
                         const uint4 lo4 = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                         const uint4 hi4 = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-                        const uint32_t off = as * kASlotBytes + rowoff;
-                        *reinterpret_cast<uint4 *>(aslot + off) = lo4;
-                        *reinterpret_cast<uint4 *>(aslot + off + 2048) = hi4;
-                        tc::fence_proxy_async_smem();
-                        // the peer's copy goes out after this CTA's MMAs are issued (below)
+                        // This CTA's MMA takes the flips from TMEM (8 columns after F; the
+                        // previous block's MMAs, which read them, are done): no shared-memory
+                        // write and no proxy fence on this path.  Without room in TMEM, from
+                        // this CTA's Delta slot behind a proxy fence.  The peer's copy goes out
+                        // after this CTA's MMAs are issued (below).
+                        if (a_tmem) {
+                            tc::tmem_st8(lane_addr + (uint32_t)ncol, pk);
+                            tc::tc_fence_before();
+                        } else {
+                            const uint32_t off = as * kASlotBytes + rowoff;
+                            *reinterpret_cast<uint4 *>(aslot + off) = lo4;
+                            *reinterpret_cast<uint4 *>(aslot + off + 2048) = hi4;
+                            tc::fence_proxy_async_smem();
+                        }
                         dlo = lo4;
                         dhi = hi4;
                         send = true;
@@ -568,7 +593,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
                         const bool last = (atomicAdd(&arrivals[as], 1u) & 3u) == 3u;
                         if (last) {
                             __threadfence_block();
-                            tc::fence_proxy_async_smem();
+                            if (send && !a_tmem) tc::fence_proxy_async_smem();
                             tc::tc_fence_after();
                             const uint32_t lbo_b = (uint32_t)ncol * 16u;
                             const uint32_t w_base = tc::smem_u32(wblk);
@@ -581,8 +606,12 @@ __global__ void __launch_bounds__(kPThreads, 1)
                                         const uint64_t bd = tc::smem_desc(
                                             w_base + (uint32_t)term * tile_bytes + (uint32_t)j0 * 16u,
                                             lbo_b, 128u);
-                                        tc::mma_bf16(tmem + (uint32_t)j0, adesc, bd,
-                                                     tc::idesc_bf16_f32(128, (uint32_t)nr), 1u);
+                                        const uint32_t id = tc::idesc_bf16_f32(128, (uint32_t)nr);
+                                        if (send && a_tmem)   // this CTA decided: A in TMEM
+                                            tc::mma_bf16_tmem_a(tmem + (uint32_t)j0,
+                                                                tmem + (uint32_t)ncol, bd, id, 1u);
+                                        else   // A in the Delta slot
+                                            tc::mma_bf16(tmem + (uint32_t)j0, adesc, bd, id, 1u);
                                     }
                                 }
                             };
@@ -626,13 +655,14 @@ __global__ void __launch_bounds__(kPThreads, 1)
         // This CTA's part of sum_i x_i F_i over its item columns, into CTA 0's part[rank][r].
         long long sumF = 0;
         if (ok) {
-            for (int c0 = 0; c0 < ncol; c0 += 32) {
-                float v[32];
-                tc::tmem_ld32(lane_addr + (uint32_t)c0, v);
-                const int s = col0 + c0;
-                const uint32_t bits = s < words * 32 ? xs[(s >> 5) * kPLanes + r] : 0u;
+            for (int c0 = 0; c0 < ncol; c0 += 16) {
+                float v[16];
+                tc::tmem_ld16(lane_addr + (uint32_t)c0, v);
+                const int s = col0 + c0;   // a multiple of 16
+                const uint32_t bits =
+                    s < words * 32 ? (xs[(s >> 5) * kPLanes + r] >> (s & 31)) & 0xFFFFu : 0u;
 #pragma unroll
-                for (int i = 0; i < 32; ++i)
+                for (int i = 0; i < 16; ++i)
                     if ((bits >> i) & 1u) sumF += (long long)v[i];
             }
         }
@@ -698,6 +728,8 @@ bool pair_eligible(int n, int m, bool has_w) {
     return has_w && m <= kMaxBlockedConstraints && npi >= 128 && npi <= 1024;
 }
 
+bool pair_a_tmem(int n) { return pair_a_in_tmem(n); }
+
 size_t pair_smem_bytes(int max_n, int max_words, bool hilo) {
     const size_t half = (size_t)pair_half(pair_npad(max_n));
     const size_t slot = 2 * half * 16 * (hilo ? 2 : 1);
@@ -709,7 +741,7 @@ size_t pair_smem_bytes(int max_n, int max_words, bool hilo) {
 namespace {
 template <int MC, bool H>
 cudaError_t pair_launch(const SampleArgs &a, int32_t *status, long long polls, size_t smem,
-                        uint32_t cols, uint32_t slot_cap, cudaStream_t st) {
+                        uint32_t cols, uint32_t slot_cap, int a_tmem, cudaStream_t st) {
     auto kern = pair_sampler_kernel<MC, H>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -725,33 +757,35 @@ cudaError_t pair_launch(const SampleArgs &a, int32_t *status, long long polls, s
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, kern, a, status, polls, cols, slot_cap);
+    e = cudaLaunchKernelEx(&cfg, kern, a, status, polls, cols, slot_cap, a_tmem);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 template <bool H>
 cudaError_t pair_mc(const SampleArgs &a, int max_m, int32_t *status, long long polls, size_t smem,
-                    uint32_t cols, uint32_t slot_cap, cudaStream_t st) {
-    if (max_m <= 1) return pair_launch<1, H>(a, status, polls, smem, cols, slot_cap, st);
-    if (max_m <= 2) return pair_launch<2, H>(a, status, polls, smem, cols, slot_cap, st);
-    if (max_m <= 4) return pair_launch<4, H>(a, status, polls, smem, cols, slot_cap, st);
-    return pair_launch<8, H>(a, status, polls, smem, cols, slot_cap, st);
+                    uint32_t cols, uint32_t slot_cap, int at, cudaStream_t st) {
+    if (max_m <= 1) return pair_launch<1, H>(a, status, polls, smem, cols, slot_cap, at, st);
+    if (max_m <= 2) return pair_launch<2, H>(a, status, polls, smem, cols, slot_cap, at, st);
+    if (max_m <= 4) return pair_launch<4, H>(a, status, polls, smem, cols, slot_cap, at, st);
+    return pair_launch<8, H>(a, status, polls, smem, cols, slot_cap, at, st);
 }
 }  // namespace
 
 cudaError_t launch_pair_sampler(const SampleArgs &a, int max_m, int max_n, int max_words, bool hilo,
                                 int32_t *status, long long dec_wait_polls, cudaStream_t st) {
     const int half = pair_half(pair_npad(max_n));
+    const bool a_tmem = pair_a_in_tmem(max_n);
     uint32_t cols = 32;
-    while (cols < (uint32_t)half) cols <<= 1;
+    while (cols < (uint32_t)half + (a_tmem ? 8u : 0u)) cols <<= 1;   // F, then the own A operand
     const uint32_t slot_cap = (uint32_t)(2 * half * 16 * (hilo ? 2 : 1));
     // one CTA per SM (its TMEM allocation may take all 512 columns)
     size_t smem = pair_smem_bytes(max_n, max_words, hilo);
     const size_t floor_smem = 228 * 1024 / 2 + 1;
     if (smem < floor_smem) smem = floor_smem;
     const long long polls = dec_wait_polls > 0 ? dec_wait_polls : 0;
-    if (hilo) return pair_mc<true>(a, max_m, status, polls, smem, cols, slot_cap, st);
-    return pair_mc<false>(a, max_m, status, polls, smem, cols, slot_cap, st);
+    const int at = a_tmem ? 1 : 0;
+    if (hilo) return pair_mc<true>(a, max_m, status, polls, smem, cols, slot_cap, at, st);
+    return pair_mc<false>(a, max_m, status, polls, smem, cols, slot_cap, at, st);
 }
 
 }  // namespace sais

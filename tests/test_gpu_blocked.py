@@ -149,7 +149,8 @@ def test_blocked_streamed_and_hilo(case):
                  block_k=16, oracle_chains=(0, 3))
 
 
-@pytest.mark.parametrize("case", ["n500", "n1000_hilo", "mixed_ragged", "n640_trace"])
+@pytest.mark.parametrize("case", ["n500", "n1000_hilo", "mixed_ragged", "n640_trace", "n1020",
+                                  "n990_tail"])
 def test_pair_sampler_equals_plain_and_oracle(case):
     """Items beyond one SM's TMEM: the fields split over a CTA pair (cluster of two), flips
     exchanged through distributed shared memory; identical to the plain sampler and the
@@ -164,9 +165,15 @@ def test_pair_sampler_equals_plain_and_oracle(case):
         insts = [wl.qkp(700, 0.5, 33), wl.qkp(200, 0.75, 34), wl.qkp(960, 1.0, 35)]
         _compare(insts, [[0.5], [1.5], [3.0]], C=160, T=30, beta=10.0, seed=15, it=2,
                  block_k=16, oracle_chains=(0, 1))
-    else:
+    elif case == "n640_trace":
         _compare([wl.qkp(640, 0.5, 36)], [[0.8]], C=128, T=20, beta=10.0, seed=16, it=3,
                  block_k=16, trace=True, oracle_chains=(0, 1))
+    elif case == "n1020":   # halves of 512 columns: the own A operand from shared memory
+        _compare([wl.qkp(1020, 0.5, 38)], [[1.2]], C=128, T=12, beta=10.0, seed=17, it=0,
+                 block_k=16, oracle_chains=(0, 1))
+    else:                   # n = 990: halves of 496 columns, 16-column tails
+        _compare([wl.qkp(990, 0.75, 39), wl.qkp(250, 0.5, 40)], [[0.6], [1.0]], C=128, T=12,
+                 beta=10.0, seed=18, it=1, block_k=16, oracle_chains=(0, 1))
 
 
 def test_pair_timeout_path_reports_and_recovers():
