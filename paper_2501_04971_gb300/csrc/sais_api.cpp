@@ -506,7 +506,7 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
     // Pool layout: [InstDev x count] then per instance W, Wbf(, Wbf_lo), hF, acol, D, asum, b,
     // slack_off, each 256-byte aligned.
     struct Off {
-        size_t W, Wbf, Wlo, hF, acol, D, asum, spinc, b, so;
+        size_t W, Wbf, Wlo, Wd, hF, acol, D, asum, spinc, b, so;
     };
     int32_t feat_rows = 0;
     for (const HostInst &h : p->host) feat_rows += h.m;
@@ -523,10 +523,12 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
         const HostInst &h = p->host[j];
         const size_t nn = (size_t)h.npad * h.npad;
         Off &o = off[j];
-        o.W = o.Wbf = o.Wlo = SIZE_MAX;
+        o.W = o.Wbf = o.Wlo = o.Wd = SIZE_MAX;
         if (h.has_w) {
             o.W = cur;
             cur = align_up(cur + nn * 2, 256);
+            o.Wd = cur;
+            cur = align_up(cur + (size_t)h.npad * 16 * 4, 256);
             o.Wbf = cur;
             cur = align_up(cur + nn * 2, 256);
             if (h.need_lo) {
@@ -602,6 +604,12 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
                     Wb[e] = hi;
                     if (Wl) Wl[e] = bf16_bits((float)w - bf16_value(hi));
                 }
+            float *Wd = reinterpret_cast<float *>(stage.data() + o.Wd);
+            for (int32_t i = 0; i < h.n; ++i)
+                for (int32_t jj = (i / 16) * 16; jj < std::min(h.n, (i / 16) * 16 + 16); ++jj)
+                    Wd[(size_t)(i / 16) * 256 + (i % 16) * 16 + (jj % 16)] =
+                        (float)h.W[(size_t)i * h.n + jj];
+            r.Wdiag = reinterpret_cast<const float *>(base + o.Wd);
             r.W = reinterpret_cast<const int16_t *>(base + o.W);
             r.Wbf = reinterpret_cast<const uint16_t *>(base + o.Wbf);
             r.Wbf_lo = h.need_lo ? reinterpret_cast<const uint16_t *>(base + o.Wlo) : nullptr;

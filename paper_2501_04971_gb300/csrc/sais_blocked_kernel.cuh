@@ -351,14 +351,26 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                     const int s = s0 + ii;
                     // Row s of the block's W columns (only the part right of spin ii is used):
                     // loaded ahead of the decision so that it is ready if any chain flips.
+                    // W streamed (K = 16): the block's 16 x 16 diagonal tile of W in FP32
+                    // (exact, hi and lo already added; the same address for every lane), the
+                    // quads right of spin ii -- measured faster than the BF16 tile columns here.
+                    // W resident: its BF16 columns in shared memory (faster there).
                     uint4 wrow[K / 8], wrlo[K / 8];
+                    float4 wq[4];
+                    if constexpr (K == 16 && kStream) {
+                        const float4 *wd4 = reinterpret_cast<const float4 *>(
+                            ip->Wdiag + (size_t)(s0 / 16) * 256 + ii * 16);
 #pragma unroll
-                    for (int cc = (ii + 1) >> 3; cc < K / 8; ++cc) {
-                        wrow[cc] = *reinterpret_cast<const uint4 *>(
-                            wblk + ((size_t)cc * npad + s) * 16);
-                        if (kHiLo)
-                            wrlo[cc] = *reinterpret_cast<const uint4 *>(
-                                wblk + tile_bytes + ((size_t)cc * npad + s) * 16);
+                        for (int q = (ii + 1) >> 2; q < 4; ++q) wq[q] = __ldg(wd4 + q);
+                    } else {
+#pragma unroll
+                        for (int cc = (ii + 1) >> 3; cc < K / 8; ++cc) {
+                            wrow[cc] = *reinterpret_cast<const uint4 *>(
+                                wblk + ((size_t)cc * npad + s) * 16);
+                            if (kHiLo)
+                                wrlo[cc] = *reinterpret_cast<const uint4 *>(
+                                    wblk + tile_bytes + ((size_t)cc * npad + s) * 16);
+                        }
                     }
                     {
                         const float Fi = Fr[ii];
@@ -415,9 +427,15 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                                 return __uint_as_float((e & 1) ? (u & 0xFFFF0000u) : (u << 16));
                             };
                             auto wcol = [&](int jj) -> float {
-                                float w = half(wrow[jj >> 3], jj & 7);
-                                if (kHiLo) w += half(wrlo[jj >> 3], jj & 7);   // exact: integers
-                                return w;
+                                if constexpr (K == 16 && kStream) {
+                                    const float4 &v = wq[jj >> 2];
+                                    const int e = jj & 3;
+                                    return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+                                } else {
+                                    float w = half(wrow[jj >> 3], jj & 7);
+                                    if (kHiLo) w += half(wrlo[jj >> 3], jj & 7);   // exact
+                                    return w;
+                                }
                             };
                             Fr[ii + 1] = fmaf(df, wcol(ii + 1), Fr[ii + 1]);
                             if (ii + 2 < K && __any_sync(0xffffffffu, d != 0)) {

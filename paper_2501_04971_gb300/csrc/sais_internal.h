@@ -43,6 +43,9 @@ struct InstDev {
     // element (j, s) at index ((s/8) npad + j) 8 + s%8; Wbf_lo holds W - Wbf when |W| > 256.
     const uint16_t *Wbf;
     const uint16_t *Wbf_lo;
+    // The 16 x 16 diagonal blocks of W as FP32 (exact integers), block b at 256 b, row-major:
+    // the in-block corrections of the blocked sampler when W is streamed (NULL if !has_w).
+    const float *Wdiag;
 };
 
 // Arguments of one sampling launch over all instances of a handle.
