@@ -265,7 +265,8 @@ SAIS_API sais_status sais_solve(sais_problem *p, const sais_solve_params *prm,
  * variant for callers that cannot allocate memory while they run (a real-time or latency-
  * critical loop that must not enter the allocator, a host that plans every byte of device memory
  * up front, a plug-in handed only its own buffers).  Same parameters and results as sais_solve
- * (use_graph must be 0); the device scratch lives in one static array of 16 MiB that every GPU
+ * (use_graph must be 0, variant SAIS_PLAIN or SAIS_BLOCKED: SAIS_AUTO may allocate its work
+ * list); the device scratch lives in one static array of 16 MiB that every GPU
  * loading the library holds until the process exits, and the call makes no cudaMalloc, cudaFree,
  * event or graph call, host or device.
  *  - The first call on a device looks up the array's address (with that device current); make

@@ -59,6 +59,10 @@ extern "C" sais_status sais_solve_noalloc(sais_problem *p, const sais_solve_para
     if (prm->use_graph)
         return set_error(SAIS_EINVAL,
                          "sais_solve_noalloc does not build CUDA graphs (use_graph must be 0)");
+    if (prm->variant == SAIS_AUTO)
+        return set_error(SAIS_EINVAL,
+                         "sais_solve_noalloc takes SAIS_PLAIN or SAIS_BLOCKED (SAIS_AUTO may "
+                         "allocate its work list)");
     ProblemView v;
     sais_status st = problem_view(p, &v);
     if (st != SAIS_OK) return st;

@@ -78,3 +78,10 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     st, got = _noalloc(prob, 2, 32, 20, 10.0, 20.0, 1)   # a size that fits still works after it
     assert st == sais.SAIS_OK, sais.sais_last_error()
     prob.close()
+
+
+def test_noalloc_rejects_auto_variant():
+    prob = sais.Problem([wl.qkp(60, 0.5, 6)])
+    st, _ = _noalloc(prob, 2, 32, 10, 10.0, 20.0, 1, variant="auto")
+    assert st == sais.SAIS_EINVAL and "SAIS_AUTO" in sais.sais_last_error()
+    prob.close()
