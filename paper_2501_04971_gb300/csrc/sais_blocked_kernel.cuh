@@ -272,6 +272,12 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                 c[k] = 0.f;
             }
         }
+        // The constraint values as FP32 too (exact: |g| < 2^24, checked at creation), so that the
+        // decision chain updates them and c_k without integer <-> float conversions; the int32
+        // copy is refreshed from them where it is needed (exact re-runs, readout).
+        float gf[MC];
+#pragma unroll
+        for (int k = 0; k < MC; ++k) gf[k] = (float)g[k];
         const float errk = field_err_factor(m);
         // Fault-injection test (dec_wait_polls > 0): wait on a barrier nothing completes, so the
         // bound expires and the kernel takes its timeout path.
@@ -337,12 +343,11 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                 uint32_t xw = xs[wi * kLanes + r];
                 const uint32_t xold = xw;
                 // Block-start chain state, kept for an exact re-run of the block.
-                int32_t g0[MC];
-                float cb[MC];
+                float gf0[MC], cb[MC];
                 const float M0 = Mmax;
 #pragma unroll
                 for (int k = 0; k < MC; ++k) {
-                    g0[k] = g[k];
+                    gf0[k] = gf[k];
                     cb[k] = c[k];
                 }
                 bool near_tie = false;
@@ -375,16 +380,16 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                     {
                         const float Fi = Fr[ii];
                         const int xi = (xw >> (sb + ii)) & 1;
-                        int32_t ak[MC];
+                        float akf[MC];
                         float acc = sf * Fi;
                         const float tabs = fabsf(acc);
 #pragma unroll
                         for (int k = 0; k < MC; ++k) {
                             if (k < kPreM)
-                                ak[k] = Ap[ii][k < kPreM ? k : 0];
+                                akf[k] = (float)Ap[ii][k < kPreM ? k : 0];
                             else
-                                ak[k] = (k < m) ? __ldg(acol + (size_t)s * m + k) : 0;
-                            acc = fmaf(-(float)ak[k], c[k], acc);
+                                akf[k] = (k < m) ? (float)__ldg(acol + (size_t)s * m + k) : 0.f;
+                            acc = fmaf(-akf[k], c[k], acc);
                         }
                         const float Di = Dp[ii];
                         acc = fmaf(xi ? 1.f : -1.f, Di, acc);
@@ -395,20 +400,19 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                                             kThetaRelErr * fabsf(theta) + kThetaAbsErr;
                         // A decision the FP32 bound cannot settle is only flagged here; the
                         // warp then re-runs the block below with the FP64 path.
-                        const int xn = y > 0.f;
                         near_tie |= !(fabsf(y) > bound);
-                        const int d = xn - xi;
+                        // The flip d = x_new - x_i in {-1, 0, +1}, kept as FP32.
+                        const float df = (y > 0.f ? 1.f : 0.f) - (xi ? 1.f : 0.f);
                         // Constraint state follows the flip without a branch (d = 0 leaves every
                         // value bit-identical).
-                        xw ^= (uint32_t)(d != 0) << (sb + ii);
+                        xw ^= (uint32_t)(df != 0.f) << (sb + ii);
                         Mmax = 0.f;
 #pragma unroll
                         for (int k = 0; k < MC; ++k) {
                             if (k < m) {
-                                g[k] += ak[k] * d;
-                                c[k] = fmaf(kappa, (float)g[k], cA[k]);
-                                Mmax = fmaxf(Mmax, fmaf(fabsf(kappa), fabsf((float)g[k]),
-                                                        fabsf(cA[k])));
+                                gf[k] = fmaf(akf[k], df, gf[k]);   // exact integers
+                                c[k] = fmaf(kappa, gf[k], cA[k]);
+                                Mmax = fmaxf(Mmax, fmaf(fabsf(kappa), fabsf(gf[k]), fabsf(cA[k])));
                             }
                         }
                         if (ii + 1 < K) {
@@ -417,7 +421,6 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                             // The next spin's field is on the dependency chain: corrected
                             // unconditionally (d = 0 adds an exact zero); the others only when a
                             // chain of the warp flipped.
-                            const float df = (float)d;
                             // BF16 value of column jj of the row (jj is a compile-time
                             // constant after unrolling; no local arrays, so nothing goes to the
                             // stack)
@@ -438,7 +441,7 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                                 }
                             };
                             Fr[ii + 1] = fmaf(df, wcol(ii + 1), Fr[ii + 1]);
-                            if (ii + 2 < K && __any_sync(0xffffffffu, d != 0)) {
+                            if (ii + 2 < K && __any_sync(0xffffffffu, df != 0.f)) {
 #pragma unroll
                                 for (int jj = ii + 2; jj < K; ++jj)
                                     Fr[jj] = fmaf(df, wcol(jj), Fr[jj]);
@@ -455,7 +458,7 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                     Mmax = M0;
 #pragma unroll
                     for (int k = 0; k < MC; ++k) {
-                        g[k] = g0[k];
+                        g[k] = (int32_t)gf0[k];
                         c[k] = cb[k];
                     }
 #pragma unroll 1
@@ -521,6 +524,8 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                             }
                         }
                     }
+#pragma unroll
+                    for (int k = 0; k < MC; ++k) gf[k] = (float)g[k];
                 }
                 xs[wi * kLanes + r] = xw;
                 // Delta of the block (BF16 -1, 0, +1) into this chain's TMEM row of the MMA's A
@@ -616,6 +621,8 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                     }
                 }
             }
+#pragma unroll
+            for (int k = 0; k < MC; ++k) g[k] = (int32_t)gf[k];
             if (valid) {
                 const size_t cidx = (size_t)j * a.chains + chain;
                 for (int w = 0; w < a.words; ++w)
