@@ -282,6 +282,11 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 c[k] = 0.f;
             }
         }
+        // Constraint values as FP32 too (exact: |g| < 2^24), updated on the decision chain without
+        // conversions; the int32 copy is refreshed where needed (exact re-runs, readout).
+        float gf[MC];
+#pragma unroll
+        for (int k = 0; k < MC; ++k) gf[k] = (float)g[k];
         const float errk = field_err_factor(m);
         bool ok = polls > 0 ? p_wait_warp<false>(&bars[0], 0, abort_flag, status, polls) : true;
         uint32_t it = 0, ib = 0, cons_par = 0u;   // bit s: parity of Delta slot s's next fill
@@ -355,12 +360,11 @@ __global__ void __launch_bounds__(kPThreads, 1)
 #pragma unroll
                         for (int ii = 0; ii < kPK; ++ii) Fr[ii] = 0.f;   // slack spins: F = 0
                     }
-                    int32_t g0[MC];
-                    float cb[MC];
+                    float gf0[MC], cb[MC];
                     const float M0 = Mmax;
 #pragma unroll
                     for (int k = 0; k < MC; ++k) {
-                        g0[k] = g[k];
+                        gf0[k] = gf[k];
                         cb[k] = c[k];
                     }
                     bool near_tie = false;
@@ -379,16 +383,16 @@ __global__ void __launch_bounds__(kPThreads, 1)
                         }
                         const float Fi = Fr[ii];
                         const int xi = (xw >> (sb + ii)) & 1;
-                        int32_t ak[MC];
+                        float akf[MC];
                         float acc = sf * Fi;
                         const float tabs = fabsf(acc);
 #pragma unroll
                         for (int k = 0; k < MC; ++k) {
                             if (k < kPreM)
-                                ak[k] = Ap[ii][k < kPreM ? k : 0];
+                                akf[k] = (float)Ap[ii][k < kPreM ? k : 0];
                             else
-                                ak[k] = (k < m) ? __ldg(acol + (size_t)s * m + k) : 0;
-                            acc = fmaf(-(float)ak[k], c[k], acc);
+                                akf[k] = (k < m) ? (float)__ldg(acol + (size_t)s * m + k) : 0.f;
+                            acc = fmaf(-akf[k], c[k], acc);
                         }
                         const float Di = Dp[ii];
                         acc = fmaf(xi ? 1.f : -1.f, Di, acc);
@@ -397,18 +401,16 @@ __global__ void __launch_bounds__(kPThreads, 1)
                         const float y = z + theta;
                         const float bound = ez * (tabs + Sp[ii] * Mmax + Di) +
                                             kThetaRelErr * fabsf(theta) + kThetaAbsErr;
-                        const int xn = y > 0.f;
                         near_tie |= !(fabsf(y) > bound);
-                        const int d = xn - xi;
-                        xw ^= (uint32_t)(d != 0) << (sb + ii);
+                        const float df = (y > 0.f ? 1.f : 0.f) - (xi ? 1.f : 0.f);
+                        xw ^= (uint32_t)(df != 0.f) << (sb + ii);
                         Mmax = 0.f;
 #pragma unroll
                         for (int k = 0; k < MC; ++k) {
                             if (k < m) {
-                                g[k] += ak[k] * d;
-                                c[k] = fmaf(kappa, (float)g[k], cA[k]);
-                                Mmax = fmaxf(Mmax, fmaf(fabsf(kappa), fabsf((float)g[k]),
-                                                        fabsf(cA[k])));
+                                gf[k] = fmaf(akf[k], df, gf[k]);   // exact integers
+                                c[k] = fmaf(kappa, gf[k], cA[k]);
+                                Mmax = fmaxf(Mmax, fmaf(fabsf(kappa), fabsf(gf[k]), fabsf(cA[k])));
                             }
                         }
                         if (item && ii + 1 < kPK) {
@@ -417,7 +419,6 @@ __global__ void __launch_bounds__(kPThreads, 1)
                             // The next spin's field is on the dependency chain: corrected
                             // unconditionally (d = 0 adds an exact zero); the others only when a
                             // chain of the warp flipped.
-                            const float df = (float)d;
                             // BF16 value of column jj of the row (jj is a compile-time
                             // constant after unrolling; no local arrays, so nothing goes to the
                             // stack)
@@ -432,7 +433,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
                                 return w;
                             };
                             Fr[ii + 1] = fmaf(df, wcol(ii + 1), Fr[ii + 1]);
-                            if (ii + 2 < kPK && __any_sync(0xffffffffu, d != 0)) {
+                            if (ii + 2 < kPK && __any_sync(0xffffffffu, df != 0.f)) {
 #pragma unroll
                                 for (int jj = ii + 2; jj < kPK; ++jj)
                                     Fr[jj] = fmaf(df, wcol(jj), Fr[jj]);
@@ -447,7 +448,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
                         Mmax = M0;
 #pragma unroll
                         for (int k = 0; k < MC; ++k) {
-                            g[k] = g0[k];
+                            g[k] = (int32_t)gf0[k];
                             c[k] = cb[k];
                         }
 #pragma unroll 1
@@ -516,6 +517,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
                                 }
                             }
                         }
+#pragma unroll
+                        for (int k = 0; k < MC; ++k) gf[k] = (float)g[k];
                     }
                     xs[wi * kPLanes + r] = xw;
                     if (item) {
@@ -568,17 +571,18 @@ __global__ void __launch_bounds__(kPThreads, 1)
 #pragma unroll
                         for (int k = 0; k < MC; ++k) {
                             if (k < kPreM)
-                                g[k] += Ap[ii][k < kPreM ? k : 0] * d;
+                                gf[k] = fmaf((float)Ap[ii][k < kPreM ? k : 0], (float)d, gf[k]);
                             else if (k < m && d != 0)
-                                g[k] += __ldg(acol + (size_t)(s0 + ii) * m + k) * d;
+                                gf[k] = fmaf((float)__ldg(acol + (size_t)(s0 + ii) * m + k),
+                                             (float)d, gf[k]);
                         }
                     }
                     Mmax = 0.f;
 #pragma unroll
                     for (int k = 0; k < MC; ++k) {
                         if (k < m) {
-                            c[k] = fmaf(kappa, (float)g[k], cA[k]);
-                            Mmax = fmaxf(Mmax, fmaf(fabsf(kappa), fabsf((float)g[k]), fabsf(cA[k])));
+                            c[k] = fmaf(kappa, gf[k], cA[k]);
+                            Mmax = fmaxf(Mmax, fmaf(fabsf(kappa), fabsf(gf[k]), fabsf(cA[k])));
                         }
                     }
                     xs[wi * kPLanes + r] = xw;
@@ -671,7 +675,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
         else
             part[r] = sumF;
 #pragma unroll
-        for (int k = 0; k < MC; ++k) gout[r * kMaxBlockedConstraints + k] = g[k];
+        for (int k = 0; k < MC; ++k) gout[r * kMaxBlockedConstraints + k] = (int32_t)gf[k];
         if (lane == 0) warp_ok[warp] = ok ? 1 : 0;
         __syncwarp();
     }
