@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-gap", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--gap-instances", type=int, default=32)
+    ap.add_argument("--gap-instances", type=int, default=16, help="per density")
     ap.add_argument("--gap-iters", type=int, default=100)
     ap.add_argument("--gap-eta", type=float, default=2000.0)
     ap.add_argument("--no-ragged", action="store_true")
@@ -206,14 +206,18 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------
 
 def gap_measurement(a, sais, torch, variants):
-    """Best-known profit per instance = best feasible sample of blocked runs (4 seeds x
-    `gap_iters` iterations; uncertified).  Then, per variant, Algorithm 1
-    from lambda = 0 with a fresh seed, one iteration at a time through the C-ABI; the time to a
+    """Wall-clock to a 1 % gap on QKP N=300 at each density (`gap_instances` instances per
+    density, one batch).  Best-known profit per instance = best feasible sample of runs of the
+    first variant (4 seeds x `gap_iters` iterations; uncertified).  Then, per variant, Algorithm
+    1 from lambda = 0 with a fresh seed, one iteration at a time through the C-ABI; the time to a
     1 % gap of an instance is the device time (CUDA events) of the iterations until its best
     feasible profit reaches 0.99 x best-known.  Both variants draw identical samples, so they
     need the same number of iterations; their times differ by the per-iteration cost."""
     from paper_2501_04971_gb300 import workloads as wl
-    insts = [wl.qkp(300, 0.5, 5000 + i) for i in range(a.gap_instances)]
+    per = a.gap_instances
+    insts = [wl.qkp(300, d, 5000 + 100 * q + i) for q, d in enumerate(DENSITIES)
+             for i in range(per)]
+    dens = np.repeat(np.array(DENSITIES), per)
     prob = sais.Problem(insts)
     C, T, beta, eta = a.chains, a.sweeps, a.beta_max, a.gap_eta
     best_known = np.full(prob.count, np.iinfo(np.int64).max, np.int64)
@@ -221,9 +225,11 @@ def gap_measurement(a, sais, torch, variants):
     for seed in range(4):
         r = prob.solve(a.gap_iters, C, T, beta, eta, 777 + seed, variant=ref_variant)
         best_known = np.minimum(best_known, r["best_cost"])
-    out = {"instances": prob.count, "workload": "QKP N=300 d=0.5, %d chains x %d sweeps per "
-           "iteration, beta_max %g, P = 2dN, eta %g (normalised units)" % (C, T, beta, eta),
-           "best_known": "best of 4 seeds x %d iterations (blocked), uncertified" % a.gap_iters}
+    out = {"instances": prob.count, "workload": "QKP N=300, d in {0.25,0.5,0.75,1} x %d, %d "
+           "chains x %d sweeps per iteration, beta_max %g, P = 2dN, eta %g (normalised units)"
+           % (per, C, T, beta, eta),
+           "best_known": "best of 4 seeds x %d iterations (%s), uncertified"
+           % (a.gap_iters, ref_variant)}
     stream = torch.cuda.current_stream()
     for v in variants:
         lam = torch.zeros(prob.count * prob.m_stride, device="cuda")
@@ -245,13 +251,20 @@ def gap_measurement(a, sais, torch, variants):
             reached[np.isnan(reached) & hit] = t_acc
             if not np.isnan(reached).any():
                 break
-        ok = ~np.isnan(reached)
-        out[v] = {"reached": int(ok.sum()),
-                  "median_s": float(np.median(reached[ok])) if ok.any() else None,
-                  "p90_s": float(np.percentile(reached[ok], 90)) if ok.any() else None,
-                  "iterations_run": k + 1}
-    if all(out.get(v, {}).get("median_s") for v in ("blocked", "plain")):
-        out["speedup_median"] = out["plain"]["median_s"] / out["blocked"]["median_s"]
+
+        def stats(mask):
+            rr = reached[mask]
+            ok = ~np.isnan(rr)
+            return {"reached": int(ok.sum()), "of": int(mask.sum()),
+                    "median_s": float(np.median(rr[ok])) if ok.any() else None,
+                    "p90_s": float(np.percentile(rr[ok], 90)) if ok.any() else None}
+        out[v] = {"all": stats(np.ones(prob.count, bool)), "iterations_run": k + 1,
+                  "by_density": {str(d): stats(dens == d) for d in DENSITIES}}
+    if all(out.get(v, {}).get("all", {}).get("median_s") for v in ("blocked", "plain")):
+        out["speedup_median"] = out["plain"]["all"]["median_s"] / out["blocked"]["all"]["median_s"]
+        d5 = [out[v]["by_density"]["0.5"]["median_s"] for v in ("plain", "blocked")]
+        if all(d5):
+            out["speedup_median_d0.5"] = d5[0] / d5[1]
     prob.close()
     return out
 
@@ -440,7 +453,7 @@ def main():
         # DRAM bytes (read + write) per instance of one launch of this kernel, measured with ncu
         # on a 640-instance, 10-sweep launch (W is read once per CTA, so traffic scales with
         # instances, not sweeps)
-        traffic = 219330.0 * prob.count if (a.chains == 128 and a.block_k in (0, 16)) else None
+        traffic = 218700.0 * prob.count if (a.chains == 128 and a.block_k in (0, 16)) else None
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
             if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
         peak = peaks.get("bf16_tflops", 1900.0) * 1e12
