@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--gap-iters", type=int, default=100)
     ap.add_argument("--gap-eta", type=float, default=2000.0)
     ap.add_argument("--no-ragged", action="store_true")
+    ap.add_argument("--penalty", action="store_true",
+                    help="also compare with the penalty method (eta = 0, scaled P)")
     ap.add_argument("--warmstart", action="store_true",
                     help="also run the learned warm start: labels, training, evaluation")
     ap.add_argument("--ws-train", type=int, default=20000)
@@ -266,6 +268,43 @@ def gap_measurement(a, sais, torch, variants):
         if all(d5):
             out["speedup_median_d0.5"] = d5[0] / d5[1]
     prob.close()
+    return out
+
+
+def penalty_measurement(a, sais, torch):
+    """SAIM against the penalty method at an equal sample budget (the comparison of Table II,
+    on synthetic instances): the same instances as the gap measurement (QKP N=300, four
+    densities), Algorithm 1 with the multiplier step (eta = gap_eta, P = 2dN) and without it
+    (eta = 0, lambda = 0: a fixed penalty P = s 2dN for s in 1..64), each `gap_iters`
+    iterations x `chains` chains x `sweeps` sweeps, one CUDA graph per run.  Best-known profit
+    per instance = the best feasible sample of all these runs (uncertified)."""
+    import dataclasses
+    from paper_2501_04971_gb300 import workloads as wl
+    per = a.gap_instances
+    base = [wl.qkp(300, d, 5000 + 100 * q + i) for q, d in enumerate(DENSITIES)
+            for i in range(per)]
+    C, T, beta, K = a.chains, a.sweeps, a.beta_max, a.gap_iters
+    runs = {}
+    for name, scale, eta in [("saim", 1.0, a.gap_eta)] + \
+            [("penalty_x%d" % s_, float(s_), 0.0) for s_ in (1, 2, 4, 8, 16, 32, 64)]:
+        insts = [dataclasses.replace(i, alpha=i.alpha * scale) for i in base]
+        prob = sais.Problem(insts)
+        r = prob.solve(K, C, T, beta, eta, 31337, variant="auto", use_graph=True)
+        runs[name] = (r["best_cost"].copy(), r["feasible_count"].copy(), r["elapsed_ms"])
+        prob.close()
+    none = np.iinfo(np.int64).max
+    best = np.min(np.stack([v[0] for v in runs.values()]), axis=0)
+    samples = K * C
+    out = {"instances": len(base), "budget": "%d iterations x %d chains x %d sweeps" % (K, C, T),
+           "best_known": "best feasible sample over all runs below (uncertified)"}
+    for name, (bc, fc, ms) in runs.items():
+        feas = bc != none
+        gap = np.where(feas & (best != none), (bc - best) / np.abs(best.astype(np.float64)), 1.0)
+        out[name] = {"within_1pct": int(((gap <= 0.01) & feas).sum()),
+                     "any_feasible": int(feas.sum()),
+                     "median_gap": float(np.median(gap)),
+                     "feasible_sample_fraction": float(fc.sum() / (samples * len(base))),
+                     "device_ms": ms}
     return out
 
 
@@ -535,6 +574,9 @@ def main():
     ragged = None
     if not a.no_ragged and world == 1:
         ragged = ragged_measurement(a, sais, torch)
+    pen = None
+    if a.penalty and world == 1:
+        pen = penalty_measurement(a, sais, torch)
     warm = None
     if a.warmstart and world == 1:
         warm = warmstart_measurement(a, sais, torch)
@@ -560,6 +602,8 @@ def main():
             "gpu_launches": 3 * a.steps, "clocks": clk.summary(),
             "updates_per_step": upd_step, "plain": plain_cmp, "gap_1pct": gap,
             "ragged": ragged}
+    if pen is not None:
+        line["penalty_vs_saim"] = pen
     if warm is not None:
         line["warmstart"] = warm
     print(json.dumps(line), flush=True)
