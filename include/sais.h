@@ -106,6 +106,8 @@ typedef struct sais_layout {
     int32_t has_quadratic;   /* 1 if any instance has W                                     */
 } sais_layout;
 
+/* SAIS_PLAIN and SAIS_BLOCKED take at most 65535 instances per handle (one grid row each);
+ * SAIS_AUTO takes any number. */
 typedef enum sais_variant {
     SAIS_PLAIN = 0,          /* per-spin sampler: FP32 fields, rank-1 update on every flip  */
     SAIS_BLOCKED = 1,        /* k spins per block, rank-k field update on the tensor cores  */

@@ -732,6 +732,10 @@ sais_status check_sample_params(const sais_problem *p, const sais_sample_params 
         return fail(SAIS_EINVAL, "block_k = %d: need 0, 16, 32 or 64", prm->block_k);
     if (prm->debug_wait_polls < 0)
         return fail(SAIS_EINVAL, "debug_wait_polls = %d: need >= 0", prm->debug_wait_polls);
+    if (prm->variant != SAIS_AUTO && p->count > 65535)
+        return fail(SAIS_EUNSUPPORTED,
+                    "%d instances: SAIS_PLAIN / SAIS_BLOCKED launch one grid row per instance "
+                    "(at most 65535); SAIS_AUTO has no such limit", p->count);
     return SAIS_OK;
 }
 
