@@ -427,7 +427,12 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     import __graft_entry__
+    # one rank compiles (concurrent builds would write the same objects); the others load
+    if dist and rank != 0:
+        dist.barrier()
     __graft_entry__.build()
+    if dist and rank == 0:
+        dist.barrier()
     from paper_2501_04971_gb300 import sais
 
     insts = workload(a.per_density, rank)
