@@ -191,6 +191,35 @@ def test_pair_timeout_path_reports_and_recovers():
     prob.close()
 
 
+def _with_constraints(inst, m, seed):
+    """The QKP objective of `inst` with m random knapsack constraints instead of one."""
+    import dataclasses
+    r = np.random.default_rng(seed)
+    A = r.integers(0, 50, (m, inst.n)).astype(np.int32)
+    b = np.maximum(1, (A.sum(axis=1) // 3)).astype(np.int64)
+    return dataclasses.replace(inst, m=m, A=A, b=b)
+
+
+@pytest.mark.parametrize("case", ["unconstrained", "m8", "m3_streamed"])
+def test_blocked_constraint_counts(case):
+    """Blocked sampler at its constraint extremes: no constraint (m = 0) and m = 8 (its limit),
+    resident and streamed W."""
+    if case == "unconstrained":
+        inst = wl.qkp(90, 0.5, 41)
+        import dataclasses
+        inst = dataclasses.replace(inst, m=0, A=np.zeros((0, 90), np.int32),
+                                   b=np.zeros(0, np.int64))
+        _compare([inst], [[]], C=128, T=60, beta=10.0, seed=19, it=0, block_k=16)
+    elif case == "m8":
+        inst = _with_constraints(wl.qkp(120, 0.5, 42), 8, 42)
+        _compare([inst], [list(np.linspace(0.1, 2.0, 8))], C=128, T=60, beta=10.0, seed=20,
+                 it=1, block_k=16)
+    else:
+        inst = _with_constraints(wl.qkp(380, 0.5, 43), 3, 43)
+        _compare([inst], [[0.5, 1.0, 1.5]], C=128, T=30, beta=10.0, seed=21, it=2, block_k=16,
+                 oracle_chains=(0, 2))
+
+
 def test_blocked_unsupported_cases():
     cases = ([wl.mkp(40, 3, 1)], [wl.qkp(1100, 0.25, 2)], [wl.qkp(600, 0.5, 3), wl.qkp(40, 0.5, 4)])
     for insts in cases:

@@ -93,7 +93,8 @@ def test_states_match_oracle_qkp_n100():
 
 
 @pytest.mark.parametrize("case", ["unconstrained", "mkp", "ragged_chains", "one_sweep",
-                                  "mixed_batch", "table1_qkp", "negative_lambda", "big_profits"])
+                                  "mixed_batch", "table1_qkp", "negative_lambda", "big_profits",
+                                  "max_constraints", "single_item", "one_chain", "beta_zero"])
 def test_states_match_oracle_edge_cases(case):
     if case == "unconstrained":
         inst = wl.qkp(33, 0.5, 4)
@@ -121,6 +122,19 @@ def test_states_match_oracle_edge_cases(case):
     elif case == "big_profits":
         _sample_and_compare([wl.qkp(120, 0.5, 12, profit_max=10000)], [[1.5]], C=32, T=60,
                             beta_max=10.0, seed=9, it=0)
+    elif case == "max_constraints":   # m = 32, the most the samplers keep in registers
+        lam = list(np.linspace(0.0, 1.5, 32))
+        _sample_and_compare([wl.mkp(50, 32, 13)], [lam], C=32, T=30, beta_max=10.0, seed=10,
+                            it=1)
+    elif case == "single_item":
+        inst = wl.qkp(1, 1.0, 14)
+        _sample_and_compare([inst], [[0.3]], C=32, T=20, beta_max=10.0, seed=11, it=0)
+    elif case == "one_chain":
+        _sample_and_compare([wl.qkp(80, 0.5, 15)], [[0.6]], C=1, T=100, beta_max=10.0, seed=12,
+                            it=3)
+    else:   # beta_max = 0: every sweep samples the uniform distribution
+        _sample_and_compare([wl.qkp(60, 0.5, 16)], [[0.6]], C=64, T=5, beta_max=0.0, seed=13,
+                            it=0)
 
 
 def test_teacher_forced_decisions_config0():
