@@ -220,6 +220,23 @@ def test_blocked_constraint_counts(case):
                  oracle_chains=(0, 2))
 
 
+@pytest.mark.parametrize("case", ["one_chain", "m8", "three_clusters"])
+def test_pair_sampler_extremes(case):
+    """The CTA-pair sampler with a single valid chain, with 8 constraints (the follower's
+    update reads the coefficients past the first two from global memory), and with 300 chains
+    (three clusters per instance, the last one ragged)."""
+    if case == "one_chain":
+        _compare([wl.qkp(520, 0.5, 51)], [[1.0]], C=1, T=20, beta=10.0, seed=22, it=0,
+                 block_k=16)
+    elif case == "m8":
+        inst = _with_constraints(wl.qkp(600, 0.5, 52), 8, 52)
+        _compare([inst], [list(np.linspace(0.2, 1.6, 8))], C=128, T=16, beta=10.0, seed=23,
+                 it=1, block_k=16, oracle_chains=(0, 1))
+    else:
+        _compare([wl.qkp(470, 0.75, 53)], [[0.9]], C=300, T=16, beta=10.0, seed=24, it=2,
+                 block_k=16, oracle_chains=(290, 2))
+
+
 def test_blocked_unsupported_cases():
     cases = ([wl.mkp(40, 3, 1)], [wl.qkp(1100, 0.25, 2)], [wl.qkp(600, 0.5, 3), wl.qkp(40, 0.5, 4)])
     for insts in cases:
