@@ -72,8 +72,10 @@ _SIGS = {
     "or_replay_sweep": (_i32, [_i32, _P, _P, _f32, _u64, _u32, _u32, _u32, _P, _P, _P, _P,
                                _i32]),
     "or_lambda_update": (None, [_i32, _P, _i64, _f64, _i32, _f32, _P]),
-    "or_solve": (None, [_i32, _i32, _P, _P, _P, _P, _f32, _f32, _f32, _i32, _i32, _i32, _f32,
-                        _f64, _u64, _u32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "or_run_best": (None, [_i32, _i32, _i32, _P, _P, _P, _P, _i32, _i32, _P, _P, _P, _P, _P]),
+    "or_solve": (None, [_i32, _i32, _P, _P, _P, _P, _P, _f32, _f32, _f32, _i32, _i32, _i32,
+                        _f32, _f64, _u64, _u32, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P,
+                        _P]),
     "or_enumerate_lagrangian": (None, [_i32, _i32, _i32, _P, _P, _P, _P, _P, _f32, _f32, _f32,
                                        _P]),
     "or_brute_force_opt": (_i64, [_i32, _i32, _P, _P, _P, _P, _P]),
@@ -124,6 +126,9 @@ class Problem:
     alpha: float = 2.0
     density: float = -1.0
     penalty: float = 0.0
+    # Capacities that feasibility is checked against (None: b).  Capacity tightening B' < B
+    # (Sec. IV-B): b holds the reduced B' that L is built from, b_check the true B.
+    b_check: Optional[np.ndarray] = None
 
     def __post_init__(self):
         lib = load()
@@ -131,6 +136,7 @@ class Problem:
         self.h = _c(self.h, np.int64)
         self.A = _c(np.asarray(self.A).reshape(self.m, self.n), np.int64)
         self.b = _c(self.b, np.int64)
+        self.b_check = _c(self.b if self.b_check is None else self.b_check, np.int64)
         self.nprime = int(lib.or_num_spins(self.n, self.m, _ptr(self.b)))
         self.Q = np.array([lib.or_slack_bits(int(v)) for v in self.b], dtype=np.int32)
         self.Aext = np.zeros((self.m, self.nprime), dtype=np.int64)
@@ -155,7 +161,8 @@ class Problem:
 
     def feasible(self, x) -> bool:
         x = _c(x, np.uint8)
-        return bool(load().or_feasible(self.n, self.m, _ptr(self.A), _ptr(self.b), _ptr(x)))
+        return bool(load().or_feasible(self.n, self.m, _ptr(self.A), _ptr(self.b_check),
+                                       _ptr(x)))
 
     # --- Eq. 3 and 5 ----------------------------------------------------------------------
     def lagrangian(self, x, lam) -> float:
@@ -262,6 +269,22 @@ def replay_sweep(J, hI, beta_: float, seed: int, it: int, chain: int, t: int, x0
     return int(nbad), spins[:k].copy(), margins[:k].copy()
 
 
+def run_best(p: Problem, trace):
+    """Best feasible sweep-end state of every run (see or_run_best in saim_oracle.c) from a
+    trace (C x T x N' bytes, as returned by anneal): (cost C, states C x N', sweep C,
+    feasible sweep-end states C); cost INT64_MAX, state 0 and sweep -1 where none."""
+    tr = _c(trace, np.uint8)
+    C, T, N = tr.shape
+    assert N == p.nprime
+    cost = np.zeros(C, np.int64)
+    x = np.zeros((C, N), np.uint8)
+    sweep = np.zeros(C, np.int32)
+    nfeas = np.zeros(C, np.int32)
+    load().or_run_best(p.n, p.m, N, _ptr(p.W), _ptr(p.h), _ptr(p.A), _ptr(p.b_check), C, T,
+                       _ptr(tr), _ptr(cost), _ptr(x), _ptr(sweep), _ptr(nfeas))
+    return cost, x, sweep, nfeas
+
+
 def lambda_update(gsum, C: int, eta: float, project: bool, sigma_g, lam) -> np.ndarray:
     """Algorithm 1's multiplier step (batch mean, optional projection); returns the new lambda."""
     g = _c(gsum, np.int64)
@@ -284,8 +307,11 @@ class SolveResult:
 
 
 def solve(p: Problem, K: int, C: int, T: int, beta_max: float, eta: float, seed: int,
-          iter0: int = 0, project: bool = True, lambda0=None, keep_samples: bool = False):
-    """Algorithm 1 (Sec. III-A) with the p-bit machine of Sec. III-B as the minimiser."""
+          iter0: int = 0, project: bool = True, lambda0=None, keep_samples: bool = False,
+          run_best: bool = False):
+    """Algorithm 1 (Sec. III-A) with the p-bit machine of Sec. III-B as the minimiser.
+    Feasibility is checked against p.b_check; run_best stores each chain's best feasible
+    sweep-end state instead of its last state."""
     lib = load()
     bc = np.zeros(1, dtype=np.int64)
     bx = np.zeros(p.nprime, dtype=np.uint8)
@@ -296,8 +322,9 @@ def solve(p: Problem, K: int, C: int, T: int, beta_max: float, eta: float, seed:
     costs = np.zeros((K, C), dtype=np.int64) if keep_samples else None
     gs = np.zeros((K, C, p.m), dtype=np.int64) if keep_samples else None
     l0 = _c(lambda0, np.float32)
-    lib.or_solve(p.n, p.m, _ptr(p.W), _ptr(p.h), _ptr(p.A), _ptr(p.b), p.alpha, p.density,
-                 p.penalty, K, C, T, beta_max, eta, seed, iter0, int(project), _ptr(l0),
+    lib.or_solve(p.n, p.m, _ptr(p.W), _ptr(p.h), _ptr(p.A), _ptr(p.b), _ptr(p.b_check),
+                 p.alpha, p.density, p.penalty, K, C, T, beta_max, eta, seed, iter0,
+                 int(project), int(run_best), _ptr(l0),
                  _ptr(bc), _ptr(bx), _ptr(bi), _ptr(bch), _ptr(lt), _ptr(fc), _ptr(costs),
                  _ptr(gs))
     found = int(bc[0]) != np.iinfo(np.int64).max

@@ -429,20 +429,63 @@ OR_API void or_lambda_update(int32_t m, const int64_t *gsum, int64_t C, double e
     }
 }
 
+/* Best feasible state among the sweep-end states of C annealing runs.  The paper checks every
+ * measured sample for feasibility and stores the feasible ones (Sec. IV-A; Algorithm 1's "store
+ * feasible"); a run's last state is its measured sample.  This option measures the state at the
+ * end of every sweep t = 0..T-1 instead: trace[c][t] (N' bytes each).  For chain c: the states
+ * feasible under capacities b_check (items only, A x <= b_check), the one of least cost c(x)
+ * (Sec. IV-A), the earliest sweep on ties.  Outputs per chain: best_cost (INT64_MAX if none),
+ * best_x (N' bytes, zeros if none), best_sweep (-1 if none), nfeas (feasible sweep-end states;
+ * any output may be NULL). */
+OR_API void or_run_best(int32_t n, int32_t m, int32_t nprime, const int64_t *W, const int64_t *h,
+                        const int64_t *A, const int64_t *b_check, int32_t C, int32_t T,
+                        const uint8_t *trace, int64_t *best_cost, uint8_t *best_x,
+                        int32_t *best_sweep, int32_t *nfeas) {
+    for (int32_t c = 0; c < C; c++) {
+        int64_t bc = INT64_MAX;
+        int32_t bt = -1, nf = 0;
+        for (int32_t t = 0; t < T; t++) {
+            const uint8_t *x = trace + ((size_t)c * T + t) * nprime;
+            if (!or_feasible(n, m, A, b_check, x)) continue;
+            nf++;
+            const int64_t cost = or_cost(n, W, h, x);
+            if (cost < bc) {
+                bc = cost;
+                bt = t;
+            }
+        }
+        if (best_cost) best_cost[c] = bc;
+        if (best_sweep) best_sweep[c] = bt;
+        if (nfeas) nfeas[c] = nf;
+        if (best_x) {
+            uint8_t *bx = best_x + (size_t)c * nprime;
+            if (bt >= 0)
+                memcpy(bx, trace + ((size_t)c * T + bt) * nprime, (size_t)nprime);
+            else
+                memset(bx, 0, (size_t)nprime);
+        }
+    }
+}
+
 /* Algorithm 1 for K iterations k = iter0 .. iter0+K-1 on one instance.  Per iteration: J, h of
  * L_k from lambda_k; C annealing runs (the Ising machine minimising L_k); every chain's last
  * sample is checked, feasible ones are stored (only the best is kept: min cost, first achiever
- * in (k, chain) order); lambda takes the batch-mean subgradient step.
+ * in (k, chain) order); lambda takes the batch-mean subgradient step on the last samples.
+ * b_check (NULL: b) are the capacities that feasibility is checked against: the problem L is
+ * built from b, and b_check > b is the capacity tightening B' < B of Sec. IV-B (b holding B').
+ * run_best = 1: the sample stored from a chain is its best feasible sweep-end state
+ * (or_run_best) instead of its last state; lambda still steps on the last states.
  * Outputs: *best_cost (INT64_MAX if nothing feasible), best_x (N' bytes), best_iter/best_chain,
- * lambda_trace (K x m: lambda after each update, may be NULL), *feasible_count, and optionally
- * every sample's cost (K x C) and constraint values (K x C x m). */
+ * lambda_trace (K x m: lambda after each update, may be NULL), *feasible_count (stored feasible
+ * samples), and optionally every last sample's cost (K x C) and constraint values (K x C x m). */
 OR_API void or_solve(int32_t n, int32_t m, const int64_t *W, const int64_t *h, const int64_t *A,
-                     const int64_t *b, float alpha, float density, float penalty, int32_t K,
-                     int32_t C, int32_t T, float beta_max, double eta, uint64_t seed,
-                     uint32_t iter0, int32_t project, const float *lambda0, int64_t *best_cost,
-                     uint8_t *best_x, int32_t *best_iter, int32_t *best_chain,
-                     float *lambda_trace, int64_t *feasible_count, int64_t *cost_out,
-                     int64_t *g_out) {
+                     const int64_t *b, const int64_t *b_check, float alpha, float density,
+                     float penalty, int32_t K, int32_t C, int32_t T, float beta_max, double eta,
+                     uint64_t seed, uint32_t iter0, int32_t project, int32_t run_best,
+                     const float *lambda0, int64_t *best_cost, uint8_t *best_x,
+                     int32_t *best_iter, int32_t *best_chain, float *lambda_trace,
+                     int64_t *feasible_count, int64_t *cost_out, int64_t *g_out) {
+    if (!b_check) b_check = b;
     const int32_t nprime = or_num_spins(n, m, b);
     int64_t *Aext = (int64_t *)malloc(sizeof(int64_t) * (size_t)m * nprime);
     or_extend(n, m, A, b, nprime, Aext);
@@ -454,6 +497,9 @@ OR_API void or_solve(int32_t n, int32_t m, const int64_t *W, const int64_t *h, c
     float *lambda = (float *)malloc(sizeof(float) * (size_t)(m > 0 ? m : 1));
     int64_t *g = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
     int64_t *gsum = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+    uint8_t *trace = run_best ? (uint8_t *)malloc((size_t)C * T * nprime) : NULL;
+    int64_t *rcost = run_best ? (int64_t *)malloc(sizeof(int64_t) * (size_t)C) : NULL;
+    uint8_t *rx = run_best ? (uint8_t *)malloc((size_t)C * nprime) : NULL;
     for (int32_t k = 0; k < m; k++) lambda[k] = lambda0 ? lambda0[k] : 0.0f;
     *best_cost = INT64_MAX;
     *best_iter = -1;
@@ -462,7 +508,8 @@ OR_API void or_solve(int32_t n, int32_t m, const int64_t *W, const int64_t *h, c
     for (int32_t it = 0; it < K; it++) {
         const uint32_t kk = iter0 + (uint32_t)it;
         or_ising(n, m, nprime, W, h, Aext, b, lambda, sc[0], sc[1], sc[2], J, hI);
-        or_anneal(nprime, J, hI, beta_max, T, seed, kk, 0, C, xs, NULL);
+        or_anneal(nprime, J, hI, beta_max, T, seed, kk, 0, C, xs, trace);
+        if (run_best) or_run_best(n, m, nprime, W, h, A, b_check, C, T, trace, rcost, rx, NULL, NULL);
         for (int32_t k = 0; k < m; k++) gsum[k] = 0;
         for (int32_t c = 0; c < C; c++) {
             const uint8_t *x = xs + (size_t)c * nprime;
@@ -472,13 +519,17 @@ OR_API void or_solve(int32_t n, int32_t m, const int64_t *W, const int64_t *h, c
             if (cost_out) cost_out[(size_t)it * C + c] = cost;
             if (g_out)
                 for (int32_t k = 0; k < m; k++) g_out[((size_t)it * C + c) * m + k] = g[k];
-            if (or_feasible(n, m, A, b, x)) {
+            /* the sample stored from this chain: its last state, or its best sweep-end state */
+            const int stored = run_best ? rcost[c] != INT64_MAX : or_feasible(n, m, A, b_check, x);
+            const int64_t scost = run_best ? rcost[c] : cost;
+            const uint8_t *sx = run_best ? rx + (size_t)c * nprime : x;
+            if (stored) {
                 (*feasible_count)++;
-                if (cost < *best_cost) {
-                    *best_cost = cost;
+                if (scost < *best_cost) {
+                    *best_cost = scost;
                     *best_iter = (int32_t)kk;
                     *best_chain = c;
-                    memcpy(best_x, x, (size_t)nprime);
+                    memcpy(best_x, sx, (size_t)nprime);
                 }
             }
         }
@@ -493,6 +544,9 @@ OR_API void or_solve(int32_t n, int32_t m, const int64_t *W, const int64_t *h, c
     free(lambda);
     free(g);
     free(gsum);
+    free(trace);
+    free(rcost);
+    free(rx);
 }
 
 /* ------------------------------------------------------------------------------------------ */

@@ -56,6 +56,15 @@ MUTANTS = [
     ("feasibility on all spins", "if (x[i]) s += A[(size_t)k * n + i];\n        if (s > b[k]) return 0;",
      "if (x[i]) s += A[(size_t)k * n + i];\n        if (s >= b[k]) return 0;",
      ["test_slack_extension_reaches_equality"]),
+    ("run best keeps the last minimiser", "            if (cost < bc) {\n                bc = cost;",
+     "            if (cost <= bc) {\n                bc = cost;",
+     ["test_run_best_is_the_best_feasible_sweep_end_state"]),
+    ("run best counts every sweep",
+     "if (!or_feasible(n, m, A, b_check, x)) continue;\n            nf++;",
+     "nf++;\n            if (!or_feasible(n, m, A, b_check, x)) continue;",
+     ["test_run_best_is_the_best_feasible_sweep_end_state"]),
+    ("tightened solve checks the reduced capacities", "if (!b_check) b_check = b;",
+     "b_check = b;", ["test_capacity_tightening_checks_the_true_capacities"]),
 ]
 
 
@@ -81,7 +90,9 @@ def test_planted_mistake_is_caught(name, orig, mut, tests, tmpdir_mod):
     try:
         for t in tests:
             fn = getattr(pins, t)
-            params = {"kind": ["qkp", "mkp"]} if t == "test_energy_identity_exhaustive" else {}
+            params = {"test_energy_identity_exhaustive": {"kind": ["qkp", "mkp"]},
+                      "test_run_best_is_the_best_feasible_sweep_end_state":
+                          {"kind": ["qkp", "mkp", "qkp_tight"]}}.get(t, {})
             runs = [dict(kind=k) for k in params["kind"]] if params else [{}]
             for kw in runs:
                 try:

@@ -433,6 +433,120 @@ def test_solve_stores_best_feasible_and_resumes_bit_exactly():
         assert full.best_cost == min(c for c in cand if c is not None)
 
 
+def _np_cost(inst, X):
+    """c(x) = -x^T W x / 2 - h^T x (Sec. IV-A) of every row of X (items first), int64 numpy."""
+    Xi = X[:, :inst.n].astype(np.int64)
+    lin = Xi @ np.asarray(inst.h, np.int64)
+    if inst.W is None:
+        return -lin
+    W = np.asarray(inst.W, np.int64)
+    return -np.einsum("ci,ij,cj->c", Xi, W, Xi) // 2 - lin
+
+
+def _np_feasible(inst, X, cap):
+    """A x <= cap on the items (Sec. IV-A), every row of X, numpy."""
+    A = np.asarray(inst.A, np.int64).reshape(inst.m, inst.n)
+    return ((X[:, :inst.n].astype(np.int64) @ A.T) <= np.asarray(cap, np.int64)[None, :]).all(1)
+
+
+@pytest.mark.parametrize("kind", ["qkp", "mkp", "qkp_tight"])
+def test_run_best_is_the_best_feasible_sweep_end_state(kind):
+    """The best-in-run option stores, per chain, the least-cost state feasible under the true
+    capacities among the states at the ends of the sweeps, the earliest sweep on ties: checked
+    against numpy evaluations of the cost and the items' loads of every traced state."""
+    if kind == "mkp":
+        inst = wl.mkp(30, 3, 5)
+    else:
+        inst = wl.qkp(30, 0.5, 4)
+    if kind == "qkp_tight":
+        bt = np.maximum(1, (np.asarray(inst.b) * 4) // 5)
+        p = oracle.Problem(inst.n, inst.m, inst.W, inst.h, inst.A, bt, alpha=inst.alpha,
+                           density=inst.density, b_check=inst.b)
+    else:
+        p = _problem(inst)
+    lam = np.full(inst.m, 0.5, np.float32)
+    J, hI, _ = p.ising(lam)
+    C, T = 12, 150
+    _, tr = oracle.anneal(J, hI, 10.0, T, 21, 3, C, trace=True)
+    cost, x, sweep, nfeas = oracle.run_best(p, tr)
+    some = False
+    for c in range(C):
+        X = tr[c]
+        feas = _np_feasible(inst, X, inst.b)
+        assert nfeas[c] == int(feas.sum())
+        if not feas.any():
+            assert cost[c] == np.iinfo(np.int64).max and sweep[c] == -1 and not x[c].any()
+            continue
+        some = True
+        cs = np.where(feas, _np_cost(inst, X), np.iinfo(np.int64).max)
+        t = int(np.argmin(cs))      # numpy's argmin takes the first minimiser
+        assert sweep[c] == t and cost[c] == cs[t]
+        assert np.array_equal(x[c], X[t])
+    assert some
+    # a made-up trace with repeated states: the earliest sweep of the least-cost feasible state
+    r = np.random.default_rng(6)
+    pool = r.integers(0, 2, (6, p.nprime)).astype(np.uint8)
+    idx = r.integers(0, 6, (4, 40))
+    fake = pool[idx]
+    cost2, _, sweep2, nfeas2 = oracle.run_best(p, fake)
+    feas = _np_feasible(inst, pool, inst.b)
+    cs = np.where(feas, _np_cost(inst, pool), np.iinfo(np.int64).max)
+    for c in range(4):
+        ok = feas[idx[c]]
+        assert nfeas2[c] == int(ok.sum())
+        if ok.any():
+            best = cs[idx[c]].min()
+            assert cost2[c] == best and sweep2[c] == int(np.flatnonzero(cs[idx[c]] == best)[0])
+    if kind == "qkp_tight":
+        # states between B' and B count as feasible: some sweep-end state exceeds B' but not B
+        A = np.asarray(inst.A, np.int64).reshape(inst.m, inst.n)
+        loads = tr[:, :, :inst.n].reshape(-1, inst.n).astype(np.int64) @ A.T
+        assert ((loads > bt[None, :]) & (loads <= np.asarray(inst.b)[None, :])).any()
+
+
+def test_solve_run_best_keeps_the_multiplier_path():
+    """With the best-in-run option the multipliers still step on the last samples (the same
+    lambda trace and last-sample costs as without it), every stored sample is a sweep-end
+    state, so the best cost can only improve and the stored-feasible count can only grow."""
+    inst = wl.mkp(40, 3, 8)
+    p = _problem(inst)
+    kw = dict(K=8, C=16, T=100, beta_max=10.0, eta=20.0, seed=3, keep_samples=True)
+    last = oracle.solve(p, **kw)
+    rb = oracle.solve(p, run_best=True, **kw)
+    assert np.array_equal(last.lambda_trace, rb.lambda_trace)
+    assert np.array_equal(last.costs, rb.costs) and np.array_equal(last.g, rb.g)
+    assert rb.feasible_count >= last.feasible_count
+    assert rb.best_cost is not None
+    if last.best_cost is not None:
+        assert rb.best_cost <= last.best_cost
+    assert _np_feasible(inst, rb.best_x[None, :], inst.b)[0]
+    assert _np_cost(inst, rb.best_x[None, :])[0] == rb.best_cost
+
+
+def test_capacity_tightening_checks_the_true_capacities():
+    """B' < B (Sec. IV-B): the sampled problem is the one built from B' (its slack bits,
+    scales and penalty), feasibility uses B, and a long run on a tiny instance reaches the
+    brute-force optimum under B, never a state beyond B."""
+    W, h, A, b = _tiny_qkp(n=9, b=17, seed=8)
+    bt = np.array([12])
+    base = oracle.Problem(9, 1, W, h, A, bt, alpha=2.0, density=0.5)
+    p = oracle.Problem(9, 1, W, h, A, bt, alpha=2.0, density=0.5, b_check=b)
+    assert p.nprime == base.nprime == 9 + 4            # Q = floor(log2 12) + 1
+    assert (p.sigma_g, p.P) == (base.sigma_g, base.P)
+    r = np.random.default_rng(1)
+    X = r.integers(0, 2, (400, p.nprime)).astype(np.uint8)
+    loads = X[:, :9].astype(np.int64) @ A[0]
+    for x, ld in zip(X, loads):
+        assert p.feasible(x) == (ld <= 17) and base.feasible(x) == (ld <= 12)
+    # brute-force optimum under B (numpy enumeration of the 2^9 item states)
+    S = ((np.arange(1 << 9)[:, None] >> np.arange(9)) & 1).astype(np.int64)
+    c_all = -np.einsum("si,ij,sj->s", S, W, S) // 2 - S @ h
+    opt = c_all[(S @ A[0]) <= 17].min()
+    res = oracle.solve(p, K=30, C=16, T=200, beta_max=10.0, eta=2.0, seed=2, run_best=True)
+    assert res.best_cost == opt
+    assert int(res.best_x[:9].astype(np.int64) @ A[0]) <= 17
+
+
 def _dual_reachable(p, inst, lam_grid):
     """Costs of the feasible ground states of L(., lambda) over a grid of lambda (one
     constraint), by enumeration: L is affine in lambda, L = L0 + lambda (L1 - L0)."""
