@@ -81,6 +81,11 @@ typedef struct sais_problem_desc {
                            (QKP: nonzero p_ij, i <= j, over n(n+1)/2) or 2/(N'+1) when W is
                            NULL (Sec. IV-B)                                                   */
     float penalty;      /* > 0: use this P instead of the alpha rule                        */
+    const int64_t *b_tight; /* NULL, or m reduced capacities B'_k, 1 <= B'_k <= b_k: capacity
+                           tightening (Sec. IV-B).  The sampled problem is the one with
+                           capacities B' in full (slack bits, sigma_g, g, penalty rule); the
+                           feasibility test and the kept best samples use b.  A zero-
+                           initialised descriptor leaves it NULL.                            */
 } sais_problem_desc;
 
 /* Scalars derived from one instance on the host (no GPU involved). */
@@ -164,6 +169,9 @@ typedef struct sais_solve_params {
     int32_t chains_per_cta;  /* as in sais_sample_params                                    */
     int32_t use_graph;       /* 1: replay the iteration as a captured CUDA graph            */
     const float *lambda0;    /* host [count*m_stride] initial multipliers, or NULL for 0    */
+    int32_t run_best;        /* 1: the sample kept from each chain is its best feasible
+                                sweep-end state (sais_sample_run_best) instead of its last
+                                state; the multipliers still step on the last states        */
 } sais_solve_params;
 
 /* Results of sais_solve, all caller-allocated HOST arrays (any may be NULL to skip it). */
@@ -213,6 +221,7 @@ SAIS_API sais_status sais_instance_scalars(const sais_problem *p, int32_t index,
  *   cost     device [count*chains] int64 c(x) = -x^T W x / 2 - h^T x (written)
  *   g        device [count*chains*m_stride] int64 g_k(x) = A_ext x - b, slack included
  *   feasible device [count*chains] uint8, 1 iff A x <= b on the items (Sec. IV-A), or NULL
+ *            (b: the descriptor's capacities, also when b_tight is set)
  * Errors: SAIS_EINVAL (NULL buffers, chains < 1, sweeps < 1, beta_max < 0 or not finite, bad
  * block_k / chains_per_cta), SAIS_EUNSUPPORTED, SAIS_ECUDA (launch failure). */
 SAIS_API sais_status sais_sample(sais_problem *p, const sais_sample_params *prm,
@@ -226,6 +235,24 @@ SAIS_API sais_status sais_sample_trace(sais_problem *p, const sais_sample_params
                                        const float *lambda, uint32_t *x, int64_t *cost,
                                        int64_t *g, uint8_t *feasible, uint32_t *trace,
                                        void *stream);
+
+/* sais_sample that also keeps, per chain, the best feasible state among the states at the ends
+ * of the sweeps of its run.  The paper measures one sample per run, its last state (Sec. IV-A);
+ * this option measures every sweep end, so a feasible state passed mid-run is not lost (the
+ * oracle's run-best option).  x, cost, g and feasible are the last samples as in sais_sample
+ * (the multiplier step uses them); in addition:
+ *   run_x      device [count*chains*words] the least-cost sweep-end state that is feasible
+ *              (A x <= b on the items), the earliest sweep on ties; zeros if none (written)
+ *   run_cost   device [count*chains] int64 its cost c(x), INT64_MAX if none (written)
+ *   run_sweep  device [count*chains] int32 its sweep t, -1 if none, or NULL
+ *   run_nfeas  device [count*chains] int32 number of feasible sweep-end states, or NULL
+ * sais_track_best takes run_x and run_cost (with feasible = NULL) to keep the best of a solve.
+ * Errors: as sais_sample. */
+SAIS_API sais_status sais_sample_run_best(sais_problem *p, const sais_sample_params *prm,
+                                          const float *lambda, uint32_t *x, int64_t *cost,
+                                          int64_t *g, uint8_t *feasible, uint32_t *run_x,
+                                          int64_t *run_cost, int32_t *run_sweep,
+                                          int32_t *run_nfeas, void *stream);
 
 /* The multiplier step of Algorithm 1, lambda_k <- lambda_k + eta g_k(x), with the normalised
  * constraint sigma_g g averaged over the `chains` samples of each instance and, if
@@ -243,7 +270,9 @@ SAIS_API sais_status sais_update_lambda(sais_problem *p, const int64_t *g, int32
  * cost (lowest chain index on ties) replaces the kept best of its instance when it is strictly
  * better, so the kept sample is the first achiever in (iteration, chain) order; the number of
  * feasible samples is added to feasible_count.
- *   x, cost, feasible   device, as written by sais_sample for `chains` chains (read)
+ *   x, cost, feasible   device, as written by sais_sample for `chains` chains (read);
+ *                       feasible may be NULL: then a sample is feasible iff its cost is not
+ *                       INT64_MAX (the run_x / run_cost outputs of sais_sample_run_best)
  *   iter                outer iteration of the samples (stored with a new best)
  *   best_cost       device [count] int64 (in/out; start at INT64_MAX)
  *   best_x          device [count*words] (in/out)

@@ -60,7 +60,8 @@ struct HostInst {
     std::vector<int32_t> acol;             // nprime x m (spin-major)
     std::vector<float> D, asum;            // npad
     std::vector<float> spinc;              // npad x 4: a_0 (int bits), D, sum a, a_1 (int bits)
-    std::vector<int32_t> b;                // m
+    std::vector<int32_t> b;                // m capacities of the sampled problem (B' if tightened)
+    std::vector<int32_t> margin;           // m: b_k - B'_k capped at sum_i a_ki (0 untightened)
     std::vector<float> hF;                 // npad
     std::vector<float> feat;               // m x 8 features of the warm-start network
     const int32_t *W = nullptr;            // borrowed from the descriptor during creation
@@ -109,13 +110,20 @@ sais_status build_host(const sais_problem_desc *d, HostInst &h) {
     }
     h.need_lo = max_w > 256;
     h.lo_own = h.need_lo;
+    // Capacity tightening (Sec. IV-B): the sampled problem uses B' (slack bits, sigma_g, g,
+    // penalty rule); feasibility keeps the caller's b through a per-constraint margin.
+    const int64_t *bs = d->b_tight ? d->b_tight : d->b;
     int64_t maxabs_g = 0;
     h.Q.assign(m, 0);
+    h.margin.assign(m, 0);
     h.slack_off.assign(m + 1, 0);
     int32_t nprime = n;
     for (int32_t k = 0; k < m; ++k) {
-        const int64_t bk = d->b[k];
-        if (bk < 1) return fail(SAIS_EINVAL, "b[%d] = %lld: capacities must be >= 1", k, (long long)bk);
+        const int64_t bk = bs[k];
+        if (d->b[k] < 1) return fail(SAIS_EINVAL, "b[%d] = %lld: capacities must be >= 1", k, (long long)d->b[k]);
+        if (bk < 1 || bk > d->b[k])
+            return fail(SAIS_EINVAL, "b_tight[%d] = %lld: need 1 <= b_tight <= b = %lld", k,
+                        (long long)bk, (long long)d->b[k]);
         int64_t rowsum = 0;
         for (int32_t i = 0; i < n; ++i) {
             const int32_t a = d->A[(size_t)k * n + i];
@@ -124,6 +132,9 @@ sais_status build_host(const sais_problem_desc *d, HostInst &h) {
             maxabs_g = std::max(maxabs_g, (int64_t)a);
         }
         maxabs_g = std::max(maxabs_g, bk);
+        // items load l <= b  <=>  l - B' <= b - B'; the load never exceeds the row sum, so the
+        // margin is capped there (it then fits int32)
+        h.margin[k] = (int32_t)std::min<int64_t>(d->b[k] - bk, rowsum);
         h.Q[k] = binary_digits(bk);
         h.slack_off[k] = nprime;
         nprime += h.Q[k];
@@ -160,7 +171,7 @@ sais_status build_host(const sais_problem_desc *d, HostInst &h) {
     h.asum.assign(h.npad, 0.f);
     h.b.assign(m, 0);
     for (int32_t k = 0; k < m; ++k) {
-        h.b[k] = (int32_t)d->b[k];
+        h.b[k] = (int32_t)bs[k];
         for (int32_t i = 0; i < n; ++i) h.acol[(size_t)i * m + k] = d->A[(size_t)k * n + i];
         for (int32_t q = 0; q < h.Q[k]; ++q)
             h.acol[(size_t)(h.slack_off[k] + q) * m + k] = 1 << q;
@@ -218,7 +229,7 @@ sais_status build_host(const sais_problem_desc *d, HostInst &h) {
         }
         const double amu = as / n, avar = asq / n - amu * amu;
         float *f = &h.feat[(size_t)k * 8];
-        f[0] = (float)(as > 0.0 ? std::min(1.0, (double)d->b[k] / as) : 1.0);
+        f[0] = (float)(as > 0.0 ? std::min(1.0, (double)bs[k] / as) : 1.0);
         f[1] = (float)((double)h.sg * amu);
         f[2] = (float)((double)h.sg * std::sqrt(std::max(avar, 0.0)));
         f[3] = (float)((double)h.sf * pmu);
@@ -546,8 +557,8 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
         cur = align_up(cur + h.asum.size() * 4, 256);
         o.spinc = cur;
         cur = align_up(cur + h.spinc.size() * 4, 256);
-        o.b = cur;
-        cur = align_up(cur + (size_t)std::max(h.m, 1) * 4, 256);
+        o.b = cur;   // b, then the feasibility margins
+        cur = align_up(cur + (size_t)std::max(h.m, 1) * 8, 256);
         o.so = cur;
         cur = align_up(cur + (size_t)(h.m + 1) * 4, 256);
     }
@@ -619,7 +630,10 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
         std::memcpy(stage.data() + o.D, h.D.data(), h.D.size() * 4);
         std::memcpy(stage.data() + o.asum, h.asum.data(), h.asum.size() * 4);
         std::memcpy(stage.data() + o.spinc, h.spinc.data(), h.spinc.size() * 4);
-        if (h.m) std::memcpy(stage.data() + o.b, h.b.data(), h.b.size() * 4);
+        if (h.m) {
+            std::memcpy(stage.data() + o.b, h.b.data(), h.b.size() * 4);
+            std::memcpy(stage.data() + o.b + (size_t)h.m * 4, h.margin.data(), h.margin.size() * 4);
+        }
         std::memcpy(stage.data() + o.so, h.slack_off.data(), h.slack_off.size() * 4);
         r.hF = reinterpret_cast<const float *>(base + o.hF);
         r.acol = reinterpret_cast<const int32_t *>(base + o.acol);
@@ -627,6 +641,7 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
         r.asum = reinterpret_cast<const float *>(base + o.asum);
         r.spinc = reinterpret_cast<const float4 *>(base + o.spinc);
         r.b = reinterpret_cast<const int32_t *>(base + o.b);
+        r.fmargin = reinterpret_cast<const int32_t *>(base + o.b) + h.m;
         r.slack_off = reinterpret_cast<const int32_t *>(base + o.so);
         recs[j] = r;
         h.W = nullptr;
@@ -752,9 +767,18 @@ sais_status plain_cpb(const sais_problem *p, int want, int *cpb) {
     return SAIS_OK;
 }
 
+// Best-in-run outputs of a sampling launch (all NULL: off).
+struct RunOut {
+    uint32_t *x = nullptr;
+    int64_t *cost = nullptr;
+    int32_t *sweep = nullptr;
+    int32_t *nfeas = nullptr;
+};
+
 sais_status enqueue_sample(sais_problem *p, const sais_sample_params *prm, const float *lambda,
                            const uint32_t *iter_dev, uint32_t *x, int64_t *cost, int64_t *g,
-                           uint8_t *feasible, uint32_t *trace, cudaStream_t st) {
+                           uint8_t *feasible, uint32_t *trace, cudaStream_t st,
+                           const RunOut &run = RunOut{}) {
     SampleArgs a{};
     a.inst = p->d_inst;
     a.count = p->count;
@@ -772,6 +796,10 @@ sais_status enqueue_sample(sais_problem *p, const sais_sample_params *prm, const
     a.g = g;
     a.feasible = feasible;
     a.trace = trace;
+    a.run_x = run.x;
+    a.run_cost = run.cost;
+    a.run_sweep = run.sweep;
+    a.run_nfeas = run.nfeas;
     a.status = p->d_status;
     a.inst_chains = p->d_inst_chains;
     if (!p->inst_chains.empty())
@@ -896,6 +924,24 @@ sais_status sais_sample_trace(sais_problem *p, const sais_sample_params *prm, co
                           static_cast<cudaStream_t>(stream));
 }
 
+sais_status sais_sample_run_best(sais_problem *p, const sais_sample_params *prm,
+                                 const float *lambda, uint32_t *x, int64_t *cost, int64_t *g,
+                                 uint8_t *feasible, uint32_t *run_x, int64_t *run_cost,
+                                 int32_t *run_sweep, int32_t *run_nfeas, void *stream) {
+    sais_status s = check_sample_params(p, prm);
+    if (s != SAIS_OK) return s;
+    if (!lambda || !x || !cost || !g || !run_x || !run_cost)
+        return fail(SAIS_EINVAL, "NULL device buffer");
+    DeviceGuard dg(p->device);
+    RunOut run;
+    run.x = run_x;
+    run.cost = run_cost;
+    run.sweep = run_sweep;
+    run.nfeas = run_nfeas;
+    return enqueue_sample(p, prm, lambda, nullptr, x, cost, g, feasible, nullptr,
+                          static_cast<cudaStream_t>(stream), run);
+}
+
 sais_status sais_synchronize(sais_problem *p, void *stream) {
     if (!p) return fail(SAIS_EINVAL, "NULL problem");
     DeviceGuard dg(p->device);
@@ -939,8 +985,7 @@ sais_status sais_track_best(sais_problem *p, const uint32_t *x, const int64_t *c
                             const uint8_t *feasible, int32_t chains, uint32_t iter,
                             int64_t *best_cost, uint32_t *best_x, int32_t *best_iter,
                             int32_t *best_chain, int64_t *feasible_count, void *stream) {
-    if (!p || !x || !cost || !feasible || !best_cost || !best_x || !best_iter || !best_chain ||
-        !feasible_count)
+    if (!p || !x || !cost || !best_cost || !best_x || !best_iter || !best_chain || !feasible_count)
         return fail(SAIS_EINVAL, "NULL argument");
     if (chains < 1) return fail(SAIS_EINVAL, "chains = %d: need >= 1", chains);
     DeviceGuard dg(p->device);
@@ -993,9 +1038,11 @@ sais_status sais_solve(sais_problem *p, const sais_solve_params *prm, sais_solve
            sz_g = nch * p->m_stride * 8, sz_feas = nch, sz_bc = (size_t)count * 8,
            sz_bx = (size_t)count * p->words * 4, sz_bi = (size_t)count * 4,
            sz_fc = (size_t)count * 8, sz_tr = (size_t)K * count * p->m_stride * 4;
-    size_t offs[12], cur = 0;
-    const size_t sizes[12] = {sz_lam, sz_x, sz_cost, sz_g, sz_feas, sz_bc, sz_bx, sz_bi, sz_bi, sz_fc, sz_tr, 4};
-    for (int i = 0; i < 12; ++i) {
+    const bool rb = prm->run_best != 0;
+    size_t offs[14], cur = 0;
+    const size_t sizes[14] = {sz_lam, sz_x, sz_cost, sz_g, sz_feas, sz_bc, sz_bx, sz_bi, sz_bi,
+                              sz_fc, sz_tr, 4, rb ? sz_x : 0, rb ? sz_cost : 0};
+    for (int i = 0; i < 14; ++i) {
         offs[i] = cur;
         cur = align_up(cur + sizes[i], 256);
     }
@@ -1017,6 +1064,11 @@ sais_status sais_solve(sais_problem *p, const sais_solve_params *prm, sais_solve
     int64_t *d_fc = reinterpret_cast<int64_t *>(scr + offs[9]);
     float *d_tr = reinterpret_cast<float *>(scr + offs[10]);
     uint32_t *d_iter = reinterpret_cast<uint32_t *>(scr + offs[11]);
+    RunOut run;   // best-in-run: the kept sample of a chain is its best feasible sweep end
+    if (rb) {
+        run.x = reinterpret_cast<uint32_t *>(scr + offs[12]);
+        run.cost = reinterpret_cast<int64_t *>(scr + offs[13]);
+    }
 
     std::vector<int64_t> h_bc(count, std::numeric_limits<int64_t>::max());
     std::vector<int32_t> h_m1(count, -1);
@@ -1039,10 +1091,10 @@ sais_status sais_solve(sais_problem *p, const sais_solve_params *prm, sais_solve
     pa.track_best = 1;
     pa.do_lambda = 1;
     pa.inst_chains = p->d_inst_chains;
-    pa.x = d_x;
-    pa.cost = d_cost;
+    pa.x = rb ? run.x : d_x;
+    pa.cost = rb ? run.cost : d_cost;
     pa.g = d_g;
-    pa.feasible = d_feas;
+    pa.feasible = rb ? nullptr : d_feas;
     pa.lambda = d_lam;
     pa.lambda_trace = d_tr;
     pa.iter_dev = d_iter;
@@ -1054,7 +1106,8 @@ sais_status sais_solve(sais_problem *p, const sais_solve_params *prm, sais_solve
     pa.feasible_count = d_fc;
 
     auto one_iteration = [&]() -> sais_status {
-        sais_status r = enqueue_sample(p, &sp, d_lam, d_iter, d_x, d_cost, d_g, d_feas, nullptr, st);
+        sais_status r = enqueue_sample(p, &sp, d_lam, d_iter, d_x, d_cost, d_g, d_feas, nullptr, st,
+                                       run);
         if (r != SAIS_OK) return r;
         cudaError_t e = launch_post(pa, st);
         if (e == cudaSuccess) e = launch_advance_iter(d_iter, st);
@@ -1350,8 +1403,11 @@ sais_status problem_view(const sais_problem *p, ProblemView *out) {
 sais_status enqueue_sample_internal(sais_problem *p, const sais_sample_params *prm,
                                    const float *lambda, const uint32_t *iter_dev, uint32_t *x,
                                    int64_t *cost, int64_t *g, uint8_t *feasible,
-                                   cudaStream_t stream) {
-    return enqueue_sample(p, prm, lambda, iter_dev, x, cost, g, feasible, nullptr, stream);
+                                   uint32_t *run_x, int64_t *run_cost, cudaStream_t stream) {
+    RunOut run;
+    run.x = run_x;
+    run.cost = run_cost;
+    return enqueue_sample(p, prm, lambda, iter_dev, x, cost, g, feasible, nullptr, stream, run);
 }
 
 sais_status check_sample_params_internal(const sais_problem *p, const sais_sample_params *prm) {

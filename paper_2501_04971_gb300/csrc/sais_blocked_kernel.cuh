@@ -285,6 +285,13 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                       ? wait_bounded_warp(&bars[1], 0, abort_flag, status, dec_wait_polls)
                       : true;
         if (ok && !kStream) ok = wait_bounded_warp(&bars[0], 0, abort_flag, status, 0);
+        // Best feasible sweep-end state of the run (a.run_cost set): at a sweep end where a
+        // chain of the warp is feasible, the warp waits for the sweep's last MMA and reads the
+        // cost c(x) = -(sum_i x_i F_i + h^T x)/2 off the fields in TMEM; the block path is
+        // untouched.
+        const bool track = a.run_cost != nullptr;
+        long long rbest = LLONG_MAX;
+        int rsweep = -1, rnf = 0;
         uint32_t it = 0;
         float th[K];
         for (int t = 0; ok && t < a.sweeps; ++t) {
@@ -589,6 +596,59 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                 }
                 ++it;
             }
+            if (ok && track) {
+                bool feas = true;
+#pragma unroll
+                for (int k = 0; k < MC; ++k) {
+                    if (k < m) {
+                        const int o0 = ip->slack_off[k], o1 = ip->slack_off[k + 1];
+                        long long sv = 0;
+                        for (int s = o0; s < o1; ++s)
+                            if ((xs[(s >> 5) * kLanes + r] >> (s & 31)) & 1u) sv += 1LL << (s - o0);
+                        if ((long long)gf[k] - sv > (long long)ip->fmargin[k]) feas = false;
+                    }
+                }
+                long long cost = LLONG_MAX;
+                if (__any_sync(0xffffffffu, feas)) {
+                    // F is current once the sweep's last MMA is done (the next block waits for
+                    // the same phase; no later one can complete before this warp's next block).
+                    if (!wait_bounded_warp(&bars[29], (it - 1u) & 1u, abort_flag, status,
+                                           dec_wait_polls)) {
+                        ok = false;
+                    } else {
+                        tc::tc_fence_after();
+                        long long sumF = 0, sumh = 0;
+                        for (int c0 = 0; c0 < npad; c0 += 32) {
+                            float v[32];
+                            tc::tmem_ld32(lane_addr + (uint32_t)c0, v);
+                            const uint32_t bits = c0 < words * 32 ? xs[(c0 >> 5) * kLanes + r] : 0u;
+                            int32_t pf = 0, ph = 0;   // |F|, |h| < 2^24: 32 terms fit int32
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) {
+                                if ((bits >> i) & 1u) {
+                                    pf += __float2int_rz(v[i]);
+                                    ph += __float2int_rz(__ldg(hF + c0 + i));
+                                }
+                            }
+                            sumF += pf;
+                            sumh += ph;
+                        }
+                        cost = -(sumF + sumh) / 2;
+                    }
+                }
+                if (ok && feas) {
+                    ++rnf;
+                    if (cost < rbest) {
+                        rbest = cost;
+                        rsweep = t;
+                        if (valid) {
+                            uint32_t *rx = a.run_x + ((size_t)j * a.chains + chain) * a.words;
+                            for (int w = 0; w < a.words; ++w)
+                                rx[w] = w < words ? xs[w * kLanes + r] : 0u;
+                        }
+                    }
+                }
+            }
             if (ok && a.trace && valid) {
                 uint32_t *tr = a.trace + (((size_t)j * a.chains + chain) * a.sweeps + t) * a.words;
                 for (int w = 0; w < a.words; ++w) tr[w] = w < words ? xs[w * kLanes + r] : 0u;
@@ -636,12 +696,19 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                         long long sv = 0;
                         for (int s = o0; s < o1; ++s)
                             if ((xs[(s >> 5) * kLanes + r] >> (s & 31)) & 1u) sv += 1LL << (s - o0);
-                        if ((long long)g[k] - sv > 0) feas = false;
+                        if ((long long)g[k] - sv > (long long)ip->fmargin[k]) feas = false;
                         a.g[cidx * a.m_stride + k] = g[k];
                     }
                 }
                 for (int k = m; k < a.m_stride; ++k) a.g[cidx * a.m_stride + k] = 0;
                 if (a.feasible) a.feasible[cidx] = feas ? 1 : 0;
+                if (track) {
+                    a.run_cost[cidx] = rbest;
+                    if (a.run_sweep) a.run_sweep[cidx] = rsweep;
+                    if (a.run_nfeas) a.run_nfeas[cidx] = rnf;
+                    if (rsweep < 0)
+                        for (int w = 0; w < a.words; ++w) a.run_x[cidx * a.words + w] = 0u;
+                }
             }
         }
     }

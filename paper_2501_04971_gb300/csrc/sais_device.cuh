@@ -14,6 +14,8 @@
 
 #include <cuda_runtime.h>
 
+#include <climits>
+
 #include "sais_internal.h"
 
 namespace sais {

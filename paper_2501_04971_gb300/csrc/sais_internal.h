@@ -37,7 +37,9 @@ struct InstDev {
     const float *D;        // npad: fl(P sigma_g^2 sum_k a_ki^2) (zero past N')
     const float *asum;     // npad: sum_k a_ki, exact in FP32 (zero past N')
     const float4 *spinc;   // npad: {a_0i (int bits), D_i, sum_k a_ki, a_1i (int bits)}
-    const int32_t *b;      // m capacities
+    const int32_t *b;      // m capacities of the sampled problem (B' when tightened)
+    const int32_t *fmargin;    // m: a sample is feasible iff g_k - (slack value)_k <= fmargin[k]
+                               // (items load <= the caller's capacity; 0 unless tightened)
     const int32_t *slack_off;  // m+1: first slack spin of constraint k; [m] = N'
     // BF16 copy of W for the blocked sampler in its shared-memory image: column-chunk major,
     // element (j, s) at index ((s/8) npad + j) 8 + s%8; Wbf_lo holds W - Wbf when |W| > 256.
@@ -66,6 +68,11 @@ struct SampleArgs {
     int64_t *g;              // [count*chains*m_stride]
     uint8_t *feasible;       // [count*chains] or NULL
     uint32_t *trace;         // [count*chains*sweeps*words] or NULL
+    // Best feasible sweep-end state of each run (all NULL: off; run_cost set: on).
+    uint32_t *run_x;         // [count*chains*words]
+    int64_t *run_cost;       // [count*chains], INT64_MAX when no sweep ended feasible
+    int32_t *run_sweep;      // [count*chains] or NULL: the sweep that reached it, -1 if none
+    int32_t *run_nfeas;      // [count*chains] or NULL: feasible sweep-end states
     int32_t *status;         // device status word (SAIS_ETIMEOUT etc.), or NULL
     // Ragged launches: work[2 i], work[2 i + 1] = (instance, chain group) of CTA i, nwork
     // entries; NULL = the full grid (chain groups x instances).  inst_chains[j] = chains of
@@ -90,7 +97,7 @@ struct PostArgs {
     const uint32_t *x;
     const int64_t *cost;
     const int64_t *g;
-    const uint8_t *feasible;
+    const uint8_t *feasible;     // NULL: feasible iff cost != INT64_MAX
     float *lambda;           // in/out
     float *lambda_trace;     // [iters*count*m_stride] or NULL
     const uint32_t *iter_dev;    // current iteration (trace row = *iter_dev - iter0)
@@ -138,10 +145,11 @@ struct ProblemView {
     long long spin_chains_total;    // sum of N' x chains when per-instance chains are set, else 0
 };
 sais_status problem_view(const sais_problem *p, ProblemView *out);
+// run_x / run_cost: best-in-run outputs, or NULL (off).
 sais_status enqueue_sample_internal(sais_problem *p, const sais_sample_params *prm,
                                    const float *lambda, const uint32_t *iter_dev, uint32_t *x,
                                    int64_t *cost, int64_t *g, uint8_t *feasible,
-                                   cudaStream_t stream);
+                                   uint32_t *run_x, int64_t *run_cost, cudaStream_t stream);
 sais_status check_sample_params_internal(const sais_problem *p, const sais_sample_params *prm);
 sais_status set_error(sais_status s, const char *fmt, ...);
 // Inference launch of the warm-start network: lambda[dst[r]] = max(0, y(feat row r)).

@@ -83,7 +83,8 @@ extern "C" sais_status sais_solve_noalloc(sais_problem *p, const sais_solve_para
 
     const int count = v.count, C = prm->chains, K = prm->iters;
     const size_t nch = (size_t)count * C;
-    const size_t sizes[12] = {
+    const bool rb = prm->run_best != 0;
+    const size_t sizes[14] = {
         (size_t)count * v.m_stride * 4,        // lambda
         nch * v.words * 4,                     // x
         nch * 8,                               // cost
@@ -95,9 +96,11 @@ extern "C" sais_status sais_solve_noalloc(sais_problem *p, const sais_solve_para
         (size_t)count * 4,                     // best_chain
         (size_t)count * 8,                     // feasible_count
         (size_t)K * count * v.m_stride * 4,    // lambda trace
-        4};                                    // iteration counter
-    size_t offs[12], need = 0;
-    for (int i = 0; i < 12; ++i) {
+        4,                                     // iteration counter
+        rb ? nch * v.words * 4 : 0,            // best-in-run states
+        rb ? nch * 8 : 0};                     // best-in-run costs
+    size_t offs[14], need = 0;
+    for (int i = 0; i < 14; ++i) {
         offs[i] = need;
         need = align256(need + sizes[i]);
     }
@@ -138,6 +141,8 @@ extern "C" sais_status sais_solve_noalloc(sais_problem *p, const sais_solve_para
     int64_t *d_fc = reinterpret_cast<int64_t *>(scr + offs[9]);
     float *d_tr = reinterpret_cast<float *>(scr + offs[10]);
     uint32_t *d_iter = reinterpret_cast<uint32_t *>(scr + offs[11]);
+    uint32_t *d_rx = rb ? reinterpret_cast<uint32_t *>(scr + offs[12]) : nullptr;
+    int64_t *d_rc = rb ? reinterpret_cast<int64_t *>(scr + offs[13]) : nullptr;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 
 #define NOALLOC_CUDA(expr)                                                              \
@@ -169,10 +174,10 @@ extern "C" sais_status sais_solve_noalloc(sais_problem *p, const sais_solve_para
     pa.project = prm->project_nonneg ? 1 : 0;
     pa.track_best = 1;
     pa.do_lambda = 1;
-    pa.x = d_x;
-    pa.cost = d_cost;
+    pa.x = rb ? d_rx : d_x;   // best-in-run: the kept sample of a chain is its best sweep end
+    pa.cost = rb ? d_rc : d_cost;
     pa.g = d_g;
-    pa.feasible = d_feas;
+    pa.feasible = rb ? nullptr : d_feas;
     pa.lambda = d_lam;
     pa.lambda_trace = d_tr;
     pa.iter_dev = d_iter;
@@ -184,7 +189,8 @@ extern "C" sais_status sais_solve_noalloc(sais_problem *p, const sais_solve_para
     pa.feasible_count = d_fc;
     pa.inst_chains = v.d_inst_chains;
     for (int k = 0; k < K; ++k) {
-        st = enqueue_sample_internal(p, &sp, d_lam, d_iter, d_x, d_cost, d_g, d_feas, s);
+        st = enqueue_sample_internal(p, &sp, d_lam, d_iter, d_x, d_cost, d_g, d_feas, d_rx, d_rc,
+                                     s);
         if (st != SAIS_OK) return st;
         NOALLOC_CUDA(launch_post(pa, s));
         NOALLOC_CUDA(launch_advance_iter(d_iter, s));

@@ -44,10 +44,13 @@ constexpr uint32_t kASlots = 4;                       // Delta ring: a decider r
 // 2..5 Delta slot free (2 arrivals: both CTAs' MMAs), 6..9 Delta slot filled by the peer
 // (this CTA arms it with the expected 4096 bytes; the peer's asynchronous stores complete
 // them), 10..13 drain, 14..21 noise full (2 q + slot),
-// 22..29 noise consumed, 30..32 tile full, 33..35 tile free.
-constexpr int kBars = 36;
+// 22..29 noise consumed, 30..32 tile full, 33..35 tile free, 36..37 (CTA 0) CTA 1's partial
+// cost of a sweep end arrived (4 arrivals: CTA 1's decision warps), 38..39 (CTA 1) that slot
+// read by CTA 0 (4 arrivals).  The last two pairs serve the best-in-run option only.
+constexpr int kBars = 40;
 constexpr int kBarMma = 1, kBarFree = 2, kBarFull = 6, kBarDrain = 10, kBarNoise = 14,
-              kBarNoiseFree = 22, kBarTile = 30, kBarTileFree = 33;
+              kBarNoiseFree = 22, kBarTile = 30, kBarTileFree = 33, kBarCost = 36,
+              kBarCostFree = 38;
 
 __device__ __forceinline__ bool p_expired(long long n, long long polls, unsigned long long t0) {
     return polls > 0 ? n >= polls : (long long)(clock64() - t0) > kPWaitCycles;
@@ -131,7 +134,10 @@ __global__ void __launch_bounds__(kPThreads, 1)
     uint32_t *xs = reinterpret_cast<uint32_t *>(aslot + kASlots * kASlotBytes);
     float *thbuf = reinterpret_cast<float *>(xs + words * kPLanes);   // [2][K][128]
     long long *part = reinterpret_cast<long long *>(thbuf + 2 * kPK * kPLanes);   // [2][128]
-    int32_t *gout = reinterpret_cast<int32_t *>(part + 2 * kPLanes);            // [128][8]
+    long long *cpart = part + 2 * kPLanes;   // [2][128] CTA 1's partial costs at sweep ends
+    long long *rbest_s = cpart + 2 * kPLanes;                                     // [128]
+    int32_t *rinfo_s = reinterpret_cast<int32_t *>(rbest_s + kPLanes);           // [128][2]
+    int32_t *gout = rinfo_s + 2 * kPLanes;                                        // [128][8]
     uint64_t *bars = reinterpret_cast<uint64_t *>(gout + kPLanes * kMaxBlockedConstraints);
     uint32_t *arrivals = reinterpret_cast<uint32_t *>(bars + kBars);
     uint32_t *tmem_slot = arrivals + kASlots;   // arrivals: [kASlots] decision warps done
@@ -140,7 +146,9 @@ __global__ void __launch_bounds__(kPThreads, 1)
 
     if (threadIdx.x == kPLanes) {
         for (int i = 0; i < kBars; ++i) {
-            const uint32_t cnt = (i >= kBarFree && i < kBarFree + (int)kASlots) ? 2u : 1u;
+            const uint32_t cnt = (i >= kBarFree && i < kBarFree + (int)kASlots) ? 2u
+                                 : i >= kBarCost                                ? 4u
+                                                                                : 1u;
             tc::mbar_init(&bars[i], cnt);
         }
         for (uint32_t i = 0; i < kASlots; ++i) arrivals[i] = 0u;
@@ -291,6 +299,14 @@ __global__ void __launch_bounds__(kPThreads, 1)
         bool ok = polls > 0 ? p_wait_warp<false>(&bars[0], 0, abort_flag, status, polls) : true;
         uint32_t it = 0, ib = 0, cons_par = 0u;   // bit s: parity of Delta slot s's next fill
         float th[kPK];
+        // Best feasible sweep-end state of the run (a.run_cost set).  Both CTAs hold the same
+        // chain states, so both see which chains are feasible at a sweep end; where a chain of
+        // the warp is, each CTA reads sum_i x_i F_i over its own item columns off TMEM (after
+        // its last MMA of the sweep), CTA 1 sends its part to CTA 0, and CTA 0 forms the cost
+        // -(sum_i x_i F_i + h^T x)/2 and keeps the best.  The block path is untouched.
+        const bool track = a.run_cost != nullptr;
+        long long rbest = LLONG_MAX;
+        int rsweep = -1, rnf = 0;
         for (int t = 0; ok && t < a.sweeps; ++t) {
             const float beta = beta_of_sweep(a.beta_max, t, a.sweeps);
             const float hb = 0.5f * beta;
@@ -639,6 +655,90 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 }
                 ++it;
             }
+            if (ok && track) {
+                bool feas = true;
+#pragma unroll
+                for (int k = 0; k < MC; ++k) {
+                    if (k < m) {
+                        const int o0 = ip->slack_off[k], o1 = ip->slack_off[k + 1];
+                        long long sv = 0;
+                        for (int s = o0; s < o1; ++s)
+                            if ((xs[(s >> 5) * kPLanes + r] >> (s & 31)) & 1u) sv += 1LL << (s - o0);
+                        if ((long long)gf[k] - sv > (long long)ip->fmargin[k]) feas = false;
+                    }
+                }
+                // This CTA's sum_i x_i F_i over its item columns, where the warp needs it.
+                long long part_own = 0;
+                if (__any_sync(0xffffffffu, feas)) {
+                    // The sweep's last MMA of this CTA (item block ib - 1) done: F is current.
+                    if (!p_wait_warp<false>(&bars[kBarMma], (ib - 1u) & 1u, abort_flag, status, polls)) {
+                        ok = false;
+                    } else {
+                        tc::tc_fence_after();
+                        for (int c0 = 0; c0 < ncol; c0 += 16) {
+                            float v[16];
+                            tc::tmem_ld16(lane_addr + (uint32_t)c0, v);
+                            const int sc = col0 + c0;   // a multiple of 16
+                            const uint32_t bits =
+                                sc < words * 32 ? (xs[(sc >> 5) * kPLanes + r] >> (sc & 31)) & 0xFFFFu : 0u;
+                            int32_t pf = 0;   // |F| < 2^24: 16 terms fit int32
+#pragma unroll
+                            for (int i = 0; i < 16; ++i)
+                                if ((bits >> i) & 1u) pf += __float2int_rz(v[i]);
+                            part_own += pf;
+                        }
+                    }
+                }
+                // Sweep end: CTA 1's part into CTA 0's slot t % 2 (plain stores, then a release
+                // arrival), once CTA 0 has read what the slot held two sweeps ago.  Sent every
+                // sweep (0 where not needed) so that both CTAs step the slots' phases together.
+                const uint32_t cs = (uint32_t)t & 1u, cu = (uint32_t)t >> 1;
+                if (!ok) {
+                } else if (rank == 1) {
+                    if (t >= 2 && !p_wait_warp<true>(&bars[kBarCostFree + cs], (cu - 1u) & 1u,
+                                                     abort_flag, status, polls))
+                        ok = false;
+                    if (ok) {
+                        tc::st_cluster_s64(tc::mapa(tc::smem_u32(cpart + cs * kPLanes + r), 0u),
+                                           part_own);
+                        __syncwarp();
+                        if (lane == 0) {
+                            tc::fence_acq_rel_cluster();
+                            tc::mbar_arrive_remote(tc::mapa(tc::smem_u32(&bars[kBarCost + cs]), 0u));
+                        }
+                    }
+                } else if (!p_wait_warp<true>(&bars[kBarCost + cs], cu & 1u, abort_flag, status,
+                                              polls)) {
+                    ok = false;
+                } else {
+                    const long long tot = part_own + cpart[cs * kPLanes + r];
+                    __syncwarp();
+                    if (lane == 0)
+                        tc::mbar_arrive_remote(tc::mapa(tc::smem_u32(&bars[kBarCostFree + cs]), 1u));
+                    if (feas) {
+                        long long sumh = 0;
+                        for (int w = 0; w < words; ++w) {
+                            uint32_t bits = xs[w * kPLanes + r];
+                            while (bits) {
+                                const int i = w * 32 + __ffs(bits) - 1;
+                                bits &= bits - 1u;
+                                sumh += (long long)__float2int_rz(__ldg(ip->hF + i));
+                            }
+                        }
+                        const long long cost = -(tot + sumh) / 2;
+                        ++rnf;
+                        if (cost < rbest) {
+                            rbest = cost;
+                            rsweep = t;
+                            if (valid) {
+                                uint32_t *rx = a.run_x + ((size_t)j * a.chains + chain) * a.words;
+                                for (int w = 0; w < a.words; ++w)
+                                    rx[w] = w < words ? xs[w * kPLanes + r] : 0u;
+                            }
+                        }
+                    }
+                }
+            }
             if (ok && a.trace && valid && rank == 0) {
                 uint32_t *tr = a.trace + (((size_t)j * a.chains + chain) * a.sweeps + t) * a.words;
                 for (int w = 0; w < a.words; ++w) tr[w] = w < words ? xs[w * kPLanes + r] : 0u;
@@ -676,6 +776,11 @@ __global__ void __launch_bounds__(kPThreads, 1)
             part[r] = sumF;
 #pragma unroll
         for (int k = 0; k < MC; ++k) gout[r * kMaxBlockedConstraints + k] = (int32_t)gf[k];
+        if (rank == 0 && track) {
+            rbest_s[r] = rbest;
+            rinfo_s[2 * r] = rsweep;
+            rinfo_s[2 * r + 1] = rnf;
+        }
         if (lane == 0) warp_ok[warp] = ok ? 1 : 0;
         __syncwarp();
     }
@@ -713,11 +818,18 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 for (int s = o0; s < o1; ++s)
                     if ((xs[(s >> 5) * kPLanes + r] >> (s & 31)) & 1u) sv += 1LL << (s - o0);
                 const int32_t gk = gout[r * kMaxBlockedConstraints + k];
-                if ((long long)gk - sv > 0) feas = false;
+                if ((long long)gk - sv > (long long)ip->fmargin[k]) feas = false;
                 a.g[cidx * a.m_stride + k] = gk;
             }
             for (int k = m; k < a.m_stride; ++k) a.g[cidx * a.m_stride + k] = 0;
             if (a.feasible) a.feasible[cidx] = feas ? 1 : 0;
+            if (a.run_cost) {
+                a.run_cost[cidx] = rbest_s[r];
+                if (a.run_sweep) a.run_sweep[cidx] = rinfo_s[2 * r];
+                if (a.run_nfeas) a.run_nfeas[cidx] = rinfo_s[2 * r + 1];
+                if (rinfo_s[2 * r] < 0)
+                    for (int w = 0; w < a.words; ++w) a.run_x[cidx * a.words + w] = 0u;
+            }
         }
     }
 }
@@ -738,7 +850,7 @@ size_t pair_smem_bytes(int max_n, int max_words, bool hilo) {
     const size_t half = (size_t)pair_half(pair_npad(max_n));
     const size_t slot = 2 * half * 16 * (hilo ? 2 : 1);
     return kPRing * slot + kASlots * kASlotBytes + (size_t)max_words * kPLanes * 4 +
-           (size_t)2 * kPK * kPLanes * 4 + (size_t)2 * kPLanes * 8 +
+           (size_t)2 * kPK * kPLanes * 4 + (size_t)6 * kPLanes * 8 +
            (size_t)kPLanes * kMaxBlockedConstraints * 4 + kBars * 8 + 64;
 }
 

@@ -74,6 +74,11 @@ __global__ void __launch_bounds__(128) plain_sampler_kernel(SampleArgs a) {
         for (int i = 0; i < npad; ++i) Fs[i * cpb + tid] = hF[i];
     for (int w = 0; w < words; ++w) xs[w * cpb + tid] = 0u;
     const float errk = field_err_factor(m);
+    // Best feasible sweep-end state of the run (when a.run_cost is set): the cost of the current
+    // state follows every flip, c(x') - c(x) = -d F_i (F_i = h_i + sum_j W_ij x_j, W_ii = 0).
+    const bool track = a.run_cost != nullptr;
+    long long ccur = 0, rbest = LLONG_MAX;
+    int rsweep = -1, rnf = 0;
 
     for (int t = 0; t < a.sweeps; ++t) {
         const float beta = beta_of_sweep(a.beta_max, t, a.sweeps);
@@ -114,6 +119,7 @@ __global__ void __launch_bounds__(128) plain_sampler_kernel(SampleArgs a) {
                 const int d = xn - xi;
                 if (d != 0) {
                     xw ^= 1u << (i & 31);
+                    ccur -= (long long)(d * __float2int_rz(Fi));   // |F| < 2^24: exact
                     Mmax = 0.f;
 #pragma unroll
                     for (int k = 0; k < MC; ++k) {
@@ -143,6 +149,30 @@ __global__ void __launch_bounds__(128) plain_sampler_kernel(SampleArgs a) {
                     }
                 }
                 if ((i & 31) == 31 || i == nprime - 1) xs[(i >> 5) * cpb + tid] = xw;
+            }
+        }
+        if (track) {
+            bool feas = true;
+#pragma unroll
+            for (int k = 0; k < MC; ++k) {
+                if (k < m) {
+                    const int o0 = ip->slack_off[k], o1 = ip->slack_off[k + 1];
+                    long long sv = 0;
+                    for (int s = o0; s < o1; ++s)
+                        if ((xs[(s >> 5) * cpb + tid] >> (s & 31)) & 1u) sv += 1LL << (s - o0);
+                    if ((long long)g[k] - sv > (long long)ip->fmargin[k]) feas = false;
+                }
+            }
+            if (feas) {
+                ++rnf;
+                if (ccur < rbest) {
+                    rbest = ccur;
+                    rsweep = t;
+                    if (valid) {
+                        uint32_t *rx = a.run_x + ((size_t)j * a.chains + chain) * a.words;
+                        for (int w = 0; w < a.words; ++w) rx[w] = w < words ? xs[w * cpb + tid] : 0u;
+                    }
+                }
             }
         }
         if (a.trace && valid) {
@@ -176,12 +206,19 @@ __global__ void __launch_bounds__(128) plain_sampler_kernel(SampleArgs a) {
             long long sv = 0;
             for (int s = o0; s < o1; ++s)
                 if ((xs[(s >> 5) * cpb + tid] >> (s & 31)) & 1u) sv += 1LL << (s - o0);
-            if ((long long)g[k] - sv > 0) feas = false;
+            if ((long long)g[k] - sv > (long long)ip->fmargin[k]) feas = false;
             a.g[cidx * a.m_stride + k] = g[k];
         }
     }
     for (int k = m; k < a.m_stride; ++k) a.g[cidx * a.m_stride + k] = 0;
     if (a.feasible) a.feasible[cidx] = feas ? 1 : 0;
+    if (track) {
+        a.run_cost[cidx] = rbest;
+        if (a.run_sweep) a.run_sweep[cidx] = rsweep;
+        if (a.run_nfeas) a.run_nfeas[cidx] = rnf;
+        if (rsweep < 0)
+            for (int w = 0; w < a.words; ++w) a.run_x[cidx * a.words + w] = 0u;
+    }
 }
 
 template <int MC>

@@ -66,7 +66,8 @@ __global__ void __launch_bounds__(kPostThreads) post_kernel(PostArgs a) {
         long long bc = LLONG_MAX;
         int bch = INT_MAX, nf = 0;
         for (int c = tid; c < C; c += kPostThreads) {
-            if (a.feasible[base + c]) {
+            // feasible == NULL: a sample is feasible iff its cost is set (best-in-run outputs)
+            if (a.feasible ? a.feasible[base + c] != 0 : a.cost[base + c] != LLONG_MAX) {
                 ++nf;
                 const long long v = a.cost[base + c];
                 if (v < bc || (v == bc && c < bch)) {

@@ -28,7 +28,7 @@ _VARIANTS = {"plain": SAIS_PLAIN, "blocked": SAIS_BLOCKED, "auto": SAIS_AUTO}
 
 class sais_problem_desc(ctypes.Structure):
     _fields_ = [("n", _i32), ("m", _i32), ("W", _P), ("h", _P), ("A", _P), ("b", _P),
-                ("alpha", _f32), ("density", _f32), ("penalty", _f32)]
+                ("alpha", _f32), ("density", _f32), ("penalty", _f32), ("b_tight", _P)]
 
 
 class sais_problem_scalars(ctypes.Structure):
@@ -52,7 +52,7 @@ class sais_solve_params(ctypes.Structure):
     _fields_ = [("iters", _i32), ("chains", _i32), ("sweeps", _i32), ("beta_max", _f32),
                 ("eta", _f64), ("seed", _u64), ("iter0", _u32), ("project_nonneg", _i32),
                 ("variant", _i32), ("block_k", _i32), ("chains_per_cta", _i32),
-                ("use_graph", _i32), ("lambda0", _P)]
+                ("use_graph", _i32), ("lambda0", _P), ("run_best", _i32)]
 
 
 class sais_tuning(ctypes.Structure):
@@ -77,6 +77,8 @@ _SIGS = {
     "sais_instance_scalars": [_P, _i32, ctypes.POINTER(sais_problem_scalars)],
     "sais_sample": [_P, ctypes.POINTER(sais_sample_params), _P, _P, _P, _P, _P, _P],
     "sais_sample_trace": [_P, ctypes.POINTER(sais_sample_params), _P, _P, _P, _P, _P, _P, _P],
+    "sais_sample_run_best": [_P, ctypes.POINTER(sais_sample_params), _P, _P, _P, _P, _P, _P, _P,
+                             _P, _P, _P],
     "sais_update_lambda": [_P, _P, _i32, _f64, _i32, _P, _P],
     "sais_track_best": [_P, _P, _P, _P, _i32, _u32, _P, _P, _P, _P, _P, _P],
     "sais_solve": [_P, ctypes.POINTER(sais_solve_params), ctypes.POINTER(sais_solve_result), _P],
@@ -187,6 +189,13 @@ def sais_sample_trace(h, prm, lam_ptr, x_ptr, cost_ptr, g_ptr, feas_ptr, trace_p
                                    feas_ptr, trace_ptr, stream_ptr), "sais_sample_trace")
 
 
+def sais_sample_run_best(h, prm, lam_ptr, x_ptr, cost_ptr, g_ptr, feas_ptr, run_x_ptr,
+                         run_cost_ptr, run_sweep_ptr, run_nfeas_ptr, stream_ptr):
+    _check(lib().sais_sample_run_best(h, ctypes.byref(prm), lam_ptr, x_ptr, cost_ptr, g_ptr,
+                                      feas_ptr, run_x_ptr, run_cost_ptr, run_sweep_ptr,
+                                      run_nfeas_ptr, stream_ptr), "sais_sample_run_best")
+
+
 def sais_update_lambda(h, g_ptr, chains: int, eta: float, project: int, lam_ptr, stream_ptr):
     _check(lib().sais_update_lambda(h, g_ptr, chains, eta, project, lam_ptr, stream_ptr),
            "sais_update_lambda")
@@ -245,7 +254,8 @@ def sais_last_error() -> str:
 # --- convenience wrapper ------------------------------------------------------------------
 
 def _desc(inst, keep: list) -> sais_problem_desc:
-    """sais_problem_desc for an object with n, m, W, h, A, b, alpha, density (+ penalty)."""
+    """sais_problem_desc for an object with n, m, W, h, A, b, alpha, density (+ penalty, and
+    b_tight: reduced capacities B' for capacity tightening)."""
     def arr(a, dt):
         if a is None:
             return None
@@ -261,6 +271,8 @@ def _desc(inst, keep: list) -> sais_problem_desc:
     d.alpha = float(inst.alpha)
     d.density = float(inst.density)
     d.penalty = float(getattr(inst, "penalty", 0.0) or 0.0)
+    bt = getattr(inst, "b_tight", None)
+    d.b_tight = arr(bt if (bt is not None and inst.m) else None, np.int64)
     return d
 
 
@@ -363,6 +375,40 @@ class Problem:
             out["trace"] = torch.empty(n * trace_sweeps * self.words, dtype=torch.int32, device=dev)
         return out
 
+    def alloc_run_best(self, chains: int):
+        """Device outputs of sais_sample_run_best's best-in-run part."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        n = self.count * chains
+        return {"x": torch.empty(n * self.words, dtype=torch.int32, device=dev),
+                "cost": torch.empty(n, dtype=torch.int64, device=dev),
+                "sweep": torch.empty(n, dtype=torch.int32, device=dev),
+                "nfeas": torch.empty(n, dtype=torch.int32, device=dev)}
+
+    def sample_run_best(self, lam, chains: int, sweeps: int, beta_max: float, seed: int,
+                        it: int = 0, variant="plain", block_k: int = 0, chains_per_cta: int = 0,
+                        out=None, run=None, stream=None):
+        """sais_sample_run_best: the last samples as sample() returns them, plus "run": each
+        chain's best feasible sweep-end state x [count, chains, words], its cost (INT64_MAX if
+        none), sweep (-1 if none) and the number of feasible sweep ends."""
+        prm = self._params(chains, sweeps, beta_max, seed, it, variant, block_k, chains_per_cta)
+        o = out or self.alloc_outputs(chains)
+        r = run or self.alloc_run_best(chains)
+        sais_sample_run_best(self.handle, prm, _P(lam.data_ptr()), _P(o["x"].data_ptr()),
+                             _P(o["cost"].data_ptr()), _P(o["g"].data_ptr()),
+                             _P(o["feasible"].data_ptr()), _P(r["x"].data_ptr()),
+                             _P(r["cost"].data_ptr()), _P(r["sweep"].data_ptr()),
+                             _P(r["nfeas"].data_ptr()), _stream_ptr(stream))
+        C = chains
+        return {"x": o["x"].view(self.count, C, self.words),
+                "cost": o["cost"].view(self.count, C),
+                "g": o["g"].view(self.count, C, self.m_stride),
+                "feasible": o["feasible"].view(self.count, C),
+                "run": {"x": r["x"].view(self.count, C, self.words),
+                        "cost": r["cost"].view(self.count, C),
+                        "sweep": r["sweep"].view(self.count, C),
+                        "nfeas": r["nfeas"].view(self.count, C)}}
+
     def sample(self, lam, chains: int, sweeps: int, beta_max: float, seed: int, it: int = 0,
                variant="plain", block_k: int = 0, chains_per_cta: int = 0, trace: bool = False,
                out=None, stream=None, debug_wait_polls: int = 0):
@@ -404,9 +450,11 @@ class Problem:
                 "feasible_count": torch.zeros(self.count, dtype=torch.int64, device=dev)}
 
     def track_best(self, out: dict, chains: int, it: int, best: dict, stream=None):
-        """The "store feasible x_k" step (sais_track_best) for samples `out` of sample()."""
+        """The "store feasible x_k" step (sais_track_best) for samples `out` of sample(), or for
+        the "run" part of sample_run_best() (no "feasible": a set cost marks a feasible one)."""
+        feas = out.get("feasible")
         sais_track_best(self.handle, _P(out["x"].data_ptr()), _P(out["cost"].data_ptr()),
-                        _P(out["feasible"].data_ptr()), chains, it,
+                        _P(feas.data_ptr()) if feas is not None else None, chains, it,
                         _P(best["best_cost"].data_ptr()), _P(best["best_x"].data_ptr()),
                         _P(best["best_iter"].data_ptr()), _P(best["best_chain"].data_ptr()),
                         _P(best["feasible_count"].data_ptr()), _stream_ptr(stream))
@@ -414,13 +462,15 @@ class Problem:
     def solve(self, iters: int, chains: int, sweeps: int, beta_max: float, eta: float,
               seed: int, iter0: int = 0, project: bool = True, lambda0=None, variant="plain",
               block_k: int = 0, chains_per_cta: int = 0, use_graph: bool = False,
-              stream=None) -> dict:
-        """Algorithm 1 on every instance (sais_solve); returns host numpy arrays."""
+              run_best: bool = False, stream=None) -> dict:
+        """Algorithm 1 on every instance (sais_solve); returns host numpy arrays.  run_best:
+        keep each chain's best feasible sweep-end state instead of its last state."""
         prm = sais_solve_params()
         prm.iters, prm.chains, prm.sweeps, prm.beta_max = iters, chains, sweeps, beta_max
         prm.eta, prm.seed, prm.iter0, prm.project_nonneg = eta, seed, iter0, int(project)
         prm.variant = _VARIANTS[variant] if isinstance(variant, str) else int(variant)
         prm.block_k, prm.chains_per_cta, prm.use_graph = block_k, chains_per_cta, int(use_graph)
+        prm.run_best = int(run_best)
         l0 = None
         if lambda0 is not None:
             l0 = np.ascontiguousarray(np.asarray(lambda0, dtype=np.float32).reshape(-1))

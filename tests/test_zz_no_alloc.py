@@ -28,12 +28,14 @@ def _built():
     torch.cuda.set_device(0)
 
 
-def _noalloc(prob, iters, chains, sweeps, beta_max, eta, seed, variant="plain", lambda0=None):
+def _noalloc(prob, iters, chains, sweeps, beta_max, eta, seed, variant="plain", lambda0=None,
+             run_best=False):
     """Call sais_solve_noalloc through the C-ABI with host result arrays."""
     prm = sais.sais_solve_params()
     prm.iters, prm.chains, prm.sweeps, prm.beta_max = iters, chains, sweeps, beta_max
     prm.eta, prm.seed, prm.iter0, prm.project_nonneg = eta, seed, 0, 1
     prm.variant = sais._VARIANTS[variant]
+    prm.run_best = int(run_best)
     keep = None
     if lambda0 is not None:
         keep = np.ascontiguousarray(lambda0, np.float32).reshape(-1)
@@ -66,6 +68,21 @@ def test_noalloc_matches_solve_on_two_calls(variant):
         assert st == sais.SAIS_OK, sais.sais_last_error()
         for k in KEYS:
             assert np.array_equal(got[k], want[k]), (call, k)
+    prob.close()
+
+
+def test_noalloc_run_best_with_tightening_matches_solve():
+    """The best-in-run option and tightened capacities through the allocation-free form."""
+    insts = [wl.qkp(100, 0.5, 8), wl.qkp(80, 0.75, 9)]
+    for inst in insts:
+        inst.b_tight = np.maximum(1, (np.asarray(inst.b) * 4) // 5).astype(np.int64)
+    prob = sais.Problem(insts)
+    for variant in ("plain", "blocked"):
+        want = prob.solve(6, 128, 120, 10.0, 20.0, 21, variant=variant, run_best=True)
+        st, got = _noalloc(prob, 6, 128, 120, 10.0, 20.0, 21, variant=variant, run_best=True)
+        assert st == sais.SAIS_OK, sais.sais_last_error()
+        for k in KEYS:
+            assert np.array_equal(got[k], want[k]), (variant, k)
     prob.close()
 
 
