@@ -72,10 +72,12 @@ _SIGS = {
     "or_replay_sweep": (_i32, [_i32, _P, _P, _f32, _u64, _u32, _u32, _u32, _P, _P, _P, _P,
                                _i32]),
     "or_lambda_update": (None, [_i32, _P, _i64, _f64, _i32, _f32, _P]),
+    "or_lambda_update_rule": (None, [_i32, _P, _i64, _f64, _i32, _f32, _u32, _f64, _i32, _f64,
+                                     _P, _P]),
     "or_run_best": (None, [_i32, _i32, _i32, _P, _P, _P, _P, _i32, _i32, _P, _P, _P, _P, _P]),
     "or_solve": (None, [_i32, _i32, _P, _P, _P, _P, _P, _f32, _f32, _f32, _i32, _i32, _i32,
-                        _f32, _f64, _u64, _u32, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P,
-                        _P]),
+                        _f32, _f64, _u64, _u32, _i32, _i32, _f64, _i32, _f64, _P, _P, _P, _P,
+                        _P, _P, _P, _P, _P]),
     "or_enumerate_lagrangian": (None, [_i32, _i32, _i32, _P, _P, _P, _P, _P, _f32, _f32, _f32,
                                        _P]),
     "or_brute_force_opt": (_i64, [_i32, _i32, _P, _P, _P, _P, _P]),
@@ -294,6 +296,19 @@ def lambda_update(gsum, C: int, eta: float, project: bool, sigma_g, lam) -> np.n
     return out
 
 
+def lambda_update_rule(gsum, C: int, eta: float, project: bool, sigma_g, lam, it: int,
+                       decay: float = 0.0, eta_sqrt: bool = False, mu: float = 0.0, avg=None):
+    """The multiplier step with a step-size rule (or_lambda_update_rule): returns the new
+    lambda; `avg` (FP64 array, the averaged subgradient) is updated in place when mu != 0."""
+    g = _c(gsum, np.int64)
+    out = np.array(lam, dtype=np.float32, copy=True)
+    if mu != 0.0:
+        assert avg is not None and avg.dtype == np.float64 and avg.flags.c_contiguous
+    load().or_lambda_update_rule(len(out), _ptr(g), C, eta, int(project), np.float32(sigma_g),
+                                 it, decay, int(eta_sqrt), mu, _ptr(avg), _ptr(out))
+    return out
+
+
 @dataclass
 class SolveResult:
     best_cost: Optional[int]
@@ -308,10 +323,12 @@ class SolveResult:
 
 def solve(p: Problem, K: int, C: int, T: int, beta_max: float, eta: float, seed: int,
           iter0: int = 0, project: bool = True, lambda0=None, keep_samples: bool = False,
-          run_best: bool = False):
+          run_best: bool = False, eta_decay: float = 0.0, eta_sqrt: bool = False,
+          momentum: float = 0.0):
     """Algorithm 1 (Sec. III-A) with the p-bit machine of Sec. III-B as the minimiser.
     Feasibility is checked against p.b_check; run_best stores each chain's best feasible
-    sweep-end state instead of its last state."""
+    sweep-end state instead of its last state; eta_decay, eta_sqrt and momentum select the
+    step-size rule of lambda_update_rule (the average starts at 0 in every call)."""
     lib = load()
     bc = np.zeros(1, dtype=np.int64)
     bx = np.zeros(p.nprime, dtype=np.uint8)
@@ -324,7 +341,7 @@ def solve(p: Problem, K: int, C: int, T: int, beta_max: float, eta: float, seed:
     l0 = _c(lambda0, np.float32)
     lib.or_solve(p.n, p.m, _ptr(p.W), _ptr(p.h), _ptr(p.A), _ptr(p.b), _ptr(p.b_check),
                  p.alpha, p.density, p.penalty, K, C, T, beta_max, eta, seed, iter0,
-                 int(project), int(run_best), _ptr(l0),
+                 int(project), int(run_best), eta_decay, int(eta_sqrt), momentum, _ptr(l0),
                  _ptr(bc), _ptr(bx), _ptr(bi), _ptr(bch), _ptr(lt), _ptr(fc), _ptr(costs),
                  _ptr(gs))
     found = int(bc[0]) != np.iinfo(np.int64).max

@@ -414,19 +414,48 @@ OR_API int32_t or_replay_sweep(int32_t nprime, const double *J, const double *hI
 /* Algorithm 1: multiplier update, the outer loop, and the final selection                    */
 /* ------------------------------------------------------------------------------------------ */
 
-/* lambda_{k+1} = lambda_k + eta g(x_k) (Algorithm 1) with g in normalised units (sigma_g g),
- * gsum[k] = sum over the C chains of g_k (int64, exact), mean over chains, optional projection
- * on lambda >= 0.  FP64 evaluation order: mean = S/C; step = eta*(sigma_g*mean); l = lambda+step;
- * the result is rounded to FP32. */
-OR_API void or_lambda_update(int32_t m, const int64_t *gsum, int64_t C, double eta,
-                             int32_t project, float sg, float *lambda) {
+/* The multiplier step with a step-size rule.  Sec. III-A ascends the dual along the
+ * subgradient g(x) and notes that the surrogate-gradient method converges with approximate
+ * minimisers too; that method lets the step size shrink and the direction be a combination of
+ * recent subgradients.  The two variants here (not in the paper; definitions, not readings):
+ *   eta_it = eta / (1 + decay it)        (eta_sqrt = 0)
+ *   eta_it = eta / sqrt(1 + decay it)    (eta_sqrt = 1), it = the outer-iteration index;
+ *   d = mu avg + (1 - mu) mean, stored back into avg (an exponentially weighted average of
+ *   the batch-mean subgradients, avg = 0 before the first step); mu = 0 gives d = mean.
+ * lambda_k <- lambda_k + eta_it sigma_g d_k, projected on lambda >= 0 if asked, rounded to FP32.
+ * FP64, evaluated in this order without fused operations: mean = S/C; d; den = 1 + decay*it
+ * (its square root if eta_sqrt); eta_it = eta/den (eta itself when decay = 0);
+ * step = eta_it*(sigma_g*d); l = lambda + step.  avg may be NULL when mu = 0. */
+OR_API void or_lambda_update_rule(int32_t m, const int64_t *gsum, int64_t C, double eta,
+                                  int32_t project, float sg, uint32_t it, double decay,
+                                  int32_t eta_sqrt, double mu, double *avg, float *lambda) {
+    double eta_it = eta;
+    if (decay != 0.0) {
+        double den = 1.0 + decay * (double)it;
+        if (eta_sqrt) den = sqrt(den);
+        eta_it = eta / den;
+    }
     for (int32_t k = 0; k < m; k++) {
         const double mean = (double)gsum[k] / (double)C;
-        const double step = eta * ((double)sg * mean);
+        double d = mean;
+        if (mu != 0.0) {
+            d = mu * avg[k] + (1.0 - mu) * mean;
+            avg[k] = d;
+        }
+        const double step = eta_it * ((double)sg * d);
         double l = (double)lambda[k] + step;
         if (project && l < 0.0) l = 0.0;
         lambda[k] = (float)l;
     }
+}
+
+/* lambda_{k+1} = lambda_k + eta g(x_k) (Algorithm 1) with g in normalised units (sigma_g g),
+ * gsum[k] = sum over the C chains of g_k (int64, exact), mean over chains, optional projection
+ * on lambda >= 0.  FP64 evaluation order: mean = S/C; step = eta*(sigma_g*mean); l = lambda+step;
+ * the result is rounded to FP32.  (The rule above with a constant step and no averaging.) */
+OR_API void or_lambda_update(int32_t m, const int64_t *gsum, int64_t C, double eta,
+                             int32_t project, float sg, float *lambda) {
+    or_lambda_update_rule(m, gsum, C, eta, project, sg, 0u, 0.0, 0, 0.0, NULL, lambda);
 }
 
 /* Best feasible state among the sweep-end states of C annealing runs.  The paper checks every
@@ -475,6 +504,8 @@ OR_API void or_run_best(int32_t n, int32_t m, int32_t nprime, const int64_t *W, 
  * built from b, and b_check > b is the capacity tightening B' < B of Sec. IV-B (b holding B').
  * run_best = 1: the sample stored from a chain is its best feasible sweep-end state
  * (or_run_best) instead of its last state; lambda still steps on the last states.
+ * eta_decay, eta_sqrt, mu: the step-size rule of or_lambda_update_rule (0, 0, 0: Algorithm 1's
+ * constant step), with the outer-iteration index kk and the average starting at 0.
  * Outputs: *best_cost (INT64_MAX if nothing feasible), best_x (N' bytes), best_iter/best_chain,
  * lambda_trace (K x m: lambda after each update, may be NULL), *feasible_count (stored feasible
  * samples), and optionally every last sample's cost (K x C) and constraint values (K x C x m). */
@@ -482,6 +513,7 @@ OR_API void or_solve(int32_t n, int32_t m, const int64_t *W, const int64_t *h, c
                      const int64_t *b, const int64_t *b_check, float alpha, float density,
                      float penalty, int32_t K, int32_t C, int32_t T, float beta_max, double eta,
                      uint64_t seed, uint32_t iter0, int32_t project, int32_t run_best,
+                     double eta_decay, int32_t eta_sqrt, double mu,
                      const float *lambda0, int64_t *best_cost, uint8_t *best_x,
                      int32_t *best_iter, int32_t *best_chain, float *lambda_trace,
                      int64_t *feasible_count, int64_t *cost_out, int64_t *g_out) {
@@ -497,6 +529,7 @@ OR_API void or_solve(int32_t n, int32_t m, const int64_t *W, const int64_t *h, c
     float *lambda = (float *)malloc(sizeof(float) * (size_t)(m > 0 ? m : 1));
     int64_t *g = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
     int64_t *gsum = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+    double *avg = (double *)calloc((size_t)(m > 0 ? m : 1), sizeof(double));
     uint8_t *trace = run_best ? (uint8_t *)malloc((size_t)C * T * nprime) : NULL;
     int64_t *rcost = run_best ? (int64_t *)malloc(sizeof(int64_t) * (size_t)C) : NULL;
     uint8_t *rx = run_best ? (uint8_t *)malloc((size_t)C * nprime) : NULL;
@@ -533,7 +566,8 @@ OR_API void or_solve(int32_t n, int32_t m, const int64_t *W, const int64_t *h, c
                 }
             }
         }
-        or_lambda_update(m, gsum, C, eta, project, sc[1], lambda);
+        or_lambda_update_rule(m, gsum, C, eta, project, sc[1], kk, eta_decay, eta_sqrt, mu, avg,
+                              lambda);
         if (lambda_trace)
             for (int32_t k = 0; k < m; k++) lambda_trace[(size_t)it * m + k] = lambda[k];
     }
@@ -544,6 +578,7 @@ OR_API void or_solve(int32_t n, int32_t m, const int64_t *W, const int64_t *h, c
     free(lambda);
     free(g);
     free(gsum);
+    free(avg);
     free(trace);
     free(rcost);
     free(rx);

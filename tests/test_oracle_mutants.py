@@ -65,6 +65,13 @@ MUTANTS = [
      ["test_run_best_is_the_best_feasible_sweep_end_state"]),
     ("tightened solve checks the reduced capacities", "if (!b_check) b_check = b;",
      "b_check = b;", ["test_capacity_tightening_checks_the_true_capacities"]),
+    ("averaging weights swapped", "d = mu * avg[k] + (1.0 - mu) * mean;",
+     "d = (1.0 - mu) * avg[k] + mu * mean;", ["test_step_rule_closed_forms"]),
+    ("square-root decay ignored", "if (eta_sqrt) den = sqrt(den);", "(void)eta_sqrt;",
+     ["test_step_rule_closed_forms"]),
+    ("decay on the relative iteration", "or_lambda_update_rule(m, gsum, C, eta, project, sc[1], kk,",
+     "or_lambda_update_rule(m, gsum, C, eta, project, sc[1], (uint32_t)it,",
+     ["test_solve_step_rule_matches_the_step_function"]),
 ]
 
 
@@ -92,8 +99,9 @@ def test_planted_mistake_is_caught(name, orig, mut, tests, tmpdir_mod):
             fn = getattr(pins, t)
             params = {"test_energy_identity_exhaustive": {"kind": ["qkp", "mkp"]},
                       "test_run_best_is_the_best_feasible_sweep_end_state":
-                          {"kind": ["qkp", "mkp", "qkp_tight"]}}.get(t, {})
-            runs = [dict(kind=k) for k in params["kind"]] if params else [{}]
+                          {"kind": ["qkp", "mkp", "qkp_tight"]},
+                      "test_step_rule_closed_forms": {"eta_sqrt": [False, True]}}.get(t, {})
+            runs = [{name: v} for name, vals in params.items() for v in vals] or [{}]
             for kw in runs:
                 try:
                     fn(**kw)

@@ -396,6 +396,65 @@ def test_lambda_invariants():
                           oracle.lambda_update(g1, 1, 20.0, False, sg, lam0))
 
 
+def test_step_rule_reduces_to_algorithm1():
+    """With no decay and no averaging the step-size rule is Algorithm 1's constant step, bit
+    for bit, at any iteration index."""
+    r = np.random.default_rng(9)
+    sg = np.float32(1 / 3000)
+    lam = r.random(6).astype(np.float32)
+    for it in range(40):
+        gs = r.integers(-4000, 4000, 6) * 16
+        want = oracle.lambda_update(gs, 16, 20.0, True, sg, lam)
+        got = oracle.lambda_update_rule(gs, 16, 20.0, True, sg, lam, it)
+        assert np.array_equal(got, want)
+        lam = want
+
+
+@pytest.mark.parametrize("eta_sqrt", [False, True])
+def test_step_rule_closed_forms(eta_sqrt):
+    """A constant subgradient mean gbar from iteration it0 on: the average after j steps is
+    (1 - mu^j) gbar, and lambda moves by the sum of eta/(1 + c it) (or its square root)
+    sigma_g (1 - mu^(j+1)) gbar; checked against the closed sums in exact rationals (the
+    decay) and FP64, within the FP32 rounding of lambda at each step."""
+    from fractions import Fraction as Fr
+    C, gbar, eta, c, mu, sg, it0, K = 16, 7, 3000.0, 0.5, 0.75, np.float32(2.0 ** -12), 5, 30
+    lam = np.array([0.5], np.float32)
+    avg = np.zeros(1, np.float64)
+    for j in range(K):
+        lam = oracle.lambda_update_rule(np.array([gbar * C]), C, eta, False, sg, lam, it0 + j,
+                                        decay=c, eta_sqrt=eta_sqrt, mu=mu, avg=avg)
+    assert abs(avg[0] - (1 - mu ** K) * gbar) <= 1e-12 * gbar
+    total = 0.0
+    for j in range(K):
+        den = Fr(1) + Fr(c) * (it0 + j)
+        step = float(Fr(eta) / den) if not eta_sqrt else eta / math.sqrt(float(den))
+        total += step * float(sg) * (1 - mu ** (j + 1)) * gbar
+    want = 0.5 + total
+    assert abs(float(lam[0]) - want) <= K * float(np.spacing(np.float32(want)))
+    # the two rules differ by far more than that tolerance
+    other = 0.0
+    for j in range(K):
+        den = 1.0 + c * (it0 + j)
+        step = eta / (math.sqrt(den) if not eta_sqrt else den)
+        other += step * float(sg) * (1 - mu ** (j + 1)) * gbar
+    assert abs(other - total) > 100 * K * float(np.spacing(np.float32(want)))
+
+
+def test_solve_step_rule_matches_the_step_function():
+    """Algorithm 1 with the step-size rule equals the rule applied to the oracle's own last
+    samples (decay on the absolute iteration index, the average starting at 0)."""
+    inst = wl.qkp(30, 0.5, 6)
+    p = _problem(inst)
+    kw = dict(K=10, C=8, T=60, beta_max=10.0, eta=200.0, seed=9, iter0=3, keep_samples=True)
+    res = oracle.solve(p, eta_decay=0.3, eta_sqrt=True, momentum=0.6, **kw)
+    lam = np.zeros(1, np.float32)
+    avg = np.zeros(1, np.float64)
+    for k in range(10):
+        lam = oracle.lambda_update_rule(res.g[k].sum(axis=0), 8, 200.0, True, p.sigma_g, lam,
+                                        3 + k, decay=0.3, eta_sqrt=True, mu=0.6, avg=avg)
+        assert np.array_equal(res.lambda_trace[k], lam)
+
+
 def test_algorithm1_single_chain_no_projection():
     """With C = 1 and no projection the batch step is Algorithm 1's lambda <- lambda + eta g(x_k)
     applied to the last sample of each run, and the returned solution is the best stored
