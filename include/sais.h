@@ -172,6 +172,10 @@ typedef struct sais_solve_params {
     int32_t run_best;        /* 1: the sample kept from each chain is its best feasible
                                 sweep-end state (sais_sample_run_best) instead of its last
                                 state; the multipliers still step on the last states        */
+    double eta_decay;        /* step-size rule of sais_update_lambda_rule (0: constant eta) */
+    int32_t eta_sqrt;        /* 1: eta / sqrt(1 + eta_decay k) instead of eta / (1 + ...)   */
+    double momentum;         /* averaging weight mu in [0, 1) (0: the batch mean itself); the
+                                average starts at 0 in every call                           */
 } sais_solve_params;
 
 /* Results of sais_solve, all caller-allocated HOST arrays (any may be NULL to skip it). */
@@ -264,6 +268,25 @@ SAIS_API sais_status sais_sample_run_best(sais_problem *p, const sais_sample_par
 SAIS_API sais_status sais_update_lambda(sais_problem *p, const int64_t *g, int32_t chains,
                                         double eta, int32_t project_nonneg, float *lambda,
                                         void *stream);
+
+/* sais_update_lambda with a step-size rule (not in the paper).  Sec. III-A relies on the
+ * surrogate-gradient method, which lets the step shrink and the direction combine recent
+ * subgradients.  With k = iter (the outer-iteration index) and per constraint:
+ *   eta_k = eta / (1 + eta_decay k), or eta / sqrt(1 + eta_decay k) when eta_sqrt = 1;
+ *   d = momentum avg + (1 - momentum) mean  (avg: the running average, written back);
+ *   lambda <- lambda + eta_k (sigma_g d), projected on lambda >= 0 if project_nonneg.
+ * FP64 in that order (mean = S/C; den = 1 + eta_decay*k, its square root if asked;
+ * eta_k = eta/den, or eta when eta_decay = 0), each operation rounded once, lambda stored as
+ * FP32.  eta_decay = 0 and momentum = 0 give sais_update_lambda bit for bit.
+ *   avg     device [count*m_stride] FP64 (read and written; start at 0), or NULL when
+ *           momentum = 0
+ * Errors: SAIS_EINVAL (eta_decay < 0 or not finite, momentum outside [0, 1), avg NULL with
+ * momentum != 0), SAIS_ECUDA. */
+SAIS_API sais_status sais_update_lambda_rule(sais_problem *p, const int64_t *g, int32_t chains,
+                                             double eta, int32_t project_nonneg, uint32_t iter,
+                                             double eta_decay, int32_t eta_sqrt,
+                                             double momentum, double *avg, float *lambda,
+                                             void *stream);
 
 /* The "store feasible x_k" step of Algorithm 1 for one batch of samples (Sec. III-A; the
  * feasibility test of Sec. IV-A): among the chains whose sample is feasible, the one of least

@@ -775,6 +775,15 @@ struct RunOut {
     int32_t *nfeas = nullptr;
 };
 
+// The step-size rule's parameters (sais_update_lambda_rule, sais_solve).
+sais_status check_step_rule(double eta_decay, double momentum) {
+    if (!std::isfinite(eta_decay) || eta_decay < 0.0)
+        return fail(SAIS_EINVAL, "eta_decay = %g: need a finite value >= 0", eta_decay);
+    if (!(momentum >= 0.0 && momentum < 1.0))
+        return fail(SAIS_EINVAL, "momentum = %g: need 0 <= momentum < 1", momentum);
+    return SAIS_OK;
+}
+
 sais_status enqueue_sample(sais_problem *p, const sais_sample_params *prm, const float *lambda,
                            const uint32_t *iter_dev, uint32_t *x, int64_t *cost, int64_t *g,
                            uint8_t *feasible, uint32_t *trace, cudaStream_t st,
@@ -981,6 +990,40 @@ sais_status sais_update_lambda(sais_problem *p, const int64_t *g, int32_t chains
     return SAIS_OK;
 }
 
+sais_status sais_update_lambda_rule(sais_problem *p, const int64_t *g, int32_t chains,
+                                    double eta, int32_t project_nonneg, uint32_t iter,
+                                    double eta_decay, int32_t eta_sqrt, double momentum,
+                                    double *avg, float *lambda, void *stream) {
+    if (!p || !g || !lambda) return fail(SAIS_EINVAL, "NULL argument");
+    if (chains < 1) return fail(SAIS_EINVAL, "chains = %d: need >= 1", chains);
+    if (!std::isfinite(eta)) return fail(SAIS_EINVAL, "eta must be finite");
+    sais_status s = check_step_rule(eta_decay, momentum);
+    if (s != SAIS_OK) return s;
+    if (momentum != 0.0 && !avg) return fail(SAIS_EINVAL, "avg is NULL with momentum != 0");
+    DeviceGuard dg(p->device);
+    PostArgs a{};
+    a.inst = p->d_inst;
+    a.count = p->count;
+    a.chains = chains;
+    a.words = p->words;
+    a.m_stride = p->m_stride;
+    a.eta = eta;
+    a.project = project_nonneg ? 1 : 0;
+    a.eta_decay = eta_decay;
+    a.eta_sqrt = eta_sqrt ? 1 : 0;
+    a.momentum = momentum;
+    a.avg = avg;
+    a.iter = iter;
+    a.track_best = 0;
+    a.do_lambda = 1;
+    a.inst_chains = p->d_inst_chains;
+    a.g = g;
+    a.lambda = lambda;
+    cudaError_t e = launch_post(a, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(SAIS_ECUDA, "multiplier update launch: %s", cudaGetErrorString(e));
+    return SAIS_OK;
+}
+
 sais_status sais_track_best(sais_problem *p, const uint32_t *x, const int64_t *cost,
                             const uint8_t *feasible, int32_t chains, uint32_t iter,
                             int64_t *best_cost, uint32_t *best_x, int32_t *best_iter,
@@ -1017,6 +1060,10 @@ sais_status sais_solve(sais_problem *p, const sais_solve_params *prm, sais_solve
     if (!p || !prm || !res) return fail(SAIS_EINVAL, "NULL argument");
     if (prm->iters < 1) return fail(SAIS_EINVAL, "iters = %d: need >= 1", prm->iters);
     if (!std::isfinite(prm->eta)) return fail(SAIS_EINVAL, "eta must be finite");
+    {
+        sais_status r = check_step_rule(prm->eta_decay, prm->momentum);
+        if (r != SAIS_OK) return r;
+    }
     sais_sample_params sp{};
     sp.chains = prm->chains;
     sp.sweeps = prm->sweeps;
@@ -1039,10 +1086,11 @@ sais_status sais_solve(sais_problem *p, const sais_solve_params *prm, sais_solve
            sz_bx = (size_t)count * p->words * 4, sz_bi = (size_t)count * 4,
            sz_fc = (size_t)count * 8, sz_tr = (size_t)K * count * p->m_stride * 4;
     const bool rb = prm->run_best != 0;
-    size_t offs[14], cur = 0;
-    const size_t sizes[14] = {sz_lam, sz_x, sz_cost, sz_g, sz_feas, sz_bc, sz_bx, sz_bi, sz_bi,
-                              sz_fc, sz_tr, 4, rb ? sz_x : 0, rb ? sz_cost : 0};
-    for (int i = 0; i < 14; ++i) {
+    const size_t sz_avg = prm->momentum != 0.0 ? (size_t)count * p->m_stride * 8 : 0;
+    size_t offs[15], cur = 0;
+    const size_t sizes[15] = {sz_lam, sz_x, sz_cost, sz_g, sz_feas, sz_bc, sz_bx, sz_bi, sz_bi,
+                              sz_fc, sz_tr, 4, rb ? sz_x : 0, rb ? sz_cost : 0, sz_avg};
+    for (int i = 0; i < 15; ++i) {
         offs[i] = cur;
         cur = align_up(cur + sizes[i], 256);
     }
@@ -1088,6 +1136,10 @@ sais_status sais_solve(sais_problem *p, const sais_solve_params *prm, sais_solve
     pa.m_stride = p->m_stride;
     pa.eta = prm->eta;
     pa.project = prm->project_nonneg ? 1 : 0;
+    pa.eta_decay = prm->eta_decay;
+    pa.eta_sqrt = prm->eta_sqrt ? 1 : 0;
+    pa.momentum = prm->momentum;
+    pa.avg = sz_avg ? reinterpret_cast<double *>(scr + offs[14]) : nullptr;   // zeroed below
     pa.track_best = 1;
     pa.do_lambda = 1;
     pa.inst_chains = p->d_inst_chains;
@@ -1412,6 +1464,10 @@ sais_status enqueue_sample_internal(sais_problem *p, const sais_sample_params *p
 
 sais_status check_sample_params_internal(const sais_problem *p, const sais_sample_params *prm) {
     return check_sample_params(p, prm);
+}
+
+sais_status check_step_rule_internal(double eta_decay, double momentum) {
+    return check_step_rule(eta_decay, momentum);
 }
 
 sais_status set_error(sais_status s, const char *fmt, ...) {

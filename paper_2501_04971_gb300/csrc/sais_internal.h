@@ -92,6 +92,10 @@ struct PostArgs {
     int32_t m_stride;
     double eta;
     int32_t project;
+    double eta_decay;        // step-size rule (0: constant eta)
+    int32_t eta_sqrt;        // 1: eta / sqrt(1 + eta_decay k)
+    double momentum;         // averaging weight (0: the batch mean)
+    double *avg;             // [count*m_stride] running average (momentum != 0)
     int32_t track_best;      // keep the best feasible sample (sais_track_best)
     int32_t do_lambda;       // take the multiplier step (sais_update_lambda)
     const uint32_t *x;
@@ -151,6 +155,7 @@ sais_status enqueue_sample_internal(sais_problem *p, const sais_sample_params *p
                                    int64_t *cost, int64_t *g, uint8_t *feasible,
                                    uint32_t *run_x, int64_t *run_cost, cudaStream_t stream);
 sais_status check_sample_params_internal(const sais_problem *p, const sais_sample_params *prm);
+sais_status check_step_rule_internal(double eta_decay, double momentum);
 sais_status set_error(sais_status s, const char *fmt, ...);
 // Inference launch of the warm-start network: lambda[dst[r]] = max(0, y(feat row r)).
 sais_status mlp_warm_start_launch(const sais_mlp *m, const float *feat, const int32_t *dst,

@@ -80,11 +80,14 @@ extern "C" sais_status sais_solve_noalloc(sais_problem *p, const sais_solve_para
     sp.chains_per_cta = prm->chains_per_cta;
     st = check_sample_params_internal(p, &sp);
     if (st != SAIS_OK) return st;
+    st = check_step_rule_internal(prm->eta_decay, prm->momentum);
+    if (st != SAIS_OK) return st;
 
     const int count = v.count, C = prm->chains, K = prm->iters;
     const size_t nch = (size_t)count * C;
     const bool rb = prm->run_best != 0;
-    const size_t sizes[14] = {
+    const bool avg_on = prm->momentum != 0.0;
+    const size_t sizes[15] = {
         (size_t)count * v.m_stride * 4,        // lambda
         nch * v.words * 4,                     // x
         nch * 8,                               // cost
@@ -98,9 +101,10 @@ extern "C" sais_status sais_solve_noalloc(sais_problem *p, const sais_solve_para
         (size_t)K * count * v.m_stride * 4,    // lambda trace
         4,                                     // iteration counter
         rb ? nch * v.words * 4 : 0,            // best-in-run states
-        rb ? nch * 8 : 0};                     // best-in-run costs
-    size_t offs[14], need = 0;
-    for (int i = 0; i < 14; ++i) {
+        rb ? nch * 8 : 0,                      // best-in-run costs
+        avg_on ? (size_t)count * v.m_stride * 8 : 0};   // averaged subgradients
+    size_t offs[15], need = 0;
+    for (int i = 0; i < 15; ++i) {
         offs[i] = need;
         need = align256(need + sizes[i]);
     }
@@ -143,6 +147,7 @@ extern "C" sais_status sais_solve_noalloc(sais_problem *p, const sais_solve_para
     uint32_t *d_iter = reinterpret_cast<uint32_t *>(scr + offs[11]);
     uint32_t *d_rx = rb ? reinterpret_cast<uint32_t *>(scr + offs[12]) : nullptr;
     int64_t *d_rc = rb ? reinterpret_cast<int64_t *>(scr + offs[13]) : nullptr;
+    double *d_avg = avg_on ? reinterpret_cast<double *>(scr + offs[14]) : nullptr;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 
 #define NOALLOC_CUDA(expr)                                                              \
@@ -158,6 +163,7 @@ extern "C" sais_status sais_solve_noalloc(sais_problem *p, const sais_solve_para
     NOALLOC_CUDA(cudaMemsetAsync(d_bx, 0, sizes[6], s));
     NOALLOC_CUDA(cudaMemsetAsync(d_fc, 0, sizes[9], s));
     NOALLOC_CUDA(cudaMemsetAsync(d_tr, 0, sizes[10], s));
+    if (avg_on) NOALLOC_CUDA(cudaMemsetAsync(d_avg, 0, sizes[14], s));
     if (prm->lambda0)
         NOALLOC_CUDA(cudaMemcpyAsync(d_lam, prm->lambda0, sizes[0], cudaMemcpyHostToDevice, s));
     init_best_kernel<<<(count + 255) / 256, 256, 0, s>>>(d_bc, d_bi, d_bch, count);
@@ -172,6 +178,10 @@ extern "C" sais_status sais_solve_noalloc(sais_problem *p, const sais_solve_para
     pa.m_stride = v.m_stride;
     pa.eta = prm->eta;
     pa.project = prm->project_nonneg ? 1 : 0;
+    pa.eta_decay = prm->eta_decay;
+    pa.eta_sqrt = prm->eta_sqrt ? 1 : 0;
+    pa.momentum = prm->momentum;
+    pa.avg = d_avg;
     pa.track_best = 1;
     pa.do_lambda = 1;
     pa.x = rb ? d_rx : d_x;   // best-in-run: the kept sample of a chain is its best sweep end

@@ -111,11 +111,24 @@ __global__ void __launch_bounds__(kPostThreads) post_kernel(PostArgs a) {
                 a.best_x[(size_t)j * a.words + w] = a.x[(base + s_best_chain) * a.words + w];
     }
 
-    // Multiplier step (Algorithm 1) with the batch mean of the normalised constraint.
+    // Multiplier step (Algorithm 1) with the batch mean of the normalised constraint, under
+    // the step-size rule (constant eta and no averaging unless asked).
     if (a.do_lambda && tid < m) {
         const float sg = a.inst[j].sigma_g;
         const double mean = __ddiv_rn((double)gsum[tid], (double)C);
-        const double step = __dmul_rn(a.eta, __dmul_rn((double)sg, mean));
+        double eta_k = a.eta;
+        if (a.eta_decay != 0.0) {
+            double den = __dadd_rn(1.0, __dmul_rn(a.eta_decay, (double)iter));
+            if (a.eta_sqrt) den = __dsqrt_rn(den);
+            eta_k = __ddiv_rn(a.eta, den);
+        }
+        double d = mean;
+        if (a.momentum != 0.0) {
+            double *av = a.avg + (size_t)j * a.m_stride + tid;
+            d = __dadd_rn(__dmul_rn(a.momentum, *av), __dmul_rn(__dadd_rn(1.0, -a.momentum), mean));
+            *av = d;
+        }
+        const double step = __dmul_rn(eta_k, __dmul_rn((double)sg, d));
         double l = __dadd_rn((double)a.lambda[(size_t)j * a.m_stride + tid], step);
         if (a.project && l < 0.0) l = 0.0;
         const float nl = __double2float_rn(l);

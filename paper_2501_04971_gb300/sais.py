@@ -52,7 +52,8 @@ class sais_solve_params(ctypes.Structure):
     _fields_ = [("iters", _i32), ("chains", _i32), ("sweeps", _i32), ("beta_max", _f32),
                 ("eta", _f64), ("seed", _u64), ("iter0", _u32), ("project_nonneg", _i32),
                 ("variant", _i32), ("block_k", _i32), ("chains_per_cta", _i32),
-                ("use_graph", _i32), ("lambda0", _P), ("run_best", _i32)]
+                ("use_graph", _i32), ("lambda0", _P), ("run_best", _i32),
+                ("eta_decay", _f64), ("eta_sqrt", _i32), ("momentum", _f64)]
 
 
 class sais_tuning(ctypes.Structure):
@@ -80,6 +81,7 @@ _SIGS = {
     "sais_sample_run_best": [_P, ctypes.POINTER(sais_sample_params), _P, _P, _P, _P, _P, _P, _P,
                              _P, _P, _P],
     "sais_update_lambda": [_P, _P, _i32, _f64, _i32, _P, _P],
+    "sais_update_lambda_rule": [_P, _P, _i32, _f64, _i32, _u32, _f64, _i32, _f64, _P, _P, _P],
     "sais_track_best": [_P, _P, _P, _P, _i32, _u32, _P, _P, _P, _P, _P, _P],
     "sais_solve": [_P, ctypes.POINTER(sais_solve_params), ctypes.POINTER(sais_solve_result), _P],
     "sais_synchronize": [_P, _P],
@@ -199,6 +201,14 @@ def sais_sample_run_best(h, prm, lam_ptr, x_ptr, cost_ptr, g_ptr, feas_ptr, run_
 def sais_update_lambda(h, g_ptr, chains: int, eta: float, project: int, lam_ptr, stream_ptr):
     _check(lib().sais_update_lambda(h, g_ptr, chains, eta, project, lam_ptr, stream_ptr),
            "sais_update_lambda")
+
+
+def sais_update_lambda_rule(h, g_ptr, chains: int, eta: float, project: int, it: int,
+                            eta_decay: float, eta_sqrt: int, momentum: float, avg_ptr, lam_ptr,
+                            stream_ptr):
+    _check(lib().sais_update_lambda_rule(h, g_ptr, chains, eta, project, it, eta_decay,
+                                         eta_sqrt, momentum, avg_ptr, lam_ptr, stream_ptr),
+           "sais_update_lambda_rule")
 
 
 def sais_track_best(h, x_ptr, cost_ptr, feas_ptr, chains: int, it: int, best_cost_ptr,
@@ -438,6 +448,16 @@ class Problem:
         sais_update_lambda(self.handle, _P(g.data_ptr()), chains, eta, int(project),
                            _P(lam.data_ptr()), _stream_ptr(stream))
 
+    def update_lambda_rule(self, g, chains: int, eta: float, project: bool, lam, it: int,
+                           eta_decay: float = 0.0, eta_sqrt: bool = False,
+                           momentum: float = 0.0, avg=None, stream=None):
+        """sais_update_lambda_rule: the step with a decaying eta and an averaged subgradient
+        (avg: FP64 device tensor [count*m_stride], zero before the first step)."""
+        sais_update_lambda_rule(self.handle, _P(g.data_ptr()), chains, eta, int(project), it,
+                                eta_decay, int(eta_sqrt), momentum,
+                                _P(avg.data_ptr()) if avg is not None else None,
+                                _P(lam.data_ptr()), _stream_ptr(stream))
+
     def alloc_best(self):
         """Device state of sais_track_best, initialised (best_cost INT64_MAX, indices -1)."""
         import torch
@@ -462,15 +482,18 @@ class Problem:
     def solve(self, iters: int, chains: int, sweeps: int, beta_max: float, eta: float,
               seed: int, iter0: int = 0, project: bool = True, lambda0=None, variant="plain",
               block_k: int = 0, chains_per_cta: int = 0, use_graph: bool = False,
-              run_best: bool = False, stream=None) -> dict:
+              run_best: bool = False, eta_decay: float = 0.0, eta_sqrt: bool = False,
+              momentum: float = 0.0, stream=None) -> dict:
         """Algorithm 1 on every instance (sais_solve); returns host numpy arrays.  run_best:
-        keep each chain's best feasible sweep-end state instead of its last state."""
+        keep each chain's best feasible sweep-end state instead of its last state; eta_decay,
+        eta_sqrt, momentum: the step-size rule of sais_update_lambda_rule."""
         prm = sais_solve_params()
         prm.iters, prm.chains, prm.sweeps, prm.beta_max = iters, chains, sweeps, beta_max
         prm.eta, prm.seed, prm.iter0, prm.project_nonneg = eta, seed, iter0, int(project)
         prm.variant = _VARIANTS[variant] if isinstance(variant, str) else int(variant)
         prm.block_k, prm.chains_per_cta, prm.use_graph = block_k, chains_per_cta, int(use_graph)
         prm.run_best = int(run_best)
+        prm.eta_decay, prm.eta_sqrt, prm.momentum = eta_decay, int(eta_sqrt), momentum
         l0 = None
         if lambda0 is not None:
             l0 = np.ascontiguousarray(np.asarray(lambda0, dtype=np.float32).reshape(-1))

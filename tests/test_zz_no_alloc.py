@@ -29,13 +29,14 @@ def _built():
 
 
 def _noalloc(prob, iters, chains, sweeps, beta_max, eta, seed, variant="plain", lambda0=None,
-             run_best=False):
+             run_best=False, eta_decay=0.0, eta_sqrt=False, momentum=0.0):
     """Call sais_solve_noalloc through the C-ABI with host result arrays."""
     prm = sais.sais_solve_params()
     prm.iters, prm.chains, prm.sweeps, prm.beta_max = iters, chains, sweeps, beta_max
     prm.eta, prm.seed, prm.iter0, prm.project_nonneg = eta, seed, 0, 1
     prm.variant = sais._VARIANTS[variant]
     prm.run_best = int(run_best)
+    prm.eta_decay, prm.eta_sqrt, prm.momentum = eta_decay, int(eta_sqrt), momentum
     keep = None
     if lambda0 is not None:
         keep = np.ascontiguousarray(lambda0, np.float32).reshape(-1)
@@ -72,14 +73,17 @@ def test_noalloc_matches_solve_on_two_calls(variant):
 
 
 def test_noalloc_run_best_with_tightening_matches_solve():
-    """The best-in-run option and tightened capacities through the allocation-free form."""
+    """The best-in-run option, tightened capacities and the step-size rule through the
+    allocation-free form."""
     insts = [wl.qkp(100, 0.5, 8), wl.qkp(80, 0.75, 9)]
     for inst in insts:
         inst.b_tight = np.maximum(1, (np.asarray(inst.b) * 4) // 5).astype(np.int64)
     prob = sais.Problem(insts)
+    rule = dict(eta_decay=0.3, eta_sqrt=False, momentum=0.6)
     for variant in ("plain", "blocked"):
-        want = prob.solve(6, 128, 120, 10.0, 20.0, 21, variant=variant, run_best=True)
-        st, got = _noalloc(prob, 6, 128, 120, 10.0, 20.0, 21, variant=variant, run_best=True)
+        want = prob.solve(6, 128, 120, 10.0, 20.0, 21, variant=variant, run_best=True, **rule)
+        st, got = _noalloc(prob, 6, 128, 120, 10.0, 20.0, 21, variant=variant, run_best=True,
+                           **rule)
         assert st == sais.SAIS_OK, sais.sais_last_error()
         for k in KEYS:
             assert np.array_equal(got[k], want[k]), (variant, k)
