@@ -398,10 +398,14 @@ __global__ void __launch_bounds__(kPThreads, 1)
                             }
                         }
                         const float Fi = Fr[ii];
-                        const int xi = (xw >> (sb + ii)) & 1;
+                        // Spin ii's bit is unchanged since the block started: read from the block-start word,
+                        // so that it does not wait on the earlier flips.  The +-D_i term goes into the first
+                        // product (one rounding and one dependent operation fewer; the error bound holds).
+                        const int xi = (xold >> (sb + ii)) & 1;
                         float akf[MC];
-                        float acc = sf * Fi;
-                        const float tabs = fabsf(acc);
+                        const float Di = Dp[ii];
+                        float acc = fmaf(sf, Fi, xi ? Di : -Di);
+                        const float tabs = fabsf(sf * Fi);
 #pragma unroll
                         for (int k = 0; k < MC; ++k) {
                             if (k < kPreM)
@@ -410,11 +414,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
                                 akf[k] = (k < m) ? (float)__ldg(acol + (size_t)s * m + k) : 0.f;
                             acc = fmaf(-akf[k], c[k], acc);
                         }
-                        const float Di = Dp[ii];
-                        acc = fmaf(xi ? 1.f : -1.f, Di, acc);
-                        const float z = hb * acc;
                         const float theta = th[ii];
-                        const float y = z + theta;
+                        const float y = fmaf(hb, acc, theta);
                         const float bound = ez * (tabs + Sp[ii] * Mmax + Di) +
                                             kThetaRelErr * fabsf(theta) + kThetaAbsErr;
                         near_tie |= !(fabsf(y) > bound);
