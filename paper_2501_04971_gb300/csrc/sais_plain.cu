@@ -100,10 +100,24 @@ __global__ void __launch_bounds__(128) plain_sampler_kernel(SampleArgs a) {
                 int32_t ak[MC];
                 float acc = sf * Fi;
                 const float tabs = fabsf(acc);
+                if constexpr (MC >= 16) {
+                    // Four independent partial sums instead of one chain of m fused products
+                    // (the bound gamma_{m+1} sum|terms| holds for any order of the additions);
+                    // measured faster from m = 30 on, slower at m = 5.
+                    float p1 = 0.f, p2 = 0.f, p3 = 0.f;
 #pragma unroll
-                for (int k = 0; k < MC; ++k) {
-                    ak[k] = (k < m) ? __ldg(acol + (size_t)i * m + k) : 0;
-                    acc = fmaf(-(float)ak[k], c[k], acc);
+                    for (int k = 0; k < MC; ++k) {
+                        ak[k] = (k < m) ? __ldg(acol + (size_t)i * m + k) : 0;
+                        float &pk = (k & 3) == 0 ? acc : ((k & 3) == 1 ? p1 : ((k & 3) == 2 ? p2 : p3));
+                        pk = fmaf(-(float)ak[k], c[k], pk);
+                    }
+                    acc = (acc + p1) + (p2 + p3);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < MC; ++k) {
+                        ak[k] = (k < m) ? __ldg(acol + (size_t)i * m + k) : 0;
+                        acc = fmaf(-(float)ak[k], c[k], acc);
+                    }
                 }
                 const float Di = __ldg(Dv + i);
                 acc = fmaf(xi ? 1.f : -1.f, Di, acc);
