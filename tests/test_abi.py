@@ -104,6 +104,36 @@ def test_describe_rejects_invalid_instances(L):
     _bad(x, sais.SAIS_EINVAL)
 
 
+@pytest.mark.parametrize("frac", [1.0, 0.8, 0.5, 0.01])
+def test_describe_tightened_capacities_match_oracle(L, frac):
+    """Capacity tightening (Sec. IV-B): the sampled problem is the one built from B' -- slack
+    bits, sigma_g and the penalty rule on that N' -- bit for bit the oracle's problem with
+    b = B'; b_tight = b leaves the scalars unchanged."""
+    for inst in (wl.qkp(120, 0.5, 2), wl.mkp(90, 5, 3), wl.qkp(300, 0.25, 1)):
+        bt = np.maximum(1, np.floor(np.asarray(inst.b) * frac)).astype(np.int64)
+        inst.b_tight = bt
+        s = sais.describe(inst)
+        ref = oracle.Problem(inst.n, inst.m, inst.W, inst.h, inst.A, bt, alpha=inst.alpha,
+                             density=inst.density, b_check=inst.b)
+        assert s.n_spins == ref.nprime
+        assert np.float32(s.sigma_g) == ref.sigma_g
+        assert np.float32(s.penalty) == ref.P
+        assert s.density == ref.d_used
+        if frac == 1.0:
+            inst.b_tight = None
+            plain = sais.describe(inst)
+            assert (plain.n_spins, plain.sigma_g, plain.penalty) == \
+                (s.n_spins, s.sigma_g, s.penalty)
+
+
+def test_describe_rejects_bad_tightened_capacities(L):
+    x = wl.mkp(30, 3, 1)
+    x.b_tight = np.asarray(x.b, np.int64) + np.array([0, 1, 0])
+    _bad(x, sais.SAIS_EINVAL)                       # B' > B
+    x.b_tight = np.array([1, 0, 1], np.int64)
+    _bad(x, sais.SAIS_EINVAL)                       # B' < 1
+
+
 def test_last_error_message(L):
     x = wl.qkp(20, 0.5, 1); x.b = np.array([-3])
     with pytest.raises(sais.SaisError):
