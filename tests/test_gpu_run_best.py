@@ -48,10 +48,10 @@ def _lam_dev(lams, m_stride):
     return torch.tensor(a.reshape(-1), device="cuda:0")
 
 
-def _run_best_vs_oracle(insts, lams, C, T, beta_max, seed, it, variant):
+def _run_best_vs_oracle(insts, lams, C, T, beta_max, seed, it, variant, **kw):
     prob = sais.Problem(insts)
     out = prob.sample_run_best(_lam_dev(lams, prob.m_stride), C, T, beta_max, seed, it,
-                               variant=variant)
+                               variant=variant, **kw)
     torch.cuda.synchronize()
     prob.synchronize()
     x = out["x"].cpu().numpy()
@@ -80,6 +80,42 @@ def test_run_best_qkp(variant):
     """QKP N=120 (W resident in the blocked sampler), 128 chains x 150 sweeps."""
     insts = [wl.qkp(120, 0.5, 3), wl.qkp(100, 0.75, 4)]
     assert _run_best_vs_oracle(insts, [[0.4], [0.8]], 128, 150, 10.0, 7, 2, variant) > 0
+
+
+@pytest.mark.parametrize("variant,kw", [("blocked", {"block_k": 32}),
+                                        ("plain", {"chains_per_cta": 128}),
+                                        ("plain", {"chains_per_cta": 64})])
+def test_run_best_launch_shapes(variant, kw):
+    """Other launch shapes: 32-spin blocks, 64 and 128 chains per CTA (100 chains: a ragged
+    last CTA)."""
+    insts = [wl.qkp(90, 0.5, 21), wl.qkp(70, 0.75, 22)]
+    assert _run_best_vs_oracle(insts, [[0.6], [0.9]], 100, 120, 10.0, 4, 3, variant, **kw) > 0
+
+
+def test_run_best_per_instance_chains():
+    """Per-instance chain counts (SAIS_AUTO work lists): chains past an instance's count are
+    neither sampled into the outputs nor tracked; the others equal the plain sampler's."""
+    insts = [wl.qkp(100, 0.5, 31), wl.mkp(60, 3, 32), wl.qkp(200, 0.25, 33)]
+    lams = [[0.5], [1.0] * 3, [0.7]]
+    prob = sais.Problem(insts)
+    counts = np.array([128, 37, 200], np.int32)
+    prob.set_instance_chains(counts)
+    lam = _lam_dev(lams, prob.m_stride)
+    a = prob.sample_run_best(lam, 256, 60, 10.0, 6, 0, variant="auto")
+    torch.cuda.synchronize()
+    prob.synchronize()
+    run = {k: v.cpu().numpy() for k, v in a["run"].items()}
+    for j, inst in enumerate(insts):
+        ref = _ref(inst)
+        J, hI, _ = ref.ising(np.asarray(lams[j], np.float32))
+        _, tr = oracle.anneal(J, hI, 10.0, 60, 6 + j, 0, int(counts[j]), trace=True)
+        cost, rx, sweep, nfeas = oracle.run_best(ref, tr)
+        c = int(counts[j])
+        assert np.array_equal(run["cost"][j, :c], cost), j
+        assert np.array_equal(run["sweep"][j, :c], sweep), j
+        assert np.array_equal(run["nfeas"][j, :c], nfeas), j
+        assert np.array_equal(sais.unpack_bits(run["x"][j, :c], ref.nprime), rx), j
+    prob.close()
 
 
 def test_run_best_mkp_plain():
