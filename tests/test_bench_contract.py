@@ -45,3 +45,30 @@ def test_our_arm_line_small():
     assert {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"} <= set(d["e2e"])
     assert d["gpu_launches"] > 0
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])
+
+
+@pytest.mark.gpu
+def test_our_arm_optional_sections_small():
+    """The best-in-run / tightening section and the paper-scale section at tiny sizes: their
+    keys and the accounting of samples (no quality claim at these sizes)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    d = _run(["--per-density", "2", "--sweeps", "20", "--steps", "1", "--warmup", "3",
+              "--no-gap", "--no-ragged", "--no-e2e", "--no-plain", "--no-cpu", "--run-best",
+              "--rb-instances", "2", "--rb-iters", "3", "--paper-scale", "--ps-per-class", "1",
+              "--ps-iters", "256"], 900)
+    rb = d["run_best_mkp"]
+    for name in ("last_sample", "run_best", "run_best_tight_0.95", "run_best_tight_0.9"):
+        assert {"within_1pct", "any_feasible", "median_gap", "feasible_sample_fraction",
+                "device_ms"} <= set(rb[name])
+        assert 0.0 <= rb[name]["feasible_sample_fraction"] <= 1.0
+    ps = d["paper_scale_qkp"]
+    assert ps["instances"] == 12
+    assert ps["paper_single_chain"]["samples_per_instance"] == 256
+    assert ps["batched_equal_samples"]["samples_per_instance"] == 256
+    assert ps["batched_equal_iterations"]["samples_per_instance"] == 256 * 128
+    for run in ("paper_single_chain", "batched_equal_samples", "batched_equal_iterations"):
+        for n in ("100", "200", "300"):
+            acc = ps[run]["accuracy_by_size"][n]
+            assert 0.0 <= acc["min_accuracy_pct"] <= acc["median_accuracy_pct"] <= 100.0
