@@ -111,7 +111,6 @@ template <int MC, int K, bool kStream, bool kHiLo>
 __global__ void __launch_bounds__(kThreadsBlocked, 1)
     blocked_sampler_kernel(SampleArgs a, int32_t *status, long long dec_wait_polls,
                            uint32_t tmem_cols) {
-    static_assert(kStream || !kHiLo, "the hi/lo split streams W");
     extern __shared__ __align__(1024) unsigned char smem[];
     constexpr int kPreM = MC < 2 ? MC : 2;   // constraint columns in the per-spin record
     constexpr uint32_t kRing = 3;
@@ -359,11 +358,6 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                     cb[k] = c[k];
                 }
                 bool near_tie = false;
-                // W resident: an even spin's corrections of the block's later fields (beyond the
-                // next one) wait for the following odd spin, which applies both spins' behind
-                // one vote; the previous spin's row and flip are kept here.
-                uint4 wprev[K / 8];
-                float dfprev = 0.f;
 #pragma unroll
                 for (int ii = 0; ii < K; ++ii) {
                     const int s = s0 + ii;
@@ -454,22 +448,7 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                                 }
                             };
                             Fr[ii + 1] = fmaf(df, wcol(ii + 1), Fr[ii + 1]);
-                            if constexpr (!kStream) {
-                                if ((ii & 1) == 0) {
-                                    // even spin: its later corrections go with the next spin's
-#pragma unroll
-                                    for (int cc = 0; cc < K / 8; ++cc) wprev[cc] = wrow[cc];
-                                    dfprev = df;
-                                } else if (__any_sync(0xffffffffu, df != 0.f || dfprev != 0.f)) {
-                                    // odd spin: the previous spin's flip into fields ii+1.. and
-                                    // this spin's into ii+2.. (the next field already has it)
-#pragma unroll
-                                    for (int jj = ii + 1; jj < K; ++jj) {
-                                        Fr[jj] = fmaf(dfprev, half(wprev[jj >> 3], jj & 7), Fr[jj]);
-                                        if (jj >= ii + 2) Fr[jj] = fmaf(df, wcol(jj), Fr[jj]);
-                                    }
-                                }
-                            } else if (ii + 2 < K && __any_sync(0xffffffffu, df != 0.f)) {
+                            if (ii + 2 < K && __any_sync(0xffffffffu, df != 0.f)) {
 #pragma unroll
                                 for (int jj = ii + 2; jj < K; ++jj)
                                     Fr[jj] = fmaf(df, wcol(jj), Fr[jj]);
