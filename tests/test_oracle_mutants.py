@@ -65,6 +65,11 @@ MUTANTS = [
      ["test_run_best_is_the_best_feasible_sweep_end_state"]),
     ("tightened solve checks the reduced capacities", "if (!b_check) b_check = b;",
      "b_check = b;", ["test_capacity_tightening_checks_the_true_capacities"]),
+    ("run best stores the last state", "const uint8_t *sx = run_best ? rx + (size_t)c * nprime : x;",
+     "const uint8_t *sx = x;", ["test_solve_run_best_keeps_the_multiplier_path",
+                                 "test_solve_run_best_stores_each_chains_best_sweep_end"]),
+    ("decay grows the step", "eta_it = eta / den;", "eta_it = eta * den;",
+     ["test_step_rule_closed_forms"]),
     ("averaging weights swapped", "d = mu * avg[k] + (1.0 - mu) * mean;",
      "d = (1.0 - mu) * avg[k] + mu * mean;", ["test_step_rule_closed_forms"]),
     ("square-root decay ignored", "if (eta_sqrt) den = sqrt(den);", "(void)eta_sqrt;",

@@ -582,6 +582,35 @@ def test_solve_run_best_keeps_the_multiplier_path():
     assert _np_cost(inst, rb.best_x[None, :])[0] == rb.best_cost
 
 
+def test_solve_run_best_stores_each_chains_best_sweep_end():
+    """Algorithm 1 with the best-in-run option, rebuilt from its parts: per iteration the
+    annealing traces at that iteration's multipliers, each chain's best feasible sweep end
+    (or_run_best), the first least-cost one in (iteration, chain) order, and the count of
+    chains with one."""
+    inst = wl.mkp(30, 3, 11)
+    p = _problem(inst)
+    lam0 = np.full(3, 2.0, np.float32)
+    K, C, T, seed = 3, 6, 80, 13
+    res = oracle.solve(p, K=K, C=C, T=T, beta_max=20.0, eta=50.0, seed=seed, lambda0=lam0,
+                       run_best=True)
+    lams = [lam0] + [res.lambda_trace[k] for k in range(K - 1)]
+    best, where, bx, count = None, None, None, 0
+    for k in range(K):
+        J, hI, _ = p.ising(lams[k])
+        _, tr = oracle.anneal(J, hI, 20.0, T, seed, k, C, trace=True)
+        cost, x, sweep, _ = oracle.run_best(p, tr)
+        for c in range(C):
+            if sweep[c] < 0:
+                continue
+            count += 1
+            if best is None or cost[c] < best:
+                best, where, bx = int(cost[c]), (k, c), x[c]
+    assert count > 0 and best is not None
+    assert res.feasible_count == count
+    assert res.best_cost == best and (res.best_iter, res.best_chain) == where
+    assert np.array_equal(res.best_x, bx)
+
+
 def test_capacity_tightening_checks_the_true_capacities():
     """B' < B (Sec. IV-B): the sampled problem is the one built from B' (its slack bits,
     scales and penalty), feasibility uses B, and a long run on a tiny instance reaches the
