@@ -104,10 +104,38 @@ def workload_name(a) -> str:
 # CPU oracle timing (cpu_baseline leg and --impl reference)
 # ------------------------------------------------------------------------------------------
 
-def oracle_rate(insts, seconds: float, chains: int):
+def cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (x86: model name; Arm: the CPU part), with the
+    machine type."""
+    import platform
+    try:
+        lines = open("/proc/cpuinfo").read().splitlines()
+        for key in ("model name", "Model", "CPU part"):
+            for line in lines:
+                if line.startswith(key) and ":" in line:
+                    return f"{platform.machine()}, {key}: {line.split(':', 1)[1].strip()}"
+    except OSError:
+        pass
+    return f"{platform.machine()} {platform.processor()}".strip()
+
+
+def oracle_rate(insts, seconds: float, chains: int, threads: int = 0):
     """The oracle's annealing runs (or_anneal, OpenMP over chains) on a bounded sample: the
     first instance of each density, `chains` chains, sweep count calibrated so the run takes
-    about `seconds`.  Returns (updates/s, cores, description)."""
+    about `seconds`; `threads` > 0 limits the OpenMP threads for the run.  Returns
+    (updates/s, threads used, description)."""
+    import oracle
+    prev = oracle.max_threads()
+    if threads:
+        oracle.set_threads(threads)
+    try:
+        return _oracle_rate(insts, seconds, chains)
+    finally:
+        if threads:
+            oracle.set_threads(prev)
+
+
+def _oracle_rate(insts, seconds: float, chains: int):
     import oracle
     sample = [insts[i * (len(insts) // len(DENSITIES))] for i in range(len(DENSITIES))]
     probs = []
@@ -128,10 +156,21 @@ def oracle_rate(insts, seconds: float, chains: int):
     u, dt = run(2)
     T = max(2, int(2 * seconds / max(dt, 1e-6)))
     u, dt = run(T)
-    cores = os.cpu_count() or 1
+    cores = oracle.max_threads()
     desc = (f"oracle or_anneal, {len(probs)} instances (one per density), {chains} chains x "
-            f"{T} sweeps each, {u} updates in {dt:.1f} s, OpenMP over chains")
+            f"{T} sweeps each, {u} updates in {dt:.1f} s, OpenMP over chains, {cores} threads")
     return u / dt, cores, desc
+
+
+def cpu_baseline_line(insts, seconds: float, value=None, cores=None, desc=None):
+    """The cpu_baseline object: the oracle on all host cores (given, or measured here) and on
+    one core (a quarter of the time), with the host CPU named."""
+    if value is None:
+        value, cores, desc = oracle_rate(insts, seconds, 2 * (os.cpu_count() or 1))
+    v1, _, d1 = oracle_rate(insts, max(0.5, seconds / 4), 4, threads=1)
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+            "single_thread": {"value": v1, "unit": UNIT, "cores": 1, "sample": d1},
+            "cpu": cpu_model()}
 
 
 def reference_arm(a):
@@ -154,8 +193,7 @@ def reference_arm(a):
             "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(a), "sample": "bounded CPU sample"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": desc},
+            "cpu_baseline": cpu_baseline_line(insts, per, v, cores, desc),
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -697,8 +735,7 @@ def main():
         return
     cpu = None
     if world == 1 and not a.no_cpu:
-        v, cores, desc = oracle_rate(insts, a.cpu_seconds, 2 * (os.cpu_count() or 1))
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        cpu = cpu_baseline_line(insts, a.cpu_seconds)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,

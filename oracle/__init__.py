@@ -82,6 +82,8 @@ _SIGS = {
                                        _P]),
     "or_brute_force_opt": (_i64, [_i32, _i32, _P, _P, _P, _P, _P]),
     "or_bf16_round": (_f32, [_f32]),
+    "or_set_threads": (None, [_i32]),
+    "or_max_threads": (_i32, []),
     "or_features": (None, [_i32, _i32, _P, _P, _P, _P, _f32, _f32, _f32, _P]),
     "or_mlp_forward": (None, [_P, _P, _P, _i32, _i32, _P]),
     "or_mlp_grad": (_f64, [_P, _P, _P, _P, _i32, _i32, _P]),
@@ -355,6 +357,15 @@ def solve(p: Problem, K: int, C: int, T: int, beta_max: float, eta: float, seed:
 MLP_PARAMS, MLP_HIDDEN = 20612, 128
 MLP_OFF_W1, MLP_OFF_W2, MLP_OFF_W3, MLP_OFF_B3 = 0, 2048, 20480, 20608
 MLP_BF16, MLP_ABS = 1, 2
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops (timing only; results do not depend on it)."""
+    load().or_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(load().or_max_threads())
 
 
 def bf16_round(v: float) -> float:

@@ -44,6 +44,7 @@
  *     argmin keep the first achiever in (iteration, chain) order.
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -56,6 +57,10 @@
 
 /* Q = floor(log2(b)) + 1 binary slack variables encode 0 <= x_S <= b (Sec. IV-A).  For b >= 1
  * this is the number of binary digits of b. */
+/* Threads of the OpenMP loops over chains (timing the oracle on one core or on all). */
+OR_API void or_set_threads(int32_t n) { omp_set_num_threads(n > 0 ? n : 1); }
+OR_API int32_t or_max_threads(void) { return (int32_t)omp_get_max_threads(); }
+
 OR_API int32_t or_slack_bits(int64_t b) {
     int32_t q = 0;
     if (b <= 0) return 0;

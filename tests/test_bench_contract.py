@@ -25,7 +25,10 @@ def test_reference_arm_line():
     d = _run(["--impl", "reference", "--steps", "1", "--warmup", "1", "--cpu-seconds", "1"], 600)
     assert BASE_KEYS <= set(d)
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
+    assert cb["single_thread"]["cores"] == 1 and cb["single_thread"]["value"] > 0
+    assert cb["cpu"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"]
 
@@ -42,6 +45,7 @@ def test_our_arm_line_small():
     assert {"bound", "achieved", "peak", "unit", "frac", "traffic"} <= set(r)
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-9
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] > 0
+    assert d["cpu_baseline"]["single_thread"]["value"] > 0
     assert {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"} <= set(d["e2e"])
     assert d["gpu_launches"] > 0
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])
