@@ -139,3 +139,21 @@ def test_last_error_message(L):
     with pytest.raises(sais.SaisError):
         sais.describe(x)
     assert "b[0]" in sais.sais_last_error()
+
+
+def test_no_cpu_fallback(L, tmp_path):
+    """The product path fails loudly: a missing library raises, and without an sm_103 device
+    creating a problem returns SAIS_EUNSUPPORTED or SAIS_ECUDA instead of computing anywhere
+    else."""
+    with pytest.raises(RuntimeError):
+        sais.lib(str(tmp_path / "libsais_missing.so"))
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except ImportError:
+        has_gpu = False
+    if has_gpu:
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(sais.SaisError) as e:
+        sais.Problem(wl.qkp(20, 0.5, 1))
+    assert e.value.status in (sais.SAIS_EUNSUPPORTED, sais.SAIS_ECUDA)
