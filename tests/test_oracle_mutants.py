@@ -77,6 +77,16 @@ MUTANTS = [
     ("decay on the relative iteration", "or_lambda_update_rule(m, gsum, C, eta, project, sc[1], kk,",
      "or_lambda_update_rule(m, gsum, C, eta, project, sc[1], (uint32_t)it,",
      ["test_solve_step_rule_matches_the_step_function"]),
+    ("replay continues from its own decision", "ms[i] = x1[i] ? 1 : -1;", "ms[i] = mine ? 1 : -1;",
+     ["test_replay_sweep_margins_from_the_lagrangian"]),
+    ("replay draws the wrong noise word",
+     "const double rho = or_pbit_noise(seed, iter, chain, t, (uint32_t)i);\n        const double v =",
+     "const double rho = or_pbit_noise(seed, iter, chain, t, (uint32_t)i ^ 1u);\n        const double v =",
+     ["test_replay_sweep_reproduces_the_oracles_own_trace",
+      "test_replay_sweep_margins_from_the_lagrangian"]),
+    ("replay compares with the start state", "if (mine != (int)(x1[i] != 0))",
+     "if (mine != (int)(x0[i] != 0))", ["test_replay_sweep_reproduces_the_oracles_own_trace",
+                                         "test_replay_sweep_margins_from_the_lagrangian"]),
 ]
 
 

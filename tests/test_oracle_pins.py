@@ -288,6 +288,74 @@ def test_infinite_beta_is_greedy_descent():
 
 
 # --------------------------------------------------------------------------------------
+# Teacher-forced replay of recorded sweeps (Eq. 10, Sec. III-B)
+# --------------------------------------------------------------------------------------
+
+def _replay_setup():
+    inst = wl.qkp(24, 0.5, 6)
+    p = _problem(inst, penalty=0.7)
+    lam = np.array([0.45], dtype=np.float32)
+    J, hI, _ = p.ising(lam)
+    return p, lam, J, hI
+
+
+def test_replay_sweep_reproduces_the_oracles_own_trace():
+    """Replaying every recorded sweep of the oracle's own annealing runs from the recorded start
+    state gives no disagreement; changing one recorded decision (the sweep's last spin, so no
+    later decision depends on it) gives exactly one, at that spin, with the oracle's margin on
+    the side of the original bit."""
+    p, lam, J, hI = _replay_setup()
+    T, C, seed, it, bmax = 40, 3, 21, 2, 6.0
+    _, tr = oracle.anneal(J, hI, bmax, T, seed=seed, it=it, nchains=C, trace=True)
+    N = p.nprime
+    last = N - 1
+    for c in range(C):
+        for t in range(T):
+            x0 = tr[c, t - 1] if t > 0 else np.zeros(N, np.uint8)
+            b = float(oracle.beta(bmax, t, T))
+            nbad, _, _ = oracle.replay_sweep(J, hI, b, seed, it, c, t, x0, tr[c, t])
+            assert nbad == 0, (c, t)
+            if t % 7 == 3:
+                x1 = tr[c, t].copy()
+                x1[last] ^= 1
+                nbad, spins, margins = oracle.replay_sweep(J, hI, b, seed, it, c, t, x0, x1)
+                assert nbad == 1 and spins[0] == last, (c, t, nbad, spins)
+                assert (margins[0] > 0) == bool(tr[c, t, last]), (c, t, margins)
+
+
+def test_replay_sweep_margins_from_the_lagrangian():
+    """For an arbitrary recorded path x1 (random bits, so nearly every spin disagrees), the
+    replay reports exactly the spins where Eq. 10 on the current state differs from x1, and its
+    margin tanh(beta I_i) + rho there, with I_i = -(L(x|x_i=1) - L(x|x_i=0))/2 (Eq. 5, 9) and
+    rho the noise word of (seed, k, chain, t, i); the state before spin i is x1 on spins < i and
+    x0 on the rest."""
+    p, lam, J, hI = _replay_setup()
+    N = p.nprime
+    r = np.random.default_rng(8)
+    seed, it = 33, 5
+    for trial in range(6):
+        x0 = (r.random(N) < 0.5).astype(np.uint8)
+        x1 = (r.random(N) < 0.5).astype(np.uint8)
+        beta = float(np.float32(0.5 + 1.5 * trial))
+        chain, t = 3 + trial, 7 * trial
+        want_spins, want_margins = [], []
+        x = x0.copy()
+        for i in range(N):
+            hi = x.copy(); hi[i] = 1
+            lo = x.copy(); lo[i] = 0
+            I = -(p.lagrangian(hi, lam) - p.lagrangian(lo, lam)) / 2.0
+            v = math.tanh(beta * I) + oracle.pbit_noise(seed, it, chain, t, i)
+            if (v > 0) != bool(x1[i]):
+                want_spins.append(i)
+                want_margins.append(v)
+            x[i] = x1[i]
+        nbad, spins, margins = oracle.replay_sweep(J, hI, beta, seed, it, chain, t, x0, x1,
+                                                   max_out=N)
+        assert nbad == len(want_spins) and list(spins) == want_spins, trial
+        assert np.allclose(margins, want_margins, rtol=0, atol=1e-10), trial
+
+
+# --------------------------------------------------------------------------------------
 # Noise: Philox4x32-10 and rand(-1,1)
 # --------------------------------------------------------------------------------------
 
