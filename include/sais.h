@@ -189,7 +189,10 @@ typedef struct sais_solve_result {
     int64_t *feasible_count; /* [count] feasible samples seen                               */
     float *lambda_final;     /* [count*m_stride] multipliers after the last step            */
     float *lambda_trace;     /* [iters*count*m_stride] multipliers after each step          */
-    double elapsed_ms;       /* device time of the iterations (CUDA events)                 */
+    double elapsed_ms;       /* sais_solve: device time of the iterations (CUDA events);
+                                sais_solve_noalloc: host wall time of the whole call (its
+                                copies and the final synchronisation included), so the two
+                                are not like for like                                        */
     int64_t spin_updates;    /* count * chains * sweeps * N' summed over instances and k    */
 } sais_solve_result;
 
@@ -323,13 +326,17 @@ SAIS_API sais_status sais_solve(sais_problem *p, const sais_solve_params *prm,
  * list); the device scratch lives in one static array of 16 MiB that every GPU
  * loading the library holds until the process exits, and the call makes no cudaMalloc, cudaFree,
  * event or graph call, host or device.
- *  - The first call on a device looks up the array's address (with that device current); make
- *    that first call before any stream capture.
+ *  - The array's device address is looked up once per device, when a problem is created on it
+ *    (or else by the first call).  The CUDA runtime loads modules lazily by default, and this
+ *    lookup loads the library's module holding the array, so that is when the 16 MiB are
+ *    reserved: a caller that must not allocate later creates its problems beforehand, outside
+ *    any stream capture.
  *  - Sizes whose scratch would exceed 16 MiB are rejected with SAIS_EINVAL (the message gives the
  *    bytes needed); sais_solve has no such limit.
  *  - Calls share the array; calls from one process are serialised by a lock held until the
- *    call's stream has synchronised, and calls that overlapped on the GPU by other means would
- *    race.  Regions that must start at zero or at a sentinel are reset by every call.
+ *    call's stream has synchronised (on every return, once anything has been queued; every size
+ *    and variant check runs before that), and calls that overlapped on the GPU by other means
+ *    would race.  Regions that must start at zero or at a sentinel are reset by every call.
  * Synchronises `stream` before returning; elapsed_ms is host wall time of the call.
  * Errors: as sais_solve. */
 SAIS_API sais_status sais_solve_noalloc(sais_problem *p, const sais_solve_params *prm,

@@ -672,6 +672,7 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
         DeviceGuard dg(device);   // the groups' side streams belong to the problem's device
         build_groups(p);
     }
+    noalloc_prepare(device);
     *out = p;
     return SAIS_OK;
 }
@@ -784,10 +785,87 @@ sais_status check_step_rule(double eta_decay, double momentum) {
     return SAIS_OK;
 }
 
+// What one sampling launch will run, decided from the handle and the parameters alone, so that
+// every size and variant check happens before anything is queued on a stream.
+struct SamplePlan {
+    int variant = SAIS_PLAIN;   // SAIS_PLAIN, SAIS_BLOCKED or SAIS_AUTO
+    bool pair = false;          // blocked on CTA pairs (fields split over two SMs)
+    bool stream_w = false;      // blocked with W tiles streamed instead of resident
+    bool hilo = false;          // BF16 hi/lo split of W
+    int k = 16;                 // spins per block (blocked)
+    int cpb = 0;                // chains per CTA (plain)
+};
+
+sais_status plan_sample(const sais_problem *p, const sais_sample_params *prm, SamplePlan *pl) {
+    pl->variant = prm->variant;
+    if (!p->inst_chains.empty())
+        for (int j = 0; j < p->count; ++j)
+            if (p->inst_chains[j] > prm->chains)
+                return fail(SAIS_EINVAL,
+                            "instance %d has %d chains but the chains argument (the row stride) "
+                            "is %d", j, p->inst_chains[j], prm->chains);
+    if (prm->variant == SAIS_AUTO) {
+        for (const auto &g : p->groups)
+            if (g.variant == SAIS_PLAIN &&
+                plain_smem_bytes(g.max_npad_w, g.words, g.any_w, g.cpb) > (size_t)kMaxPlainSmem)
+                return fail(SAIS_EUNSUPPORTED,
+                            "plain sampler group: padded N'=%d needs %zu bytes of shared memory",
+                            g.max_npad_w, plain_smem_bytes(g.max_npad_w, g.words, g.any_w, g.cpb));
+        return SAIS_OK;
+    }
+    if (prm->variant == SAIS_PLAIN) return plain_cpb(p, prm->chains_per_cta, &pl->cpb);
+    const int k = prm->block_k ? prm->block_k : 16;
+    pl->k = k;
+    if (!p->all_w)
+        return fail(SAIS_EUNSUPPORTED,
+                    "blocked sampler: every instance needs a quadratic objective W "
+                    "(linear objectives have no dense field to update; use SAIS_PLAIN)");
+    if (k == 64) return fail(SAIS_EUNSUPPORTED, "blocked sampler: block_k = 64 not available");
+    if (p->max_m > kMaxBlockedConstraints)
+        return fail(SAIS_EUNSUPPORTED,
+                    "blocked sampler: m = %d constraints (at most %d; use SAIS_PLAIN)",
+                    p->max_m, kMaxBlockedConstraints);
+    if (p->max_npad + k > 512) {
+        // Fields split over a CTA pair (thread-block cluster of two).
+        for (int jj = 0; jj < p->count; ++jj) {
+            const HostInst &h = p->host[jj];
+            if (!pair_eligible(h.n, h.m, h.has_w))
+                return fail(SAIS_EUNSUPPORTED,
+                            "blocked sampler: N'=%d exceeds one SM's 512 TMEM columns and "
+                            "instance %d (n=%d) is outside the CTA-pair range "
+                            "(128 <= n rounded up to 64 <= 1024)",
+                            p->max_spins, jj, h.n);
+        }
+        if (k != 16)
+            return fail(SAIS_EUNSUPPORTED, "blocked sampler on CTA pairs: block_k = 16 only");
+        pl->pair = true;
+        pl->hilo = p->any_lo;
+        return SAIS_OK;
+    }
+    // W resident in shared memory when it fits and needs one BF16 term; otherwise its
+    // per-block tiles are streamed (and pair values above 256 use the hi/lo split).
+    pl->hilo = p->any_lo;
+    pl->stream_w = pl->hilo ||
+                   blocked_smem_bytes(p->max_npad, p->words, k, false, false) > kMaxSmemPerBlock;
+    if (pl->stream_w && k != 16)
+        return fail(SAIS_EUNSUPPORTED,
+                    "blocked sampler: streamed W (N'=%d%s) runs with block_k = 16 only",
+                    p->max_spins, pl->hilo ? ", pair values above 256" : "");
+    const size_t smem = blocked_smem_bytes(p->max_npad, p->words, k, pl->stream_w, pl->hilo);
+    if (smem > kMaxSmemPerBlock)
+        return fail(SAIS_EUNSUPPORTED,
+                    "blocked sampler: N'=%d needs %zu bytes of shared memory (max %zu)",
+                    p->max_spins, smem, kMaxSmemPerBlock);
+    return SAIS_OK;
+}
+
 sais_status enqueue_sample(sais_problem *p, const sais_sample_params *prm, const float *lambda,
                            const uint32_t *iter_dev, uint32_t *x, int64_t *cost, int64_t *g,
                            uint8_t *feasible, uint32_t *trace, cudaStream_t st,
                            const RunOut &run = RunOut{}) {
+    SamplePlan pl;
+    sais_status ps = plan_sample(p, prm, &pl);
+    if (ps != SAIS_OK) return ps;
     SampleArgs a{};
     a.inst = p->d_inst;
     a.count = p->count;
@@ -811,24 +889,13 @@ sais_status enqueue_sample(sais_problem *p, const sais_sample_params *prm, const
     a.run_nfeas = run.nfeas;
     a.status = p->d_status;
     a.inst_chains = p->d_inst_chains;
-    if (!p->inst_chains.empty())
-        for (int j = 0; j < p->count; ++j)
-            if (p->inst_chains[j] > prm->chains)
-                return fail(SAIS_EINVAL,
-                            "instance %d has %d chains but the chains argument (the row stride) "
-                            "is %d", j, p->inst_chains[j], prm->chains);
+    const long long polls = (long long)prm->debug_wait_polls;
     cudaError_t e;
-    if (prm->variant == SAIS_AUTO) {
-        for (const auto &g : p->groups)
-            if (g.variant == SAIS_PLAIN &&
-                plain_smem_bytes(g.max_npad_w, g.words, g.any_w, g.cpb) > (size_t)kMaxPlainSmem)
-                return fail(SAIS_EUNSUPPORTED,
-                            "plain sampler group: padded N'=%d needs %zu bytes of shared memory",
-                            g.max_npad_w, plain_smem_bytes(g.max_npad_w, g.words, g.any_w, g.cpb));
+    if (pl.variant == SAIS_AUTO) {
         sais_status s = ensure_work(p, prm->chains, st);
         if (s != SAIS_OK) return s;
         if (p->groups.size() == 1) {
-            e = launch_group(p, p->groups[0], a, (long long)prm->debug_wait_polls, st);
+            e = launch_group(p, p->groups[0], a, polls, st);
             if (e != cudaSuccess)
                 return fail(SAIS_ECUDA, "sampler launch (group): %s", cudaGetErrorString(e));
             return SAIS_OK;
@@ -841,8 +908,7 @@ sais_status enqueue_sample(sais_problem *p, const sais_sample_params *prm, const
             const size_t si = g.pair ? 0 : gi + 1;
             if (!used[si]) e = cudaStreamWaitEvent(p->side[si], p->fork, 0);
             used[si] = 1;
-            if (e == cudaSuccess)
-                e = launch_group(p, g, a, (long long)prm->debug_wait_polls, p->side[si]);
+            if (e == cudaSuccess) e = launch_group(p, g, a, polls, p->side[si]);
         }
         for (size_t si = 0; e == cudaSuccess && si < p->side.size(); ++si) {
             if (!used[si]) continue;
@@ -853,57 +919,13 @@ sais_status enqueue_sample(sais_problem *p, const sais_sample_params *prm, const
             return fail(SAIS_ECUDA, "sampler launch (groups): %s", cudaGetErrorString(e));
         return SAIS_OK;
     }
-    if (prm->variant == SAIS_BLOCKED) {
-        const int k = prm->block_k ? prm->block_k : 16;
-        if (!p->all_w)
-            return fail(SAIS_EUNSUPPORTED,
-                        "blocked sampler: every instance needs a quadratic objective W "
-                        "(linear objectives have no dense field to update; use SAIS_PLAIN)");
-        if (k == 64) return fail(SAIS_EUNSUPPORTED, "blocked sampler: block_k = 64 not available");
-        if (p->max_m > kMaxBlockedConstraints)
-            return fail(SAIS_EUNSUPPORTED,
-                        "blocked sampler: m = %d constraints (at most %d; use SAIS_PLAIN)",
-                        p->max_m, kMaxBlockedConstraints);
-        if (p->max_npad + k > 512) {
-            // Fields split over a CTA pair (thread-block cluster of two).
-            for (int jj = 0; jj < p->count; ++jj) {
-                const HostInst &h = p->host[jj];
-                if (!pair_eligible(h.n, h.m, h.has_w))
-                    return fail(SAIS_EUNSUPPORTED,
-                                "blocked sampler: N'=%d exceeds one SM's 512 TMEM columns and "
-                                "instance %d (n=%d) is outside the CTA-pair range "
-                                "(128 <= n rounded up to 64 <= 1024)",
-                                p->max_spins, jj, h.n);
-            }
-            if (k != 16)
-                return fail(SAIS_EUNSUPPORTED, "blocked sampler on CTA pairs: block_k = 16 only");
-            e = launch_pair_sampler(a, p->max_m, p->max_n, p->words, p->any_lo, p->d_status,
-                                    (long long)prm->debug_wait_polls, st);
-            if (e != cudaSuccess) return fail(SAIS_ECUDA, "sampler launch: %s", cudaGetErrorString(e));
-            return SAIS_OK;
-        }
-        // W resident in shared memory when it fits and needs one BF16 term; otherwise its
-        // per-block tiles are streamed (and pair values above 256 use the hi/lo split).
-        const bool hilo = p->any_lo;
-        bool stream_w = hilo ||
-                        blocked_smem_bytes(p->max_npad, p->words, k, false, false) > kMaxSmemPerBlock;
-        if (stream_w && k != 16)
-            return fail(SAIS_EUNSUPPORTED,
-                        "blocked sampler: streamed W (N'=%d%s) runs with block_k = 16 only",
-                        p->max_spins, hilo ? ", pair values above 256" : "");
-        const size_t smem = blocked_smem_bytes(p->max_npad, p->words, k, stream_w, hilo);
-        if (smem > kMaxSmemPerBlock)
-            return fail(SAIS_EUNSUPPORTED,
-                        "blocked sampler: N'=%d needs %zu bytes of shared memory (max %zu)",
-                        p->max_spins, smem, kMaxSmemPerBlock);
-        e = launch_blocked_sampler(a, p->max_m, p->max_npad, p->words, k, stream_w, hilo,
-                                   p->d_status, (long long)prm->debug_wait_polls, st);
-    } else {
-        int cpb = 0;
-        sais_status s = plain_cpb(p, prm->chains_per_cta, &cpb);
-        if (s != SAIS_OK) return s;
-        e = launch_plain_sampler(a, p->max_m, p->max_npad_w, p->words, cpb, st);
-    }
+    if (pl.variant == SAIS_BLOCKED && pl.pair)
+        e = launch_pair_sampler(a, p->max_m, p->max_n, p->words, pl.hilo, p->d_status, polls, st);
+    else if (pl.variant == SAIS_BLOCKED)
+        e = launch_blocked_sampler(a, p->max_m, p->max_npad, p->words, pl.k, pl.stream_w, pl.hilo,
+                                   p->d_status, polls, st);
+    else
+        e = launch_plain_sampler(a, p->max_m, p->max_npad_w, p->words, pl.cpb, st);
     if (e != cudaSuccess) return fail(SAIS_ECUDA, "sampler launch: %s", cudaGetErrorString(e));
     return SAIS_OK;
 }
@@ -1463,7 +1485,10 @@ sais_status enqueue_sample_internal(sais_problem *p, const sais_sample_params *p
 }
 
 sais_status check_sample_params_internal(const sais_problem *p, const sais_sample_params *prm) {
-    return check_sample_params(p, prm);
+    sais_status s = check_sample_params(p, prm);
+    if (s != SAIS_OK) return s;
+    SamplePlan pl;
+    return plan_sample(p, prm, &pl);
 }
 
 sais_status check_step_rule_internal(double eta_decay, double momentum) {

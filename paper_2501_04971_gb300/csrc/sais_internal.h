@@ -154,7 +154,13 @@ sais_status enqueue_sample_internal(sais_problem *p, const sais_sample_params *p
                                    const float *lambda, const uint32_t *iter_dev, uint32_t *x,
                                    int64_t *cost, int64_t *g, uint8_t *feasible,
                                    uint32_t *run_x, int64_t *run_cost, cudaStream_t stream);
+// The argument checks of sais_sample plus every size and variant check of the launch it would
+// make (nothing is queued).
 sais_status check_sample_params_internal(const sais_problem *p, const sais_sample_params *prm);
+// Looks up the device address of sais_solve_noalloc's static scratch on the current device
+// (loading the module that holds it, if the CUDA runtime has not yet).  Called when a problem is
+// created, so that the first sais_solve_noalloc on that device finds the address ready.
+void noalloc_prepare(int device);
 sais_status check_step_rule_internal(double eta_decay, double momentum);
 sais_status set_error(sais_status s, const char *fmt, ...);
 // Inference launch of the warm-start network: lambda[dst[r]] = max(0, y(feat row r)).

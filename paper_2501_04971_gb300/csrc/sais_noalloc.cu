@@ -9,12 +9,16 @@
 // cudaMalloc, cudaFree, event, graph or other allocating routine, host or device.
 //
 // Use and limits:
-//  * The first call on a device looks up the array's device address (cudaGetSymbolAddress, with
-//    that device current); make that first call before any stream capture.
+//  * The array's device address is looked up (cudaGetSymbolAddress, with the device current)
+//    once per device: when a problem is created on it, or else by the first call.  With the CUDA
+//    runtime's lazy module loading, that lookup is what loads this module and so reserves the
+//    array; a caller that must not allocate later should create its problems (or make a first
+//    call) beforehand, and outside any stream capture.
 //  * A call whose scratch would exceed kNoAllocScratchBytes is rejected with SAIS_EINVAL.
 //  * All calls share the array.  Calls from this process are serialised by a lock held until the
-//    call has synchronised its stream, so two calls never overlap; work that another caller
-//    enqueues against the array by other means would race with it.
+//    call has synchronised its stream, on every return path once anything has been queued, so two
+//    calls never overlap; work that another caller enqueues against the array by other means
+//    would race with it.  Every size and variant check runs before anything is queued.
 //  * Every region that must start at zero or at a sentinel is set at the start of each call; the
 //    rest keeps the previous call's contents and is overwritten before it is read.
 #include <chrono>
@@ -46,7 +50,32 @@ __global__ void init_best_kernel(int64_t *best_cost, int32_t *best_iter, int32_t
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
+// Address of the scratch on the current device, looked up once (caller holds the lock).
+cudaError_t scratch_address(int device, unsigned char **out) {
+    if (!g_scratch_addr[device]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        if (!ptr) return cudaErrorInvalidSymbol;
+        g_scratch_addr[device] = ptr;
+    }
+    *out = static_cast<unsigned char *>(g_scratch_addr[device]);
+    return cudaSuccess;
+}
+
 }  // namespace
+
+void noalloc_prepare(int device) {
+    if (device < 0 || device >= kMaxDevices) return;
+    std::lock_guard<std::mutex> lock(g_noalloc_lock);
+    int prev = 0;
+    if (cudaGetDevice(&prev) != cudaSuccess) return;
+    if (cudaSetDevice(device) != cudaSuccess) return;
+    unsigned char *ptr = nullptr;
+    if (scratch_address(device, &ptr) != cudaSuccess) cudaGetLastError();   // retried at the call
+    cudaSetDevice(prev);
+}
+
 }  // namespace sais
 
 using namespace sais;
@@ -124,15 +153,13 @@ extern "C" sais_status sais_solve_noalloc(sais_problem *p, const sais_solve_para
         int d;
         ~Restore() { cudaSetDevice(d); }
     } restore{prev};
-    if (!g_scratch_addr[v.device]) {
-        void *ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess || !ptr)
+    unsigned char *scr = nullptr;
+    {
+        cudaError_t e = scratch_address(v.device, &scr);
+        if (e != cudaSuccess)
             return set_error(SAIS_ECUDA, "cudaGetSymbolAddress of the static scratch: %s",
                              cudaGetErrorString(e));
-        g_scratch_addr[v.device] = ptr;
     }
-    unsigned char *scr = static_cast<unsigned char *>(g_scratch_addr[v.device]);
     float *d_lam = reinterpret_cast<float *>(scr + offs[0]);
     uint32_t *d_x = reinterpret_cast<uint32_t *>(scr + offs[1]);
     int64_t *d_cost = reinterpret_cast<int64_t *>(scr + offs[2]);
@@ -149,6 +176,15 @@ extern "C" sais_status sais_solve_noalloc(sais_problem *p, const sais_solve_para
     int64_t *d_rc = rb ? reinterpret_cast<int64_t *>(scr + offs[13]) : nullptr;
     double *d_avg = avg_on ? reinterpret_cast<double *>(scr + offs[14]) : nullptr;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // Once anything is queued, every return synchronises the stream before the lock is released
+    // (this guard is destroyed before `lock`), so a failing call leaves no work on the array.
+    struct SyncOnReturn {
+        cudaStream_t s;
+        bool armed;
+        ~SyncOnReturn() {
+            if (armed) cudaStreamSynchronize(s);
+        }
+    } sync_guard{s, false};
 
 #define NOALLOC_CUDA(expr)                                                              \
     do {                                                                                \
@@ -158,6 +194,7 @@ extern "C" sais_status sais_solve_noalloc(sais_problem *p, const sais_solve_para
     } while (0)
 
     const auto t0 = std::chrono::steady_clock::now();
+    sync_guard.armed = true;
     // Regions read before they are written: multipliers, best-so-far state, counters, trace.
     NOALLOC_CUDA(cudaMemsetAsync(d_lam, 0, sizes[0], s));
     NOALLOC_CUDA(cudaMemsetAsync(d_bx, 0, sizes[6], s));
@@ -212,11 +249,11 @@ extern "C" sais_status sais_solve_noalloc(sais_problem *p, const sais_solve_para
     if (res->feasible_count) NOALLOC_CUDA(cudaMemcpyAsync(res->feasible_count, d_fc, sizes[9], cudaMemcpyDeviceToHost, s));
     if (res->lambda_final) NOALLOC_CUDA(cudaMemcpyAsync(res->lambda_final, d_lam, sizes[0], cudaMemcpyDeviceToHost, s));
     if (res->lambda_trace) NOALLOC_CUDA(cudaMemcpyAsync(res->lambda_trace, d_tr, sizes[10], cudaMemcpyDeviceToHost, s));
-    NOALLOC_CUDA(cudaStreamSynchronize(s));
     int32_t status = 0;
-    NOALLOC_CUDA(cudaMemcpy(&status, v.d_status, 4, cudaMemcpyDeviceToHost));
+    NOALLOC_CUDA(cudaMemcpyAsync(&status, v.d_status, 4, cudaMemcpyDeviceToHost, s));
+    NOALLOC_CUDA(cudaStreamSynchronize(s));
     if (status != SAIS_OK) {
-        NOALLOC_CUDA(cudaMemset(v.d_status, 0, 4));
+        NOALLOC_CUDA(cudaMemsetAsync(v.d_status, 0, 4, s));
         return set_error((sais_status)status, "a sampler kernel reported: %s",
                          sais_status_string((sais_status)status));
     }

@@ -29,7 +29,7 @@ def _built():
 
 
 def _noalloc(prob, iters, chains, sweeps, beta_max, eta, seed, variant="plain", lambda0=None,
-             run_best=False, eta_decay=0.0, eta_sqrt=False, momentum=0.0):
+             run_best=False, eta_decay=0.0, eta_sqrt=False, momentum=0.0, stream=None):
     """Call sais_solve_noalloc through the C-ABI with host result arrays."""
     prm = sais.sais_solve_params()
     prm.iters, prm.chains, prm.sweeps, prm.beta_max = iters, chains, sweeps, beta_max
@@ -50,7 +50,8 @@ def _noalloc(prob, iters, chains, sweeps, beta_max, eta, seed, variant="plain", 
     res = sais.sais_solve_result()
     for k, v in out.items():
         setattr(res, k, v.ctypes.data_as(ctypes.c_void_p))
-    st = sais.lib().sais_solve_noalloc(prob.handle, ctypes.byref(prm), ctypes.byref(res), None)
+    sp = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    st = sais.lib().sais_solve_noalloc(prob.handle, ctypes.byref(prm), ctypes.byref(res), sp)
     return st, out
 
 
@@ -105,4 +106,38 @@ def test_noalloc_rejects_auto_variant():
     prob = sais.Problem([wl.qkp(60, 0.5, 6)])
     st, _ = _noalloc(prob, 2, 32, 10, 10.0, 20.0, 1, variant="auto")
     assert st == sais.SAIS_EINVAL and "SAIS_AUTO" in sais.sais_last_error()
+    prob.close()
+
+
+def test_noalloc_rejects_before_queueing_then_runs_on_another_stream():
+    """A call the sampler cannot run (the blocked sampler on an objective without W) is refused
+    before anything reaches the GPU; a valid call on another stream right after it still equals
+    sais_solve."""
+    mkp = sais.Problem([wl.mkp(40, 3, 2)])
+    st, _ = _noalloc(mkp, 2, 32, 10, 10.0, 20.0, 1, variant="blocked")
+    assert st == sais.SAIS_EUNSUPPORTED, sais.sais_last_error()
+    mkp.close()
+    prob = sais.Problem([wl.qkp(80, 0.5, 12)])
+    want = prob.solve(4, 64, 60, 10.0, 20.0, 9, variant="plain")
+    side = torch.cuda.Stream()
+    st, got = _noalloc(prob, 4, 64, 60, 10.0, 20.0, 9, variant="plain", stream=side)
+    assert st == sais.SAIS_OK, sais.sais_last_error()
+    for k in KEYS:
+        assert np.array_equal(got[k], want[k]), k
+    prob.close()
+
+
+def test_noalloc_second_call_leaves_free_memory_unchanged():
+    """The defining property, checked coarsely: after a first call (which may load the module
+    holding the static array), a second call changes the device's free memory by nothing.
+    cudaMemGetInfo counts whole allocations, so this sees any cudaMalloc the call might make."""
+    prob = sais.Problem([wl.qkp(100, 0.5, 13), wl.qkp(70, 0.25, 14)])
+    st, _ = _noalloc(prob, 3, 64, 50, 10.0, 20.0, 5, variant="blocked")
+    assert st == sais.SAIS_OK, sais.sais_last_error()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    st, _ = _noalloc(prob, 3, 64, 50, 10.0, 20.0, 5, variant="blocked")
+    assert st == sais.SAIS_OK, sais.sais_last_error()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
     prob.close()
