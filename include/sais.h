@@ -357,6 +357,29 @@ SAIS_API sais_status sais_set_instance_chains(sais_problem *p, const int32_t *co
 SAIS_API sais_status sais_autotune(sais_problem *p, int32_t chains, int32_t sweeps,
                                    sais_tuning *out, void *stream);
 
+/* The launch sais_sample would make for these parameters, decided from the handle alone
+ * (no GPU work): which sampler kernel, its block size and CTA shape.  Errors: those
+ * sais_sample reports before launching (SAIS_EINVAL, SAIS_EUNSUPPORTED).  No counterpart in the
+ * paper: introspection of the samplers of Sec. III-B as this library runs them. */
+typedef enum sais_kernel {
+    SAIS_KERNEL_PLAIN = 0,          /* per-spin sampler                                       */
+    SAIS_KERNEL_RANKK_RESIDENT = 1, /* blocked, rank-k field update, W resident in SMEM       */
+    SAIS_KERNEL_RANKK_STREAMED = 2, /* blocked, rank-k field update, W tiles streamed          */
+    SAIS_KERNEL_BLOCK_FIELD = 3,    /* blocked, each block's fields from a GEMM over the states */
+    SAIS_KERNEL_CTA_PAIR = 4,       /* blocked, fields split over a cluster of two CTAs        */
+    SAIS_KERNEL_GROUPS = 5          /* SAIS_AUTO: one launch per group (see sais_autotune)     */
+} sais_kernel;
+
+typedef struct sais_plan {
+    int32_t kernel;          /* sais_kernel                                                  */
+    int32_t block_k;         /* spins per block (blocked kernels), else 0                    */
+    int32_t chains_per_cta;  /* chains per CTA (per cluster for the CTA pair)                */
+    int32_t hilo;            /* 1 when W is applied as two BF16 terms (pair values > 256)    */
+} sais_plan;
+
+SAIS_API sais_status sais_sample_plan(const sais_problem *p, const sais_sample_params *prm,
+                                      sais_plan *out);
+
 /* Wait for the work queued on `stream` and report device-side failures of this problem's
  * kernels since the last call: SAIS_ETIMEOUT if a bounded wait inside a kernel gave up (the
  * kernel then stopped early and its outputs are not valid).  Resets the device status word.

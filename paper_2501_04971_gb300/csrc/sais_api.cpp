@@ -257,6 +257,8 @@ float bf16_value(uint16_t b) {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+int32_t n16_of(int32_t n) { return (n + 15) / 16 * 16; }
+
 struct DeviceGuard {
     int prev = 0;
     explicit DeviceGuard(int dev) {
@@ -273,6 +275,7 @@ struct sais_problem {
     int count = 0;
     int max_spins = 0, max_npad = 0, max_npad_w = 0, words = 0, m_stride = 1, max_m = 0;
     int max_n = 0;
+    int max_n16 = 0;              // max over quadratic instances of n rounded up to 16
     bool any_w = false;
     std::vector<HostInst> host;   // host copies (W pointer cleared after creation)
     bool any_lo = false;          // some instance needs the BF16 hi/lo split
@@ -292,9 +295,10 @@ struct sais_problem {
         int variant = SAIS_PLAIN;
         bool stream_w = false, hilo = false;
         int block_k = 16, cpb = 32;
-        int max_m = 0, max_npad = 0, max_npad_w = 0, words = 0, max_n = 0;
+        int max_m = 0, max_npad = 0, max_npad_w = 0, words = 0, max_n = 0, max_n16 = 0;
         bool any_w = false;
         bool blocked_ok = false;   // every member fits the blocked sampler
+        bool field = false;        // blocked sampler with per-block field GEMMs (one CTA)
         bool pair = false;         // blocked sampler on CTA pairs (items beyond one SM's TMEM)
         std::vector<int> members;
         size_t work_off = 0, nwork = 0;
@@ -312,24 +316,48 @@ struct sais_problem {
     size_t work_cap = 0;                // capacity in (instance, group) pairs
     int work_chains = -1;               // `chains` the work list was built for
     bool work_valid = false;
+    int32_t *h_work = nullptr;          // pinned staging copy of the work list (own allocation)
+    cudaEvent_t work_copied = nullptr;  // the last upload from h_work has completed
 };
 
 namespace {
 
-// SAIS_AUTO grouping (see struct sais_problem).  Keys: 1 blocked with W resident, 2 streamed,
-// 3 streamed hi/lo, 4 CTA-pair blocked, 5 CTA-pair hi/lo (6, 7: the same with n > 992, whose
-// pair kernels take the A operand from shared memory); plain instances split by whether they
-// have W and by padded N' (bucket of 128 spins), so each plain group sizes its shared memory for
-// its own largest member.
+// The blocked samplers, by instance size (N'_pad spins, n items):
+//  * rank-k update with every field resident in TMEM (sais_blocked_kernel.cuh), one CTA per SM:
+//    N'_pad + K <= 512; two MMAs per block of K = 16 spins, the fewest tensor-core
+//    instructions per spin;
+//  * block fields from a GEMM over the states (sais_field_kernel.cuh), one CTA per SM up to
+//    n = 992 items: for instances beyond the first, and for K = 32 streamed or hi/lo and K = 64;
+//  * a CTA pair with the fields split over two SMs (sais_pair.cu) beyond that (n <= 1024).
+bool field_fits(int n16, int words, int m, bool has_w, int k, bool hilo) {
+    return has_w && m <= kMaxBlockedConstraints && (k == 16 || m <= 2) &&
+           field_tmem_cols(n16, k) <= 512 &&
+           field_smem_bytes(n16, words, k, hilo) <= kMaxSmemPerBlock;
+}
+
+// The block size of the block-field sampler when the caller leaves it open: 32 (half the MMA
+// instructions per spin of K = 16, measured faster at n = 500 and 900) where m <= 2 allows it.
+int field_default_k(int m) { return m <= 2 ? 32 : 16; }
+
+// SAIS_AUTO grouping (see struct sais_problem).  Keys: 1 rank-k blocked with W resident, 2
+// streamed, 3 streamed hi/lo; 4 CTA-pair blocked, 5 CTA-pair hi/lo (6, 7: the same with n >
+// 992, whose pair kernels take the A operand from shared memory); 10 block-field, 11 block-field
+// hi/lo; plain instances split by whether they have W and by padded N' (bucket of 128 spins), so
+// each plain group sizes its shared memory for its own largest member.
+
 void build_groups(sais_problem *p) {
     p->groups.clear();
     auto key_of = [&](const HostInst &h) -> int {
         const bool eligible = h.has_w && h.m <= kMaxBlockedConstraints && h.npad + 16 <= 512;
-        if (!eligible && pair_eligible(h.n, h.m, h.has_w))
+        if (eligible) {
+            if (h.lo_own) return 3;
+            return blocked_smem_bytes(h.npad, h.words, 16, false, false) > kMaxSmemPerBlock ? 2 : 1;
+        }
+        if (field_fits(n16_of(h.n), h.words, h.m, h.has_w, 16, h.lo_own))
+            return h.lo_own ? 11 : 10;
+        if (pair_eligible(h.n, h.m, h.has_w))
             return (h.lo_own ? 5 : 4) + (pair_a_tmem(h.n) ? 0 : 2);
-        if (!eligible) return 100 + (h.has_w ? 1000 : 0) + (h.npad + 127) / 128;
-        if (h.lo_own) return 3;
-        return blocked_smem_bytes(h.npad, h.words, 16, false, false) > kMaxSmemPerBlock ? 2 : 1;
+        return 100 + (h.has_w ? 1000 : 0) + (h.npad + 127) / 128;
     };
     std::vector<int> keys;
     for (int j = 0; j < p->count; ++j) keys.push_back(key_of(p->host[j]));
@@ -351,6 +379,7 @@ void build_groups(sais_problem *p) {
             g.max_m = std::max(g.max_m, h.m);
             g.max_npad = std::max(g.max_npad, h.npad);
             g.max_n = std::max(g.max_n, h.n);
+            g.max_n16 = std::max(g.max_n16, n16_of(h.n));
             if (h.has_w) g.max_npad_w = std::max(g.max_npad_w, h.npad);
             g.words = std::max(g.words, h.words);
             g.any_w = g.any_w || h.has_w;
@@ -358,8 +387,10 @@ void build_groups(sais_problem *p) {
         g.variant = key >= 100 ? SAIS_PLAIN : SAIS_BLOCKED;
         g.blocked_ok = key < 100;
         g.pair = key >= 4 && key <= 7;
-        g.stream_w = key >= 2 && key <= 7;
-        g.hilo = key == 3 || key == 5 || key == 7;
+        g.field = key == 10 || key == 11;
+        g.stream_w = key >= 2 && key <= 11;
+        g.hilo = key == 3 || key == 5 || key == 7 || key == 11;
+        if (g.field) g.block_k = field_default_k(g.max_m);
         auto cost = [&](int j) {
             const HostInst &h = p->host[j];
             return (double)h.nprime * (h.has_w ? (double)h.npad : (double)std::max(1, h.m));
@@ -384,7 +415,11 @@ void build_groups(sais_problem *p) {
 int group_cta(const sais_problem::Group &g) { return g.variant == SAIS_BLOCKED ? 128 : g.cpb; }
 
 // Device work list for `chains` (the uniform count, or the stride when per-instance counts are
-// set).  Built on the host and copied; (re)allocated only outside stream capture.
+// set).  Built on the host and uploaded asynchronously on the caller's stream from a pinned
+// staging buffer, so the sampling path does not block the host: launches queued before it on
+// that stream (every group joins back into it) still read the old list, later ones the new one.
+// The host waits only when the staging buffer's previous upload is still in flight, or when
+// the list outgrows its allocation (cudaFree synchronises the device).  Refused during capture.
 sais_status ensure_work(sais_problem *p, int chains, cudaStream_t st) {
     if (p->work_valid && p->work_chains == chains) return SAIS_OK;
     std::vector<int32_t> w;
@@ -405,18 +440,29 @@ sais_status ensure_work(sais_problem *p, int chains, cudaStream_t st) {
     if (cs != cudaStreamCaptureStatusNone)
         return fail(SAIS_EINVAL, "SAIS_AUTO: prepare the launch (one call with these chains) "
                                  "before capturing a graph");
-    // Launches already queued on the stream may still read the old list.
-    cudaError_t e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return fail(SAIS_ECUDA, "work list: %s", cudaGetErrorString(e));
+    cudaError_t e = cudaSuccess;
+    if (!p->work_copied) {
+        e = cudaEventCreateWithFlags(&p->work_copied, cudaEventDisableTiming);
+        if (e != cudaSuccess) return fail(SAIS_ECUDA, "work list event: %s", cudaGetErrorString(e));
+    }
     if (w.size() / 2 > p->work_cap) {
-        if (p->d_work) cudaFree(p->d_work);
+        if (p->d_work) cudaFree(p->d_work);   // synchronises: queued launches may read it
+        if (p->h_work) cudaFreeHost(p->h_work);
         p->d_work = nullptr;
+        p->h_work = nullptr;
         p->work_cap = 0;
         e = cudaMalloc(&p->d_work, w.size() * 4);
         if (e != cudaSuccess) return fail(SAIS_ENOMEM, "work list: %s", cudaGetErrorString(e));
+        e = cudaMallocHost(&p->h_work, w.size() * 4);
+        if (e != cudaSuccess) return fail(SAIS_ENOMEM, "work list staging: %s", cudaGetErrorString(e));
         p->work_cap = w.size() / 2;
+    } else {
+        e = cudaEventSynchronize(p->work_copied);   // the staging buffer's last upload is done
+        if (e != cudaSuccess) return fail(SAIS_ECUDA, "work list: %s", cudaGetErrorString(e));
     }
-    e = cudaMemcpy(p->d_work, w.data(), w.size() * 4, cudaMemcpyHostToDevice);
+    std::memcpy(p->h_work, w.data(), w.size() * 4);
+    e = cudaMemcpyAsync(p->d_work, p->h_work, w.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(p->work_copied, st);
     if (e != cudaSuccess) return fail(SAIS_ECUDA, "work list copy: %s", cudaGetErrorString(e));
     p->work_chains = chains;
     p->work_valid = true;
@@ -431,6 +477,9 @@ cudaError_t launch_group(const sais_problem *p, const sais_problem::Group &g, co
     ga.nwork = (int32_t)g.nwork;
     if (g.variant == SAIS_BLOCKED && g.pair)
         return launch_pair_sampler(ga, g.max_m, g.max_n, g.words, g.hilo, p->d_status, polls, st);
+    if (g.variant == SAIS_BLOCKED && g.field)
+        return launch_field_sampler(ga, g.max_m, g.max_n16, g.words, g.block_k, g.hilo,
+                                    p->d_status, polls, st);
     if (g.variant == SAIS_BLOCKED)
         return launch_blocked_sampler(ga, g.max_m, g.max_npad, g.words, g.block_k, g.stream_w,
                                       g.hilo, p->d_status, polls, st);
@@ -475,6 +524,7 @@ sais_status sais_describe(const sais_problem_desc *desc, sais_problem_scalars *o
 
 sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int32_t device,
                               sais_problem **out) {
+    NvtxRange nvtx_range("sais_create_batch");
     if (!out) return fail(SAIS_EINVAL, "out is NULL");
     *out = nullptr;
     if (!descs || count < 1) return fail(SAIS_EINVAL, "need count >= 1 descriptors");
@@ -505,7 +555,10 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
         p->max_spins = std::max(p->max_spins, h.nprime);
         p->max_npad = std::max(p->max_npad, h.npad);
         p->max_n = std::max(p->max_n, h.n);
-        if (h.has_w) p->max_npad_w = std::max(p->max_npad_w, h.npad);
+        if (h.has_w) {
+            p->max_npad_w = std::max(p->max_npad_w, h.npad);
+            p->max_n16 = std::max(p->max_n16, n16_of(h.n));
+        }
         p->max_m = std::max(p->max_m, h.m);
         p->any_w = p->any_w || h.has_w;
         p->all_w = p->all_w && h.has_w;
@@ -517,7 +570,7 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
     // Pool layout: [InstDev x count] then per instance W, Wbf(, Wbf_lo), hF, acol, D, asum, b,
     // slack_off, each 256-byte aligned.
     struct Off {
-        size_t W, Wbf, Wlo, Wd, hF, acol, D, asum, spinc, b, so;
+        size_t W, Wbf, Wlo, Wd, Wg, Wglo, Wd32, Wd64, hF, acol, D, asum, spinc, b, so;
     };
     int32_t feat_rows = 0;
     for (const HostInst &h : p->host) feat_rows += h.m;
@@ -534,17 +587,26 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
         const HostInst &h = p->host[j];
         const size_t nn = (size_t)h.npad * h.npad;
         Off &o = off[j];
-        o.W = o.Wbf = o.Wlo = o.Wd = SIZE_MAX;
+        o.W = o.Wbf = o.Wlo = o.Wd = o.Wg = o.Wglo = o.Wd32 = o.Wd64 = SIZE_MAX;
         if (h.has_w) {
+            const size_t ng = (size_t)h.npad * n16_of(h.n);
             o.W = cur;
             cur = align_up(cur + nn * 2, 256);
             o.Wd = cur;
             cur = align_up(cur + (size_t)h.npad * 16 * 4, 256);
+            o.Wd32 = cur;
+            cur = align_up(cur + (size_t)h.npad * 32 * 4, 256);
+            o.Wd64 = cur;
+            cur = align_up(cur + (size_t)h.npad * 64 * 4, 256);
             o.Wbf = cur;
             cur = align_up(cur + nn * 2, 256);
+            o.Wg = cur;
+            cur = align_up(cur + ng * 2, 256);
             if (h.need_lo) {
                 o.Wlo = cur;
                 cur = align_up(cur + nn * 2, 256);
+                o.Wglo = cur;
+                cur = align_up(cur + ng * 2, 256);
             }
         }
         o.hF = cur;
@@ -594,6 +656,7 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
         r.nprime = h.nprime;
         r.npad = h.npad;
         r.words = h.words;
+        r.n16 = n16_of(h.n);
         r.has_w = h.has_w ? 1 : 0;
         r.sigma_f = h.sf;
         r.sigma_g = h.sg;
@@ -615,12 +678,34 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
                     Wb[e] = hi;
                     if (Wl) Wl[e] = bf16_bits((float)w - bf16_value(hi));
                 }
-            float *Wd = reinterpret_cast<float *>(stage.data() + o.Wd);
+            // Block-field image: element (i, jj) at ((i/8)(n16/8) + jj/8) 64 + (i%8) 8 + jj%8.
+            const int32_t n16 = n16_of(h.n);
+            uint16_t *Wg = reinterpret_cast<uint16_t *>(stage.data() + o.Wg);
+            uint16_t *Wgl = h.need_lo ? reinterpret_cast<uint16_t *>(stage.data() + o.Wglo) : nullptr;
             for (int32_t i = 0; i < h.n; ++i)
-                for (int32_t jj = (i / 16) * 16; jj < std::min(h.n, (i / 16) * 16 + 16); ++jj)
-                    Wd[(size_t)(i / 16) * 256 + (i % 16) * 16 + (jj % 16)] =
-                        (float)h.W[(size_t)i * h.n + jj];
+                for (int32_t jj = 0; jj < h.n; ++jj) {
+                    const int32_t w = h.W[(size_t)i * h.n + jj];
+                    const size_t e = ((size_t)(i >> 3) * (n16 >> 3) + (jj >> 3)) * 64 +
+                                     (size_t)(i & 7) * 8 + (jj & 7);
+                    const uint16_t hi = bf16_bits((float)w);
+                    Wg[e] = hi;
+                    if (Wgl) Wgl[e] = bf16_bits((float)w - bf16_value(hi));
+                }
+            // FP32 diagonal blocks of W for block sizes 16, 32 and 64 (row-major per block).
+            const size_t doff[3] = {o.Wd, o.Wd32, o.Wd64};
+            for (int q = 0; q < 3; ++q) {
+                const int32_t kb = 16 << q;
+                float *Wd = reinterpret_cast<float *>(stage.data() + doff[q]);
+                for (int32_t i = 0; i < h.n; ++i)
+                    for (int32_t jj = (i / kb) * kb; jj < std::min(h.n, (i / kb) * kb + kb); ++jj)
+                        Wd[(size_t)(i / kb) * kb * kb + (size_t)(i % kb) * kb + (jj % kb)] =
+                            (float)h.W[(size_t)i * h.n + jj];
+            }
             r.Wdiag = reinterpret_cast<const float *>(base + o.Wd);
+            r.Wd32 = reinterpret_cast<const float *>(base + o.Wd32);
+            r.Wd64 = reinterpret_cast<const float *>(base + o.Wd64);
+            r.Wg = reinterpret_cast<const uint16_t *>(base + o.Wg);
+            r.Wg_lo = h.need_lo ? reinterpret_cast<const uint16_t *>(base + o.Wglo) : nullptr;
             r.W = reinterpret_cast<const int16_t *>(base + o.W);
             r.Wbf = reinterpret_cast<const uint16_t *>(base + o.Wbf);
             r.Wbf_lo = h.need_lo ? reinterpret_cast<const uint16_t *>(base + o.Wlo) : nullptr;
@@ -690,6 +775,8 @@ sais_status sais_destroy_problem(sais_problem *p) {
     cudaError_t e = cudaDeviceSynchronize();
     if (p->pool) cudaFree(p->pool);
     if (p->d_work) cudaFree(p->d_work);
+    if (p->h_work) cudaFreeHost(p->h_work);
+    if (p->work_copied) cudaEventDestroy(p->work_copied);
     if (p->d_inst_chains) cudaFree(p->d_inst_chains);
     for (cudaStream_t x : p->side)
         if (x) cudaStreamDestroy(x);
@@ -790,7 +877,8 @@ sais_status check_step_rule(double eta_decay, double momentum) {
 struct SamplePlan {
     int variant = SAIS_PLAIN;   // SAIS_PLAIN, SAIS_BLOCKED or SAIS_AUTO
     bool pair = false;          // blocked on CTA pairs (fields split over two SMs)
-    bool stream_w = false;      // blocked with W tiles streamed instead of resident
+    bool field = false;         // blocked with per-block field GEMMs on one CTA
+    bool stream_w = false;      // rank-k blocked with W tiles streamed instead of resident
     bool hilo = false;          // BF16 hi/lo split of W
     int k = 16;                 // spins per block (blocked)
     int cpb = 0;                // chains per CTA (plain)
@@ -820,42 +908,49 @@ sais_status plan_sample(const sais_problem *p, const sais_sample_params *prm, Sa
         return fail(SAIS_EUNSUPPORTED,
                     "blocked sampler: every instance needs a quadratic objective W "
                     "(linear objectives have no dense field to update; use SAIS_PLAIN)");
-    if (k == 64) return fail(SAIS_EUNSUPPORTED, "blocked sampler: block_k = 64 not available");
     if (p->max_m > kMaxBlockedConstraints)
         return fail(SAIS_EUNSUPPORTED,
                     "blocked sampler: m = %d constraints (at most %d; use SAIS_PLAIN)",
                     p->max_m, kMaxBlockedConstraints);
-    if (p->max_npad + k > 512) {
-        // Fields split over a CTA pair (thread-block cluster of two).
-        for (int jj = 0; jj < p->count; ++jj) {
-            const HostInst &h = p->host[jj];
-            if (!pair_eligible(h.n, h.m, h.has_w))
-                return fail(SAIS_EUNSUPPORTED,
-                            "blocked sampler: N'=%d exceeds one SM's 512 TMEM columns and "
-                            "instance %d (n=%d) is outside the CTA-pair range "
-                            "(128 <= n rounded up to 64 <= 1024)",
-                            p->max_spins, jj, h.n);
-        }
-        if (k != 16)
-            return fail(SAIS_EUNSUPPORTED, "blocked sampler on CTA pairs: block_k = 16 only");
-        pl->pair = true;
-        pl->hilo = p->any_lo;
-        return SAIS_OK;
-    }
-    // W resident in shared memory when it fits and needs one BF16 term; otherwise its
-    // per-block tiles are streamed (and pair values above 256 use the hi/lo split).
     pl->hilo = p->any_lo;
-    pl->stream_w = pl->hilo ||
-                   blocked_smem_bytes(p->max_npad, p->words, k, false, false) > kMaxSmemPerBlock;
-    if (pl->stream_w && k != 16)
+    // Rank-k update with the fields resident (K = 16; K = 32 with W resident).
+    if ((k == 16 || k == 32) && p->max_npad + k <= 512) {
+        pl->stream_w = pl->hilo || blocked_smem_bytes(p->max_npad, p->words, k, false, false) >
+                                       kMaxSmemPerBlock;
+        const size_t smem = blocked_smem_bytes(p->max_npad, p->words, k, pl->stream_w, pl->hilo);
+        if ((k == 16 || !pl->stream_w) && smem <= kMaxSmemPerBlock) return SAIS_OK;
+    }
+    // Block fields from a GEMM over the states (the caller's K, or the default then 16).
+    for (int kf : {prm->block_k ? k : field_default_k(p->max_m), k}) {
+        if (field_fits(p->max_n16, p->words, p->max_m, true, kf, pl->hilo)) {
+            pl->k = kf;
+            pl->field = true;
+            return SAIS_OK;
+        }
+    }
+    if (k != 16 && p->max_m > 2)
         return fail(SAIS_EUNSUPPORTED,
-                    "blocked sampler: streamed W (N'=%d%s) runs with block_k = 16 only",
-                    p->max_spins, pl->hilo ? ", pair values above 256" : "");
-    const size_t smem = blocked_smem_bytes(p->max_npad, p->words, k, pl->stream_w, pl->hilo);
-    if (smem > kMaxSmemPerBlock)
+                    "blocked sampler: block_k = %d takes at most 2 constraints (m = %d)", k,
+                    p->max_m);
+    if (k != 16 && field_tmem_cols(p->max_n16, k) <= 512)
         return fail(SAIS_EUNSUPPORTED,
-                    "blocked sampler: N'=%d needs %zu bytes of shared memory (max %zu)",
-                    p->max_spins, smem, kMaxSmemPerBlock);
+                    "blocked sampler: block_k = %d with n = %d needs %zu bytes of shared memory "
+                    "(max %zu)", k, p->max_n, field_smem_bytes(p->max_n16, p->words, k, pl->hilo),
+                    kMaxSmemPerBlock);
+    // Beyond one SM (n > 992): fields split over a CTA pair (thread-block cluster of two).
+    for (int jj = 0; jj < p->count; ++jj) {
+        const HostInst &h = p->host[jj];
+        if (!pair_eligible(h.n, h.m, h.has_w))
+            return fail(SAIS_EUNSUPPORTED,
+                        "blocked sampler: n = %d items exceed what one SM holds and instance %d "
+                        "(n=%d) is outside the CTA-pair range (128 <= n rounded up to 64 <= 1024)",
+                        p->max_n, jj, h.n);
+    }
+    if (k != 16)
+        return fail(SAIS_EUNSUPPORTED,
+                    "blocked sampler: n = %d exceeds one SM at block_k = %d; CTA pairs run "
+                    "block_k = 16 only", p->max_n, k);
+    pl->pair = true;
     return SAIS_OK;
 }
 
@@ -921,6 +1016,9 @@ sais_status enqueue_sample(sais_problem *p, const sais_sample_params *prm, const
     }
     if (pl.variant == SAIS_BLOCKED && pl.pair)
         e = launch_pair_sampler(a, p->max_m, p->max_n, p->words, pl.hilo, p->d_status, polls, st);
+    else if (pl.variant == SAIS_BLOCKED && pl.field)
+        e = launch_field_sampler(a, p->max_m, p->max_n16, p->words, pl.k, pl.hilo, p->d_status,
+                                 polls, st);
     else if (pl.variant == SAIS_BLOCKED)
         e = launch_blocked_sampler(a, p->max_m, p->max_npad, p->words, pl.k, pl.stream_w, pl.hilo,
                                    p->d_status, polls, st);
@@ -936,6 +1034,7 @@ extern "C" {
 
 sais_status sais_sample(sais_problem *p, const sais_sample_params *prm, const float *lambda,
                         uint32_t *x, int64_t *cost, int64_t *g, uint8_t *feasible, void *stream) {
+    NvtxRange nvtx_range("sais_sample");
     sais_status s = check_sample_params(p, prm);
     if (s != SAIS_OK) return s;
     if (!lambda || !x || !cost || !g) return fail(SAIS_EINVAL, "NULL device buffer");
@@ -947,6 +1046,7 @@ sais_status sais_sample(sais_problem *p, const sais_sample_params *prm, const fl
 sais_status sais_sample_trace(sais_problem *p, const sais_sample_params *prm, const float *lambda,
                               uint32_t *x, int64_t *cost, int64_t *g, uint8_t *feasible,
                               uint32_t *trace, void *stream) {
+    NvtxRange nvtx_range("sais_sample_trace");
     sais_status s = check_sample_params(p, prm);
     if (s != SAIS_OK) return s;
     if (!lambda || !x || !cost || !g || !trace) return fail(SAIS_EINVAL, "NULL device buffer");
@@ -959,6 +1059,7 @@ sais_status sais_sample_run_best(sais_problem *p, const sais_sample_params *prm,
                                  const float *lambda, uint32_t *x, int64_t *cost, int64_t *g,
                                  uint8_t *feasible, uint32_t *run_x, int64_t *run_cost,
                                  int32_t *run_sweep, int32_t *run_nfeas, void *stream) {
+    NvtxRange nvtx_range("sais_sample_run_best");
     sais_status s = check_sample_params(p, prm);
     if (s != SAIS_OK) return s;
     if (!lambda || !x || !cost || !g || !run_x || !run_cost)
@@ -971,6 +1072,32 @@ sais_status sais_sample_run_best(sais_problem *p, const sais_sample_params *prm,
     run.nfeas = run_nfeas;
     return enqueue_sample(p, prm, lambda, nullptr, x, cost, g, feasible, nullptr,
                           static_cast<cudaStream_t>(stream), run);
+}
+
+sais_status sais_sample_plan(const sais_problem *p, const sais_sample_params *prm,
+                             sais_plan *out) {
+    if (!out) return fail(SAIS_EINVAL, "out is NULL");
+    sais_status s = check_sample_params(p, prm);
+    if (s != SAIS_OK) return s;
+    SamplePlan pl;
+    s = plan_sample(p, prm, &pl);
+    if (s != SAIS_OK) return s;
+    *out = sais_plan{};
+    if (pl.variant == SAIS_AUTO) {
+        out->kernel = SAIS_KERNEL_GROUPS;
+    } else if (pl.variant == SAIS_PLAIN) {
+        out->kernel = SAIS_KERNEL_PLAIN;
+        out->chains_per_cta = pl.cpb;
+    } else {
+        out->kernel = pl.pair ? SAIS_KERNEL_CTA_PAIR
+                              : (pl.field ? SAIS_KERNEL_BLOCK_FIELD
+                                          : (pl.stream_w ? SAIS_KERNEL_RANKK_STREAMED
+                                                         : SAIS_KERNEL_RANKK_RESIDENT));
+        out->block_k = pl.k;
+        out->chains_per_cta = 128;
+        out->hilo = pl.hilo ? 1 : 0;
+    }
+    return SAIS_OK;
 }
 
 sais_status sais_synchronize(sais_problem *p, void *stream) {
@@ -990,6 +1117,7 @@ sais_status sais_synchronize(sais_problem *p, void *stream) {
 
 sais_status sais_update_lambda(sais_problem *p, const int64_t *g, int32_t chains, double eta,
                                int32_t project_nonneg, float *lambda, void *stream) {
+    NvtxRange nvtx_range("sais_update_lambda");
     if (!p || !g || !lambda) return fail(SAIS_EINVAL, "NULL argument");
     if (chains < 1) return fail(SAIS_EINVAL, "chains = %d: need >= 1", chains);
     if (!std::isfinite(eta)) return fail(SAIS_EINVAL, "eta must be finite");
@@ -1016,6 +1144,7 @@ sais_status sais_update_lambda_rule(sais_problem *p, const int64_t *g, int32_t c
                                     double eta, int32_t project_nonneg, uint32_t iter,
                                     double eta_decay, int32_t eta_sqrt, double momentum,
                                     double *avg, float *lambda, void *stream) {
+    NvtxRange nvtx_range("sais_update_lambda_rule");
     if (!p || !g || !lambda) return fail(SAIS_EINVAL, "NULL argument");
     if (chains < 1) return fail(SAIS_EINVAL, "chains = %d: need >= 1", chains);
     if (!std::isfinite(eta)) return fail(SAIS_EINVAL, "eta must be finite");
@@ -1050,6 +1179,7 @@ sais_status sais_track_best(sais_problem *p, const uint32_t *x, const int64_t *c
                             const uint8_t *feasible, int32_t chains, uint32_t iter,
                             int64_t *best_cost, uint32_t *best_x, int32_t *best_iter,
                             int32_t *best_chain, int64_t *feasible_count, void *stream) {
+    NvtxRange nvtx_range("sais_track_best");
     if (!p || !x || !cost || !best_cost || !best_x || !best_iter || !best_chain || !feasible_count)
         return fail(SAIS_EINVAL, "NULL argument");
     if (chains < 1) return fail(SAIS_EINVAL, "chains = %d: need >= 1", chains);
@@ -1079,6 +1209,7 @@ sais_status sais_track_best(sais_problem *p, const uint32_t *x, const int64_t *c
 
 sais_status sais_solve(sais_problem *p, const sais_solve_params *prm, sais_solve_result *res,
                        void *stream) {
+    NvtxRange nvtx_range("sais_solve");
     if (!p || !prm || !res) return fail(SAIS_EINVAL, "NULL argument");
     if (prm->iters < 1) return fail(SAIS_EINVAL, "iters = %d: need >= 1", prm->iters);
     if (!std::isfinite(prm->eta)) return fail(SAIS_EINVAL, "eta must be finite");
@@ -1234,6 +1365,7 @@ sais_status sais_solve(sais_problem *p, const sais_solve_params *prm, sais_solve
     }
     SAIS_CUDA(cudaEventRecord(ev0, st));
     for (int k = 0; k < K; ++k) {
+        NvtxRange nvtx_iter("sais_solve iteration");
         if (exec) {
             cudaError_t e = cudaGraphLaunch(exec, st);
             if (e != cudaSuccess) {
@@ -1306,6 +1438,7 @@ sais_status sais_set_instance_chains(sais_problem *p, const int32_t *counts) {
 
 sais_status sais_autotune(sais_problem *p, int32_t chains, int32_t sweeps, sais_tuning *out,
                           void *stream) {
+    NvtxRange nvtx_range("sais_autotune");
     if (!p || !out) return fail(SAIS_EINVAL, "NULL argument");
     if (chains < 1 || sweeps < 1) return fail(SAIS_EINVAL, "need chains >= 1 and sweeps >= 1");
     DeviceGuard dg(p->device);
@@ -1363,7 +1496,11 @@ sais_status sais_autotune(sais_problem *p, int32_t chains, int32_t sweeps, sais_
             int variant, k, cpb;
         };
         std::vector<Cand> cands;
-        if (g.blocked_ok) {
+        if (g.blocked_ok && g.field) {
+            for (int k : {16, 32, 64})
+                if (field_fits(g.max_n16, g.words, g.max_m, true, k, g.hilo))
+                    cands.push_back({SAIS_BLOCKED, k, g.cpb});
+        } else if (g.blocked_ok) {
             cands.push_back({SAIS_BLOCKED, 16, g.cpb});
             if (!g.stream_w &&
                 blocked_smem_bytes(g.max_npad, g.words, 32, false, false) <= kMaxSmemPerBlock &&
@@ -1443,6 +1580,7 @@ sais_status sais_constraint_features(const sais_problem *p, float *out, int32_t 
 }
 
 sais_status sais_warm_start(sais_problem *p, const sais_mlp *m, float *lambda, void *stream) {
+    NvtxRange nvtx_range("sais_warm_start");
     if (!p || !m || !lambda) return fail(SAIS_EINVAL, "NULL argument");
     DeviceGuard dg(p->device);
     return mlp_warm_start_launch(m, p->d_feat, p->d_feat_dst, p->feat_rows, lambda, p->device,

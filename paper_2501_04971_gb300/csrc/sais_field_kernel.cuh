@@ -1,0 +1,718 @@
+// sais_field_kernel.cuh -- block-field p-bit sampler: the fields of each block of K spins come
+// from one tensor-core GEMM over the current chain states.
+//
+// The Gibbs sweep of Sec. III-B stays sequential: spins are visited in index order and each
+// decision sees every earlier flip.  The objective part of the p-bit input (Eq. 9) is the
+// integer field F_i = h_i + sum_j W_ij x_j.  Spins are taken in blocks of K:
+//   1. before block b, its K fields are computed from the chain states as they stand,
+//      F[chains, blk] = h[blk] + X[chains, :] W[:, blk], one tcgen05.mma chain of
+//      ceil(n/16) steps (M = 128 chains, N = K, K-dim = 16 item spins per step) in BF16 with
+//      FP32 accumulation.  Products and partial sums are integers below 2^24, so the fields are
+//      exact, equal to those the plain sampler carries;
+//   2. the K decisions are made one after the other on CUDA cores, each flip correcting the
+//      fields of the block's later spins (W[blk, blk], exact FP32);
+//   3. the block's new states go back into X (TMEM) and the next block's GEMM is issued.
+// Only the item spins enter X: slack spins have no pair values (Sec. IV-A).
+//
+// Tensor memory per CTA is X (BF16 0/1, 8 columns per 16 item spins) plus K columns of fields,
+// so an SM holds two CTAs of 128 chains when n <= 480 (K = 16): while one CTA waits for its
+// GEMM the other decides, and each SM sub-partition runs two independent decision chains.  A
+// sampler that kept every field F_i resident in TMEM (N' columns per 128 chains) would fit one.
+//
+// Layout (one CTA = 128 chains of one instance):
+//   TMEM   X: lane = chain, column c holds spins 2c (low half) and 2c+1 as BF16 0 / 1.
+//          D: the block's K fields (FP32) in the last K of the CTA's columns.
+//   SMEM   a ring of 3 W tiles, each the K rows of one block (BF16, the K-major B operand:
+//          element (i, j) at ((i/8)(n16/8) + j/8) 128 + (i%8) 16 + (j%8) 2 bytes) followed by the
+//          block's K x K diagonal in FP32 for the in-block corrections; the bit-packed states;
+//          a two-slot ring of noise.
+//   Warps  0-3 decide (warp w owns TMEM lanes 32w..32w+31: its 32 chains); the last of them to
+//          finish a block issues the next block's GEMM.  Warps 4-7 compute the noise (Philox,
+//          atanh) up to two blocks ahead; lane 0 of warp 4 also streams the W tiles by bulk
+//          asynchronous copies (TMA engine).  The decision warps run with 192 registers and the
+//          noise warps with 64 (setmaxnreg), from the 128 per thread the CTA launches with.
+//   After the last sweep a readout pass recomputes every field from the final states for the
+//   cost c(x) = -(sum_i x_i F_i + h^T x)/2.  With best-in-run tracking the cost also follows
+//   every flip, c' - c = -d F_i.
+// Every mbarrier wait is bounded: on expiry the kernel records SAIS_ETIMEOUT, stops, drains its
+// copies and MMAs, frees TMEM and exits.
+#pragma once
+
+#include "sais_device.cuh"
+#include "sais_tc.cuh"
+
+namespace sais {
+
+// Launch shape shared by every instantiation of the block-field sampler.
+struct FieldLaunch {
+    size_t smem;
+    uint32_t cols;
+    int32_t max_n16;
+};
+
+namespace {
+
+constexpr int kFLanes = 128;
+constexpr int kFThreads = 256;
+constexpr int kFNoiseWarp0 = 4;
+// W tile slots: three for K = 16 (the tile stager may run two blocks ahead), two for K >= 32
+// (one block ahead, which is all a block's GEMM needs; the larger tiles fit shared memory).
+__host__ __device__ constexpr uint32_t f_ring(int K) { return K == 16 ? 3u : 2u; }
+constexpr long long kFWaitCycles = 8000000000ll;   // about 4 s at 2 GHz
+// bars: 0 never completed (timeout test), 1 the block's field GEMM done (one phase per block),
+// 2..5 drain of decision warp 0..3, 6..13 noise slot written (2 q + slot), 14..21 noise slot
+// consumed, 22..24 W tile slot filled, 25..27 W tile slot free (4 arrivals: every decision warp
+// is done with the block); the ring uses the first f_ring(K) of each
+constexpr int kFBarNever = 0, kFBarMma = 1, kFBarDrain = 2, kFBarNoise = 6, kFBarNoiseFree = 14,
+              kFBarTile = 22, kFBarTileFree = 25, kFBars = 28;
+
+__device__ __forceinline__ bool f_expired(long long n, long long polls, unsigned long long t0) {
+    return polls > 0 ? n >= polls : (long long)(clock64() - t0) > kFWaitCycles;
+}
+
+__device__ __forceinline__ bool f_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                       int32_t *status, long long polls) {
+    if (tc::mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = clock64();
+    for (long long n = 0;; ++n) {
+        if (tc::mbar_try_wait(bar, parity)) return true;
+        if (abort_flag && *abort_flag) return false;
+        if (f_expired(n, polls, t0)) {
+            if (abort_flag) *abort_flag = 1;
+            if (status) atomicExch(status, (int32_t)SAIS_ETIMEOUT);
+            return false;
+        }
+    }
+}
+
+// Warp-collective bounded wait: the warp leaves together, when every lane has seen the phase or
+// when any lane sees the abort flag or the limit.
+__device__ __forceinline__ bool f_wait_warp(uint64_t *bar, uint32_t parity,
+                                            volatile int *abort_flag, int32_t *status,
+                                            long long polls) {
+    if (__all_sync(0xffffffffu, tc::mbar_try_wait(bar, parity))) return true;
+    const unsigned long long t0 = clock64();
+    for (long long n = 0;; ++n) {
+        const bool got = tc::mbar_try_wait(bar, parity);
+        if (__all_sync(0xffffffffu, got)) return true;
+        const bool give_up = *abort_flag != 0 || f_expired(n, polls, t0);
+        if (__any_sync(0xffffffffu, give_up)) {
+            if ((threadIdx.x & 31) == 0 && !*abort_flag) {
+                *abort_flag = 1;
+                if (status) atomicExch(status, (int32_t)SAIS_ETIMEOUT);
+            }
+            return false;
+        }
+    }
+}
+
+// 32 lanes x K columns of the fields (warp-collective), waited for.
+template <int K>
+__device__ __forceinline__ void f_load_fields(uint32_t taddr, float (&r)[K]) {
+    if constexpr (K == 16) {
+        tc::tmem_ld16(taddr, r);
+    } else {
+#pragma unroll
+        for (int c = 0; c < K; c += 32) {
+            float v[32];
+            tc::tmem_ld32(taddr + (uint32_t)c, v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) r[c + i] = v[i];
+        }
+    }
+}
+
+template <int K>
+__device__ __forceinline__ const float *f_diag_image(const InstDev *ip) {
+    return K == 16 ? ip->Wdiag : (K == 32 ? ip->Wd32 : ip->Wd64);
+}
+
+template <int MC, int K, bool kHiLo, bool kTrack>
+__global__ void __launch_bounds__(kFThreads, 2)
+    field_sampler_kernel(SampleArgs a, int32_t *status, long long dec_wait_polls,
+                         uint32_t tmem_cols, int32_t max_n16) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    constexpr int kXW = K >= 32 ? K / 32 : 1;   // state words a block spans
+    constexpr uint32_t kFRing = f_ring(K);
+    const int j = a.work ? a.work[2 * blockIdx.x] : (int)blockIdx.y;
+    const int grp = a.work ? a.work[2 * blockIdx.x + 1] : (int)blockIdx.x;
+    const InstDev *__restrict__ ip = a.inst + j;
+    const int m = ip->m, nprime = ip->nprime, words = ip->words, n16 = ip->n16;
+    const int kx = n16 / 16;                   // GEMM steps per block
+    const int nb = (nprime + K - 1) / K;       // blocks per sweep
+    const uint32_t tile_bytes = (uint32_t)K * (uint32_t)n16 * 2u;   // one BF16 term, one block
+    const uint32_t diag_off = tile_bytes * (kHiLo ? 2u : 1u);
+    const uint32_t slot_stride =
+        (uint32_t)K * (uint32_t)max_n16 * 2u * (kHiLo ? 2u : 1u) + (uint32_t)(K * K * 4);
+    const uint32_t dcol = tmem_cols - (uint32_t)K;   // the fields D: last K columns
+    const uint32_t total = (uint32_t)a.sweeps * (uint32_t)nb + (uint32_t)nb;   // + readout pass
+    const uint32_t ndec = (uint32_t)a.sweeps * (uint32_t)nb;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // State words per chain in shared memory: an even count, since a block of K = 64 spins may
+    // span one word past ceil(N'/32) (padding spins, always 0).
+    const int xwords = (words + 1) & ~1;
+    unsigned char *ring = smem;
+    uint32_t *xs = reinterpret_cast<uint32_t *>(smem + kFRing * slot_stride);
+    float *thbuf = reinterpret_cast<float *>(xs + xwords * kFLanes);   // [2][K][128] noise
+    uint64_t *bars = reinterpret_cast<uint64_t *>(thbuf + 2 * K * kFLanes);
+    uint32_t *arrivals = reinterpret_cast<uint32_t *>(bars + kFBars);   // [3]
+    uint32_t *tmem_slot = arrivals + 3;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kFBars; ++i)
+            tc::mbar_init(&bars[i], (i >= kFBarTileFree && i < kFBarTileFree + 3) ? 4u : 1u);
+        arrivals[0] = arrivals[1] = arrivals[2] = 0u;
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+        tc::fence_proxy_async_smem();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tmem_slot, tmem_cols);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t iter = a.iter_dev ? *a.iter_dev : a.iter;
+
+    if (warp >= kFNoiseWarp0) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 64;");
+        // Noise warps: warp 4+q produces theta = atanh(rho) for the chains of decision warp q, up
+        // to two blocks ahead, into a two-slot ring.  Lane 0 of warp 4 streams the W tiles.
+        const int q = warp - kFNoiseWarp0;
+        const int r = q * 32 + lane;
+        const uint32_t chain = (uint32_t)(grp * kFLanes + r);
+        const uint64_t seed = a.seed + (uint64_t)j;
+        const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
+        const unsigned char *Wg = reinterpret_cast<const unsigned char *>(ip->Wg);
+        const unsigned char *Wgl = reinterpret_cast<const unsigned char *>(ip->Wg_lo);
+        const unsigned char *Wd = reinterpret_cast<const unsigned char *>(f_diag_image<K>(ip));
+        const bool stager = q == 0 && lane == 0;
+        uint32_t tiles_issued = 0;
+        // W tile of block u (decision or readout) into slot u % kFRing, once that slot's previous
+        // block (u - kFRing) is done.
+        auto stage = [&](uint32_t u) -> bool {
+            const uint32_t ts = u % kFRing;
+            if (u >= kFRing &&
+                !f_wait(&bars[kFBarTileFree + ts], ((u / kFRing) - 1u) & 1u, abort_flag, status, 0))
+                return false;
+            const uint32_t b = u < ndec ? u % (uint32_t)nb : u - ndec;
+            unsigned char *dst = ring + ts * slot_stride;
+            const uint32_t dbytes = (uint32_t)(K * K * 4);
+            tc::mbar_expect_tx(&bars[kFBarTile + ts], diag_off + dbytes);
+            tc::bulk_g2s(dst, Wg + (size_t)b * tile_bytes, tile_bytes, &bars[kFBarTile + ts]);
+            if (kHiLo)
+                tc::bulk_g2s(dst + tile_bytes, Wgl + (size_t)b * tile_bytes, tile_bytes,
+                             &bars[kFBarTile + ts]);
+            tc::bulk_g2s(dst + diag_off, Wd + (size_t)b * dbytes, dbytes, &bars[kFBarTile + ts]);
+            ++tiles_issued;
+            return true;
+        };
+        bool ok = true;
+        // Tile 0 goes out before any noise (block 0's GEMM needs it at once); tile u + 1 after
+        // the noise of block u, a block ahead of its GEMM.  Its slot was freed by block
+        // u + 1 - kFRing, which needs no noise this warp has yet to produce.
+        if (stager) ok = stage(0u);
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        for (uint32_t it = 0; ok && it < ndec; ++it) {
+            const uint32_t slot = it & 1u;
+            if (it >= 2 && !f_wait_warp(&bars[kFBarNoiseFree + 2 * q + slot],
+                                        ((it >> 1) + 1u) & 1u, abort_flag, status, 0))
+                break;
+            const uint32_t t = it / (uint32_t)nb;
+            const int s0 = (int)(it % (uint32_t)nb) * K;
+            float *tb = thbuf + slot * K * kFLanes;
+#pragma unroll 4
+            for (int g4 = 0; g4 < K / 4; ++g4) {
+                const uint4 rw = philox4x32_10(
+                    make_uint4((uint32_t)((s0 >> 2) + g4), t, chain, iter), key0, key1);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    // Spins past N' (block padding) get a threshold that keeps them at 0.
+                    const bool real = s0 + 4 * g4 + e < nprime;
+                    tb[(4 * g4 + e) * kFLanes + r] = real ? theta_of_word(word_of(rw, e)) : -1e30f;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&bars[kFBarNoise + 2 * q + slot]);
+            if (stager && it + 1u < total) ok = stage(it + 1u);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        }
+        // Tiles of the readout pass (and of the last decision blocks when the sweeps are few).
+        if (stager && ok && !*abort_flag)
+            for (uint32_t u = tiles_issued; u < total; ++u)
+                if (!stage(u)) break;
+        // The copies complete before shared memory is released.
+        if (stager)
+            for (uint32_t ts = 0; ts < kFRing && ts < tiles_issued; ++ts) {
+                const uint32_t uses = (tiles_issued - ts + kFRing - 1u) / kFRing;
+                f_wait(&bars[kFBarTile + ts], (uses - 1u) & 1u, nullptr, status, 0);
+            }
+        __syncwarp();
+    } else {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 192;");
+        const int r = threadIdx.x;
+        const int chain = grp * kFLanes + r;
+        const bool valid = chain < (a.inst_chains ? a.inst_chains[j] : a.chains);
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        const uint64_t seed = a.seed + (uint64_t)j;
+        const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
+        const float sf = ip->sigma_f, sg = ip->sigma_g, kappa = ip->kappa;
+        const double psg2 = ip->psg2;
+        const float *__restrict__ hF = ip->hF;
+        const int32_t *__restrict__ acol = ip->acol;
+        const float *__restrict__ Dv = ip->D;
+        const float *__restrict__ asum = ip->asum;
+        const float4 *__restrict__ spinc = ip->spinc;
+        const float *lam = a.lambda + (size_t)j * a.m_stride;
+        const uint32_t idesc = tc::idesc_bf16_f32(128, (uint32_t)K);
+
+        // The GEMM of block u: D = X W[:, blk], kx steps per BF16 term, then one commit.  Issued
+        // by one thread once the tile is in shared memory (bounded wait).
+        auto issue_gemm = [&](uint32_t u) -> bool {
+            const uint32_t ts = u % kFRing;
+            if (!f_wait(&bars[kFBarTile + ts], (u / kFRing) & 1u, abort_flag, status, 0))
+                return false;
+            const uint32_t base = tc::smem_u32(ring + ts * slot_stride);
+            const uint32_t sbo = (uint32_t)n16 * 16u;
+#pragma unroll
+            for (int term = 0; term < (kHiLo ? 2 : 1); ++term) {
+                // descriptor of step kc: the start address advances by 256 bytes (16 in the
+                // descriptor's address field, which stays below 2^14 in shared memory)
+                uint64_t bd = tc::smem_desc(base + (uint32_t)term * tile_bytes, 128u, sbo);
+                for (int kc = 0; kc < kx; ++kc) {
+                    tc::mma_bf16_tmem_a(tmem + dcol, tmem + 8u * (uint32_t)kc, bd, idesc,
+                                        (term | kc) != 0 ? 1u : 0u);
+                    bd += 16u;
+                }
+            }
+            tc::mma_commit(&bars[kFBarMma]);
+            return true;
+        };
+        // Arrival of this warp at the end of a block (its TMEM stores waited for and fenced); the
+        // last of the four issues the GEMM of block `next` (if any).
+        auto arrive_and_issue = [&](uint32_t *counter, uint32_t next) -> bool {
+            bool ok2 = true;
+            tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                const bool last = (atomicAdd(counter, 1u) & 3u) == 3u;
+                if (last && next < total) {
+                    __threadfence_block();
+                    tc::tc_fence_after();
+                    ok2 = issue_gemm(next);
+                }
+            }
+            return __shfl_sync(0xffffffffu, ok2 ? 1 : 0, 0) != 0;
+        };
+
+        // Every run starts from x = 0 (Sec. III-B): X and the bit-packed states cleared.
+        for (int w = 0; w < xwords; ++w) xs[w * kFLanes + r] = 0u;
+        {
+            const uint32_t zero8[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+            for (int c0 = 0; c0 < 8 * kx; c0 += 8) tc::tmem_st8(lane_addr + (uint32_t)c0, zero8);
+        }
+        bool ok = arrive_and_issue(&arrivals[2], 0u);
+
+        int32_t g[MC];
+        float c[MC], cA[MC];
+        float Mmax = 0.f;
+#pragma unroll
+        for (int k = 0; k < MC; ++k) {
+            if (k < m) {
+                cA[k] = __double2float_rn((double)sg * (double)lam[k]);
+                g[k] = -ip->b[k];
+                c[k] = fmaf(kappa, (float)g[k], cA[k]);
+                Mmax = fmaxf(Mmax, fmaf(fabsf(kappa), fabsf((float)g[k]), fabsf(cA[k])));
+            } else {
+                cA[k] = 0.f;
+                g[k] = 0;
+                c[k] = 0.f;
+            }
+        }
+        // The constraint values as FP32 too (exact: |g| < 2^24, checked at creation), so that
+        // the decision chain updates them and c_k without integer <-> float conversions.
+        float gf[MC];
+#pragma unroll
+        for (int k = 0; k < MC; ++k) gf[k] = (float)g[k];
+        const float errk = field_err_factor(m);
+        // Fault-injection test (dec_wait_polls > 0): wait on a barrier nothing completes, so the
+        // bound expires and the kernel takes its timeout path.
+        if (ok && dec_wait_polls > 0)
+            ok = f_wait_warp(&bars[kFBarNever], 0, abort_flag, status, dec_wait_polls);
+        long long ccur = 0, rbest = LLONG_MAX;   // cost of the current state (kTrack)
+        int rsweep = -1, rnf = 0;
+        long long sumF = 0, sumh = 0;            // readout pass
+        float Fr[K];
+        for (uint32_t it = 0; ok && it < total; ++it) {
+            const bool readout = it >= ndec;
+            const uint32_t t = readout ? (uint32_t)a.sweeps : it / (uint32_t)nb;
+            const int b = (int)(readout ? it - ndec : it % (uint32_t)nb);
+            const int s0 = b * K;
+            const uint32_t ts = it % kFRing;
+            const uint32_t slot = it & 1u;
+            const float *thb = thbuf + slot * K * kFLanes + r;
+            // K = 16: the block's per-spin data, loaded before the wait for the block's GEMM,
+            // which they overlap: the noise theta and the record {a_0i, D_i, sum_k a_ki, a_1i}.
+            // Larger blocks load them spin by spin (registers).
+            constexpr int kPre = K == 16 ? 16 : 1;
+            float th16[kPre];
+            float4 sc16[kPre];
+            if (!readout) {
+                // Noise of the block (partner noise warp) and its W tile (diagonal for the
+                // in-block corrections).
+                if (!f_wait_warp(&bars[kFBarNoise + 2 * warp + slot], (it >> 1) & 1u, abort_flag,
+                                 status, dec_wait_polls) ||
+                    !f_wait_warp(&bars[kFBarTile + ts], (it / kFRing) & 1u, abort_flag, status,
+                                 dec_wait_polls)) {
+                    ok = false;
+                    break;
+                }
+                if (K == 16) {   // the noise is in registers: its slot may be refilled
+#pragma unroll
+                    for (int ii = 0; ii < kPre; ++ii) {
+                        th16[ii] = thb[ii * kFLanes];
+                        sc16[ii] = __ldg(spinc + s0 + ii);
+                    }
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&bars[kFBarNoiseFree + 2 * warp + slot]);
+                }
+            }
+            // This block's fields: its GEMM is done (issued by the last warp of the block before).
+            if (!f_wait_warp(&bars[kFBarMma], it & 1u, abort_flag, status, dec_wait_polls)) {
+                ok = false;
+                break;
+            }
+            tc::tc_fence_after();
+            f_load_fields<K>(lane_addr + dcol, Fr);
+#pragma unroll
+            for (int ii = 0; ii < K; ++ii) Fr[ii] += __ldg(hF + s0 + ii);   // exact integers
+            const int wi = s0 >> 5, sb = s0 & 31;
+            if (readout) {
+                // Readout pass: sum_i x_i F_i and h^T x over the block, from the final states.
+                int32_t pf = 0, ph = 0;   // |F|, |h| < 2^24 and K <= 64 terms: exact in int32
+#pragma unroll
+                for (int ii = 0; ii < K; ++ii) {
+                    const uint32_t xw = xs[((s0 + ii) >> 5) * kFLanes + r];
+                    if ((xw >> ((s0 + ii) & 31)) & 1u) {
+                        pf += __float2int_rz(Fr[ii]);
+                        ph += __float2int_rz(__ldg(hF + s0 + ii));
+                    }
+                }
+                sumF += pf;
+                sumh += ph;
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&bars[kFBarTileFree + ts]);
+                ok = arrive_and_issue(&arrivals[it & 1u], it + 1u);
+                continue;
+            }
+            const float beta = beta_of_sweep(a.beta_max, (int)t, a.sweeps);
+            const float hb = 0.5f * beta;
+            const float ez = hb * errk;
+            const float *wdg = reinterpret_cast<const float *>(ring + ts * slot_stride + diag_off);
+            uint32_t xwv[kXW];
+#pragma unroll
+            for (int q = 0; q < kXW; ++q) xwv[q] = xs[(wi + q) * kFLanes + r];
+            uint32_t xold[kXW];
+#pragma unroll
+            for (int q = 0; q < kXW; ++q) xold[q] = xwv[q];
+            // Block-start chain state, kept for an exact re-run of the block.
+            float gf0[MC], cb[MC];
+            const float M0 = Mmax;
+#pragma unroll
+            for (int k = 0; k < MC; ++k) {
+                gf0[k] = gf[k];
+                cb[k] = c[k];
+            }
+            int32_t cblk = 0;   // cost change over the block (kTrack): |sum| < K 2^24 <= 2^30
+            bool near_tie = false;
+#pragma unroll
+            for (int ii = 0; ii < K; ++ii) {
+                const int s = s0 + ii;
+                // word and bit of spin s in the block's state words (K = 16: one word, bit sb + ii;
+                // K >= 32: blocks start on a word, so the word index is a constant)
+                const int bw = K == 16 ? 0 : (ii >> 5), bi = K == 16 ? sb + ii : (ii & 31);
+                const float4 sc = K == 16 ? sc16[ii % kPre] : __ldg(spinc + s);
+                // Row ii of the block's diagonal of W (FP32, the same address for every lane):
+                // the quads right of spin ii, for the in-block corrections.
+                float4 wq[K / 4];
+#pragma unroll
+                for (int q4 = (ii + 1) >> 2; q4 < K / 4; ++q4)
+                    wq[q4] = *reinterpret_cast<const float4 *>(wdg + ii * K + 4 * q4);
+                const float Fi = Fr[ii];
+                const int xi = (xold[bw] >> bi) & 1;
+                float akf[MC];
+                float acc = sf * Fi;
+                const float tabs = fabsf(acc);
+#pragma unroll
+                for (int k = 0; k < MC; ++k) {
+                    if (k == 0)
+                        akf[k] = (float)__float_as_int(sc.x);
+                    else if (k == 1)
+                        akf[k] = (float)__float_as_int(sc.w);
+                    else
+                        akf[k] = (k < m) ? (float)__ldg(acol + (size_t)s * m + k) : 0.f;
+                    acc = fmaf(-akf[k], c[k], acc);
+                }
+                const float Di = sc.y;
+                acc = fmaf(xi ? 1.f : -1.f, Di, acc);
+                const float z = hb * acc;
+                const float theta = K == 16 ? th16[ii % kPre] : thb[ii * kFLanes];
+                const float y = z + theta;
+                const float bound =
+                    ez * (tabs + sc.z * Mmax + Di) + kThetaRelErr * fabsf(theta) + kThetaAbsErr;
+                // A decision the FP32 bound cannot settle is only flagged here; the warp then
+                // re-runs the block below with the FP64 path.
+                near_tie |= !(fabsf(y) > bound);
+                // The flip d = x_new - x_i in {-1, 0, +1}, kept as FP32.
+                const float df = (y > 0.f ? 1.f : 0.f) - (xi ? 1.f : 0.f);
+                if (kTrack) cblk -= __float2int_rz(df * Fi);
+                xwv[bw] ^= (uint32_t)(df != 0.f) << bi;
+                Mmax = 0.f;
+#pragma unroll
+                for (int k = 0; k < MC; ++k) {
+                    if (k < m) {
+                        gf[k] = fmaf(akf[k], df, gf[k]);   // exact integers
+                        c[k] = fmaf(kappa, gf[k], cA[k]);
+                        Mmax = fmaxf(Mmax, fmaf(fabsf(kappa), fabsf(gf[k]), fabsf(cA[k])));
+                    }
+                }
+                if (ii + 1 < K) {
+                    // In-block correction F_jj += W[s, s0+jj] d for the block's later spins.  The
+                    // next spin's field is on the dependency chain: corrected unconditionally (d =
+                    // 0 adds an exact zero); the others only when a chain of the warp flipped.
+                    auto wcol = [&](int jj) -> float {
+                        const float4 &v = wq[jj >> 2];
+                        const int e = jj & 3;
+                        return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+                    };
+                    Fr[ii + 1] = fmaf(df, wcol(ii + 1), Fr[ii + 1]);
+                    if (ii + 2 < K && __any_sync(0xffffffffu, df != 0.f)) {
+#pragma unroll
+                        for (int jj = ii + 2; jj < K; ++jj) Fr[jj] = fmaf(df, wcol(jj), Fr[jj]);
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, near_tie)) {
+                // Exact re-run of the block for the whole warp, from its start state: the fields
+                // from D (this block's GEMM result, unchanged until the next GEMM) plus h and the
+                // block's earlier flips, the noise recomputed, the same FP32 evaluation, and FP64
+                // where the bound cannot settle the decision.  Decisions outside near-ties come
+                // out as before.
+                // The block's bits as one word (bit ii = spin s0 + ii): start state and re-run state.
+                uint64_t bo;
+                if constexpr (K == 16)
+                    bo = (xold[0] >> sb) & 0xFFFFu;
+                else if constexpr (K == 32)
+                    bo = xold[0];
+                else
+                    bo = (uint64_t)xold[0] | ((uint64_t)xold[kXW - 1] << 32);
+                uint64_t bn = bo;
+                Mmax = M0;
+                cblk = 0;
+#pragma unroll
+                for (int k = 0; k < MC; ++k) {
+                    g[k] = (int32_t)gf0[k];
+                    c[k] = cb[k];
+                }
+#pragma unroll 1
+                for (int ii = 0; ii < K; ++ii) {
+                    const int s = s0 + ii;
+                    uint32_t fv;
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
+                                 : "=r"(fv)
+                                 : "r"(lane_addr + dcol + (uint32_t)ii));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    float Fi = __uint_as_float(fv) + __ldg(hF + s);
+                    uint64_t fl = (bn ^ bo) & ((1ull << ii) - 1ull);
+                    while (fl) {
+                        const int i2 = __ffsll((long long)fl) - 1;
+                        fl &= fl - 1ull;
+                        const int d2 = (int)((bn >> i2) & 1ull) - (int)((bo >> i2) & 1ull);
+                        Fi = fmaf((float)d2, wdg[ii * K + i2], Fi);
+                    }
+                    const int xi = (int)((bo >> ii) & 1ull);
+                    int32_t ak[MC];
+                    float acc = sf * Fi;
+                    const float tabs = fabsf(acc);
+#pragma unroll
+                    for (int k = 0; k < MC; ++k) {
+                        ak[k] = (k < m) ? __ldg(acol + (size_t)s * m + k) : 0;
+                        acc = fmaf(-(float)ak[k], c[k], acc);
+                    }
+                    const float Di = __ldg(Dv + s);
+                    acc = fmaf(xi ? 1.f : -1.f, Di, acc);
+                    const float z = hb * acc;
+                    const uint4 rw = philox4x32_10(
+                        make_uint4((uint32_t)(s >> 2), t, (uint32_t)chain, iter), key0, key1);
+                    const float theta = s < nprime ? theta_of_word(word_of(rw, s & 3)) : -1e30f;
+                    const float y = z + theta;
+                    const float bound = ez * (tabs + __ldg(asum + s) * Mmax + Di) +
+                                        kThetaRelErr * fabsf(theta) + kThetaAbsErr;
+                    int xn = y > 0.f;
+                    if (!(fabsf(y) > bound)) {
+                        const float rho = rho_of_word(word_of(rw, s & 3));
+                        xn = decide_exact<MC>(Fi, xi, ak, g, lam, m, sf, sg, psg2, beta, rho);
+                    }
+                    const int d = xn - xi;
+                    if (kTrack) cblk -= d * __float2int_rz(Fi);
+                    bn ^= (uint64_t)(d != 0) << ii;
+                    Mmax = 0.f;
+#pragma unroll
+                    for (int k = 0; k < MC; ++k) {
+                        if (k < m) {
+                            g[k] += ak[k] * d;
+                            c[k] = fmaf(kappa, (float)g[k], cA[k]);
+                            Mmax = fmaxf(Mmax, fmaf(fabsf(kappa), fabsf((float)g[k]),
+                                                    fabsf(cA[k])));
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < MC; ++k) gf[k] = (float)g[k];
+                if constexpr (K == 16) {
+                    xwv[0] = (xold[0] & ~(0xFFFFu << sb)) | ((uint32_t)bn << sb);
+                } else {
+                    xwv[0] = (uint32_t)bn;
+                    if constexpr (kXW > 1) xwv[kXW - 1] = (uint32_t)(bn >> 32);
+                }
+            }
+            if (kTrack) ccur += cblk;
+#pragma unroll
+            for (int q = 0; q < kXW; ++q) xs[(wi + q) * kFLanes + r] = xwv[q];
+            // The block's new states into X (item spins only; BF16 1.0 = 0x3F80), for the GEMMs of
+            // the blocks after it.
+            if (s0 < n16) {
+#pragma unroll
+                for (int h8 = 0; h8 < K / 16; ++h8) {
+                    if (s0 + 16 * h8 < n16) {
+                        uint32_t v8[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int i0 = 16 * h8 + 2 * e;   // spin s0 + i0 and the next one
+                            const uint32_t w0 = xwv[K == 16 ? 0 : (i0 >> 5)];
+                            const int sh = K == 16 ? sb + i0 : (i0 & 31);
+                            v8[e] = (((w0 >> sh) & 1u) ? 0x3F80u : 0u) |
+                                    (((w0 >> (sh + 1)) & 1u) ? 0x3F800000u : 0u);
+                        }
+                        tc::tmem_st8(lane_addr + (uint32_t)((s0 >> 1) + 8 * h8), v8);
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+                if (K != 16) tc::mbar_arrive(&bars[kFBarNoiseFree + 2 * warp + slot]);
+                tc::mbar_arrive(&bars[kFBarTileFree + ts]);
+            }
+            ok = arrive_and_issue(&arrivals[it & 1u], it + 1u);
+            // Sweep end: best feasible sweep-end state of the run, and the trace.
+            if (ok && b == nb - 1) {
+                if (kTrack) {
+                    bool feas = true;
+#pragma unroll
+                    for (int k = 0; k < MC; ++k) {
+                        if (k < m) {
+                            const int o0 = ip->slack_off[k], o1 = ip->slack_off[k + 1];
+                            long long sv = 0;
+                            for (int s = o0; s < o1; ++s)
+                                if ((xs[(s >> 5) * kFLanes + r] >> (s & 31)) & 1u)
+                                    sv += 1LL << (s - o0);
+                            if ((long long)gf[k] - sv > (long long)ip->fmargin[k]) feas = false;
+                        }
+                    }
+                    if (feas) {
+                        ++rnf;
+                        if (ccur < rbest) {
+                            rbest = ccur;
+                            rsweep = (int)t;
+                            if (valid) {
+                                uint32_t *rx = a.run_x + ((size_t)j * a.chains + chain) * a.words;
+                                for (int w = 0; w < a.words; ++w)
+                                    rx[w] = w < words ? xs[w * kFLanes + r] : 0u;
+                            }
+                        }
+                    }
+                }
+                if (a.trace && valid) {
+                    uint32_t *tr =
+                        a.trace + (((size_t)j * a.chains + chain) * a.sweeps + t) * a.words;
+                    for (int w = 0; w < a.words; ++w) tr[w] = w < words ? xs[w * kFLanes + r] : 0u;
+                }
+            }
+        }
+        // Drain: every MMA of the CTA completes before the outputs and the TMEM release.  Each
+        // decision warp's lane 0 commits the MMAs it issued; every warp waits for all four,
+        // bounded but not cut short by an abort.
+        if (lane == 0) tc::mma_commit(&bars[kFBarDrain + warp]);
+        __syncwarp();
+        bool drained = true;
+        if (lane == 0)
+            for (int w = 0; w < 4; ++w)
+                drained = f_wait(&bars[kFBarDrain + w], 0, nullptr, status, 0) && drained;
+        drained = __shfl_sync(0xffffffffu, drained ? 1 : 0, 0) != 0;
+        tc::tc_fence_after();
+        if (ok && drained && valid) {
+#pragma unroll
+            for (int k = 0; k < MC; ++k) g[k] = (int32_t)gf[k];
+            const size_t cidx = (size_t)j * a.chains + chain;
+            for (int w = 0; w < a.words; ++w)
+                a.x[cidx * a.words + w] = w < words ? xs[w * kFLanes + r] : 0u;
+            a.cost[cidx] = -(sumF + sumh) / 2;
+            bool feas = true;
+#pragma unroll
+            for (int k = 0; k < MC; ++k) {
+                if (k < m) {
+                    const int o0 = ip->slack_off[k], o1 = ip->slack_off[k + 1];
+                    long long sv = 0;
+                    for (int s = o0; s < o1; ++s)
+                        if ((xs[(s >> 5) * kFLanes + r] >> (s & 31)) & 1u) sv += 1LL << (s - o0);
+                    if ((long long)g[k] - sv > (long long)ip->fmargin[k]) feas = false;
+                    a.g[cidx * a.m_stride + k] = g[k];
+                }
+            }
+            for (int k = m; k < a.m_stride; ++k) a.g[cidx * a.m_stride + k] = 0;
+            if (a.feasible) a.feasible[cidx] = feas ? 1 : 0;
+            if (kTrack) {
+                a.run_cost[cidx] = rbest;
+                if (a.run_sweep) a.run_sweep[cidx] = rsweep;
+                if (a.run_nfeas) a.run_nfeas[cidx] = rnf;
+                if (rsweep < 0)
+                    for (int w = 0; w < a.words; ++w) a.run_x[cidx * a.words + w] = 0u;
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, tmem_cols);
+    }
+}
+
+template <int MC, int K, bool H, bool T>
+cudaError_t field_launch(const SampleArgs &a, int32_t *status, long long polls,
+                         const FieldLaunch &L, cudaStream_t s) {
+    auto kern = field_sampler_kernel<MC, K, H, T>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)L.smem);
+    if (e != cudaSuccess) return e;
+    const dim3 grid = a.work ? dim3(a.nwork, 1) : dim3((a.chains + kFLanes - 1) / kFLanes, a.count);
+    kern<<<grid, kFThreads, L.smem, s>>>(a, status, polls, L.cols, L.max_n16);
+    return cudaGetLastError();
+}
+
+template <int K, bool H, bool T>
+cudaError_t field_launch_mc(const SampleArgs &a, int max_m, int32_t *status, long long polls,
+                            const FieldLaunch &L, cudaStream_t s) {
+    if (max_m <= 1) return field_launch<1, K, H, T>(a, status, polls, L, s);
+    if (max_m <= 2) return field_launch<2, K, H, T>(a, status, polls, L, s);
+    if (max_m <= 4) return field_launch<4, K, H, T>(a, status, polls, L, s);
+    return field_launch<8, K, H, T>(a, status, polls, L, s);   // m <= 8
+}
+
+}  // namespace
+}  // namespace sais

@@ -7,10 +7,21 @@
 #include <cstdint>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "sais.h"
 
 namespace sais {
+
+// An NVTX range over a scope (entry points, iterations of Algorithm 1): visible in Nsight
+// timelines, a few nanoseconds when no tool is attached (NVTX is header-only and loads a tool
+// library only if one is injected).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 constexpr int kMaxConstraints = 32;    // m <= 32: per-chain constraint state lives in registers
 constexpr int kMaxBlockedConstraints = 8;   // the blocked sampler keeps 8 at most in registers
@@ -48,6 +59,18 @@ struct InstDev {
     // The 16 x 16 diagonal blocks of W as FP32 (exact integers), block b at 256 b, row-major:
     // the in-block corrections of the blocked sampler when W is streamed (NULL if !has_w).
     const float *Wdiag;
+    // Block-field sampler (sais_field_kernel.cuh).  n16 = n rounded up to 16: the K extent of
+    // its GEMM (slack spins have no pair values).  Wg holds W as BF16 with rows in groups of 8:
+    // element (i, j), i < npad, j < n16, at index ((i/8)(n16/8) + j/8) 64 + (i%8) 8 + j%8, so the
+    // rows of one block of spins form one contiguous K-major MMA operand (core matrices of 8 rows
+    // x 8 columns; 128 bytes between column groups, 16 n16 bytes between row groups); Wg_lo is
+    // W - Wg when |W| > 256.  Wd32 / Wd64: the 32 x 32 / 64 x 64 diagonal blocks of W in FP32,
+    // block b at K^2 b, row-major (K = 16 uses Wdiag).
+    int32_t n16;
+    const uint16_t *Wg;
+    const uint16_t *Wg_lo;
+    const float *Wd32;
+    const float *Wd64;
 };
 
 // Arguments of one sampling launch over all instances of a handle.
@@ -123,6 +146,13 @@ cudaError_t launch_blocked_sampler(const SampleArgs &a, int max_m, int max_npad,
                                    int32_t *status, long long dec_wait_polls,
                                    cudaStream_t stream);
 size_t blocked_smem_bytes(int max_npad, int max_words, int block_k, bool stream_w, bool hilo);
+// Block-field sampler: each block's fields from one tcgen05 GEMM over the chain states held in
+// TMEM (W present, m <= 8, 8 ceil(n/16) + K <= 512 TMEM columns).
+size_t field_smem_bytes(int max_n16, int max_words, int block_k, bool hilo);
+uint32_t field_tmem_cols(int max_n16, int block_k);
+cudaError_t launch_field_sampler(const SampleArgs &a, int max_m, int max_n16, int max_words,
+                                 int block_k, bool hilo, int32_t *status,
+                                 long long dec_wait_polls, cudaStream_t stream);
 size_t plain_smem_bytes(int max_npad, int max_words, bool any_w, int cpb);
 // Blocked sampler on a CTA pair (thread-block cluster of two) for instances whose items do not
 // fit one SM's TMEM: W present, m <= 8, 128 <= n rounded up to 64 <= 1024.

@@ -56,6 +56,14 @@ class sais_solve_params(ctypes.Structure):
                 ("eta_decay", _f64), ("eta_sqrt", _i32), ("momentum", _f64)]
 
 
+class sais_plan(ctypes.Structure):
+    _fields_ = [("kernel", _i32), ("block_k", _i32), ("chains_per_cta", _i32), ("hilo", _i32)]
+
+
+KERNEL_NAMES = {0: "plain", 1: "rank-k, W resident", 2: "rank-k, W streamed",
+                3: "block fields by GEMM", 4: "CTA pair", 5: "launch groups"}
+
+
 class sais_tuning(ctypes.Structure):
     _fields_ = [("groups", _i32), ("blocked_instances", _i32), ("plain_instances", _i32),
                 ("reserved", _i32), ("group_variant", _i32 * 16), ("group_block_k", _i32 * 16),
@@ -85,6 +93,7 @@ _SIGS = {
     "sais_track_best": [_P, _P, _P, _P, _i32, _u32, _P, _P, _P, _P, _P, _P],
     "sais_solve": [_P, ctypes.POINTER(sais_solve_params), ctypes.POINTER(sais_solve_result), _P],
     "sais_synchronize": [_P, _P],
+    "sais_sample_plan": [_P, ctypes.POINTER(sais_sample_params), ctypes.POINTER(sais_plan)],
     "sais_set_instance_chains": [_P, _P],
     "sais_autotune": [_P, _i32, _i32, ctypes.POINTER(sais_tuning), _P],
     "sais_solve_noalloc": [_P, ctypes.POINTER(sais_solve_params),
@@ -227,6 +236,12 @@ def sais_solve_noalloc(h, prm, res, stream_ptr):
            "sais_solve_noalloc")
 
 
+def sais_sample_plan(h, prm) -> sais_plan:
+    out = sais_plan()
+    _check(lib().sais_sample_plan(h, ctypes.byref(prm), ctypes.byref(out)), "sais_sample_plan")
+    return out
+
+
 def sais_set_instance_chains(h, counts_ptr):
     _check(lib().sais_set_instance_chains(h, counts_ptr), "sais_set_instance_chains")
 
@@ -332,6 +347,19 @@ class Problem:
         p.block_k, p.chains_per_cta = block_k, chains_per_cta
         p.debug_wait_polls = debug_wait_polls
         return p
+
+    def plan(self, chains: int, variant="blocked", block_k: int = 0,
+             chains_per_cta: int = 0) -> dict:
+        """The launch sais_sample would make (sais_sample_plan): kernel name, block size, CTA
+        shape, hi/lo split."""
+        pl = sais_sample_plan(self.handle, self._params(chains, 1, 1.0, 0, 0, variant, block_k,
+                                                        chains_per_cta))
+        return {"kernel": KERNEL_NAMES.get(pl.kernel, str(pl.kernel)), "block_k": pl.block_k,
+                "chains_per_cta": pl.chains_per_cta, "hilo": bool(pl.hilo)}
+
+    def blocked_kernel(self, block_k: int, chains: int = 128) -> str:
+        """Name of the kernel the blocked sampler runs at this block size."""
+        return self.plan(chains, "blocked", block_k)["kernel"]
 
     def set_instance_chains(self, counts=None):
         """sais_set_instance_chains: per-instance chain counts (None: one count for all)."""

@@ -13,7 +13,7 @@ from paper_2501_04971_gb300 import sais
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 STRUCTS = [sais.sais_problem_desc, sais.sais_problem_scalars, sais.sais_layout,
            sais.sais_sample_params, sais.sais_solve_params, sais.sais_tuning,
-           sais.sais_solve_result]
+           sais.sais_solve_result, sais.sais_plan]
 
 
 def _c_layout():

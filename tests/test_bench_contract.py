@@ -39,7 +39,7 @@ def test_our_arm_line_small():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     d = _run(["--per-density", "4", "--sweeps", "20", "--steps", "2", "--warmup", "3",
-              "--no-gap", "--no-ragged", "--cpu-seconds", "1"], 900)
+              "--no-gap", "--no-ragged", "--cpu-seconds", "1", "--ksweep-sweeps", "4"], 900)
     assert BASE_KEYS <= set(d) and d["value"] > 0
     r = d["roofline"]
     assert {"bound", "achieved", "peak", "unit", "frac", "traffic"} <= set(r)
@@ -49,6 +49,10 @@ def test_our_arm_line_small():
     assert {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"} <= set(d["e2e"])
     assert d["gpu_launches"] > 0
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])
+    ks = d["blocked_k"]
+    for k in ("16", "32", "64"):
+        assert ks[k]["value"] > 0 and ks[k]["cycles_per_spin_step"] > 0 and ks[k]["kernel"]
+    assert ks["plain"]["value"] > 0
 
 
 @pytest.mark.gpu
@@ -76,3 +80,32 @@ def test_our_arm_optional_sections_small():
         for n in ("100", "200", "300"):
             acc = ps[run]["accuracy_by_size"][n]
             assert 0.0 <= acc["min_accuracy_pct"] <= acc["median_accuracy_pct"] <= 100.0
+
+
+@pytest.mark.gpu
+def test_target_run_small(tmp_path):
+    """The target section end to end at a tiny size: a best-known table written by
+    --make-best-known (every state checked by the oracle), then the warm-started blocked,
+    cold plain and cold blocked runs against it.  Cold plain and cold blocked draw identical
+    samples, so they reach the gap at the same iterations."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    bk = str(tmp_path / "bk.json")
+    common = ["--target-per-density", "1", "--target-iters", "3", "--sweeps", "30",
+              "--best-known", bk]
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--make-best-known",
+                        *common], cwd=ROOT, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stderr[-2000:]
+    table = json.load(open(bk))
+    assert len(table["instances"]) == 4 and all(row["cost"] < 0 for row in table["instances"])
+    d = _run(["--per-density", "2", "--steps", "1", "--warmup", "3", "--no-ragged", "--no-e2e",
+              "--no-plain", "--no-cpu", "--no-ksweep", "--target-train", "40", *common], 900)
+    g = d["gap_1pct"]
+    assert g["instances"] == 4
+    for arm in ("warm_blocked", "cold_plain", "cold_blocked"):
+        assert 0 <= g[arm]["all"]["reached"] <= 4 and g[arm]["iterations_run"] <= 3
+        assert g[arm]["better_than_best_known"] >= 0
+    assert g["cold_plain"]["all"]["reached"] == g["cold_blocked"]["all"]["reached"]
+    assert g["cold_plain"]["median_iterations_reached"] == \
+        g["cold_blocked"]["median_iterations_reached"]

@@ -1,8 +1,11 @@
-"""Blocked sampler (tcgen05 rank-k field update) against the plain sampler and the oracle.
+"""Blocked samplers (tcgen05) against the plain sampler and the oracle.
 
-The rank-k update is exact (integer products and sums below 2^24 in FP32), so the blocked
-sampler must make every decision the plain sampler makes: identical states after every sweep,
-identical costs, constraint values and feasibility, and both identical to the CPU oracle.
+Three kernels: rank-k updates of fields resident in TMEM (N'_pad + K <= 512), block fields from
+a GEMM over the chain states (up to n = 992 items, and K = 32 streamed or hi/lo, K = 64), and a
+CTA pair splitting the fields beyond that.  All are exact (integer products and sums below 2^24
+in FP32), so every blocked sampler must make every decision the plain sampler makes: identical
+states after every sweep, identical costs, constraint values and feasibility, and all identical
+to the CPU oracle.
 """
 import numpy as np
 import pytest
@@ -62,21 +65,33 @@ def _compare(insts, lams, C, T, beta, seed, it, block_k, trace=False, oracle_cha
     prob.close()
 
 
-@pytest.mark.parametrize("block_k", [16, 32])
+@pytest.mark.parametrize("block_k", [16, 32, 64])
 def test_blocked_equals_plain_qkp_n100(block_k):
     _compare([wl.qkp(100, 0.25, 0)], [[0.5]], C=128, T=200, beta=10.0, seed=3, it=1,
              block_k=block_k)
 
 
-def test_blocked_fewer_chains_than_lanes():
-    _compare([wl.qkp(100, 0.25, 1)], [[0.9]], C=64, T=150, beta=10.0, seed=4, it=0, block_k=32)
+@pytest.mark.parametrize("block_k", [32, 64])
+def test_blocked_fewer_chains_than_lanes(block_k):
+    _compare([wl.qkp(100, 0.25, 1)], [[0.9]], C=64, T=150, beta=10.0, seed=4, it=0,
+             block_k=block_k)
 
 
-def test_blocked_ragged_chain_groups_and_spins():
+@pytest.mark.parametrize("block_k", [16, 32, 64])
+def test_blocked_ragged_chain_groups_and_spins(block_k):
     """200 chains (two CTAs, the second ragged) on an instance whose N' is not a multiple of
-    the block size."""
+    the block size, and whose items end inside a block of 32 or 64 (n = 45: 48 state
+    columns)."""
     inst = wl.qkp(45, 0.5, 5)
-    _compare([inst], [[0.4]], C=200, T=120, beta=10.0, seed=5, it=2, block_k=32)
+    _compare([inst], [[0.4]], C=200, T=120, beta=10.0, seed=5, it=2, block_k=block_k)
+
+
+@pytest.mark.parametrize("block_k", [32, 64])
+def test_blocked_wide_blocks_full_size_and_two_constraints(block_k):
+    """K = 32 and 64 at QKP N=300 over 1000 sweeps, and with two constraints."""
+    insts = [wl.qkp(300, 0.5, 60), _with_constraints(wl.qkp(300, 0.75, 61), 2, 61)]
+    _compare(insts, [[1.0], [0.4, 0.9]], C=128, T=1000, beta=10.0, seed=25, it=0,
+             block_k=block_k, oracle_chains=(0, 2))
 
 
 def test_blocked_mixed_batch_sizes():
@@ -129,6 +144,13 @@ def test_blocked_timeout_path_reports_and_recovers():
     prob.close()
 
 
+@pytest.mark.parametrize("block_k", [32, 64])
+def test_blocked_wide_blocks_hilo(block_k):
+    """K = 32 and 64 with the BF16 hi/lo split (pair values up to 10^4)."""
+    _compare([wl.qkp(200, 0.5, 62, profit_max=10000), wl.qkp(90, 0.25, 63)], [[3.0], [0.5]],
+             C=128, T=80, beta=10.0, seed=26, it=1, block_k=block_k, oracle_chains=(0, 2))
+
+
 @pytest.mark.parametrize("case", ["hilo_n100", "hilo_n300", "stream_n400", "hilo_stream_mixed"])
 def test_blocked_streamed_and_hilo(case):
     """W streamed through the shared-memory tile ring, and the BF16 hi/lo split for pair
@@ -150,11 +172,12 @@ def test_blocked_streamed_and_hilo(case):
 
 
 @pytest.mark.parametrize("case", ["n500", "n1000_hilo", "mixed_ragged", "n640_trace", "n1020",
-                                  "n990_tail"])
-def test_pair_sampler_equals_plain_and_oracle(case):
-    """Items beyond one SM's TMEM: the fields split over a CTA pair (cluster of two), flips
-    exchanged through distributed shared memory; identical to the plain sampler and the
-    oracle."""
+                                  "n990_tail", "n1000_mixed_pair", "n700_default_k"])
+def test_large_instances_equal_plain_and_oracle(case):
+    """Large instances: the block-field kernel (one CTA per SM) up to n = 992 items, whose state
+    columns then fill the SM's TMEM; beyond that the fields split over a CTA pair (cluster of
+    two), flips exchanged through distributed shared memory (n1000_hilo, n1020,
+    n1000_mixed_pair).  All identical to the plain sampler and the oracle."""
     if case == "n500":
         _compare([wl.qkp(500, 0.5, 31)], [[1.0]], C=128, T=60, beta=10.0, seed=13, it=1,
                  block_k=16, oracle_chains=(0, 2))
@@ -171,13 +194,21 @@ def test_pair_sampler_equals_plain_and_oracle(case):
     elif case == "n1020":   # halves of 512 columns: the own A operand from shared memory
         _compare([wl.qkp(1020, 0.5, 38)], [[1.2]], C=128, T=12, beta=10.0, seed=17, it=0,
                  block_k=16, oracle_chains=(0, 1))
-    else:                   # n = 990: halves of 496 columns, 16-column tails
+    elif case == "n990_tail":   # n = 990: 496 state columns and 16 fields, all of TMEM
         _compare([wl.qkp(990, 0.75, 39), wl.qkp(250, 0.5, 40)], [[0.6], [1.0]], C=128, T=12,
                  beta=10.0, seed=18, it=1, block_k=16, oracle_chains=(0, 1))
+    elif case == "n1000_mixed_pair":   # CTA pairs: the largest instance exceeds one SM
+        _compare([wl.qkp(1000, 0.5, 44), wl.qkp(200, 0.5, 45)], [[1.0], [0.7]], C=128, T=12,
+                 beta=10.0, seed=27, it=2, block_k=16, oracle_chains=(0, 1))
+    else:                   # the library's block size (K = 32 for the block-field kernel)
+        _compare([wl.qkp(700, 0.5, 46), wl.qkp(460, 0.25, 47)], [[0.9], [0.4]], C=160, T=20,
+                 beta=10.0, seed=28, it=0, block_k=0, oracle_chains=(0, 1))
 
 
-def test_pair_timeout_path_reports_and_recovers():
-    inst = wl.qkp(600, 0.5, 37)
+@pytest.mark.parametrize("n", [600, 1000])
+def test_large_timeout_path_reports_and_recovers(n):
+    """The timeout path of the block-field kernel (n = 600) and of the CTA pair (n = 1000)."""
+    inst = wl.qkp(n, 0.5, 37)
     prob = sais.Problem(inst)
     lam = _lam(prob, [[0.5]])
     prob.sample(lam, 128, 10, 10.0, 1, 0, variant="blocked", debug_wait_polls=1)
@@ -220,29 +251,33 @@ def test_blocked_constraint_counts(case):
                  oracle_chains=(0, 2))
 
 
+@pytest.mark.parametrize("n", [520, 1000])
 @pytest.mark.parametrize("case", ["one_chain", "m8", "three_clusters"])
-def test_pair_sampler_extremes(case):
-    """The CTA-pair sampler with a single valid chain, with 8 constraints (the follower's
-    update reads the coefficients past the first two from global memory), and with 300 chains
-    (three clusters per instance, the last one ragged)."""
+def test_large_instance_extremes(case, n):
+    """One CTA at n = 520 and the CTA pair at n = 1000, each with a single valid chain, with 8
+    constraints (the pair's follower reads the coefficients past the first two from global
+    memory), and with 300 chains (three CTAs or clusters per instance, the last one ragged)."""
     if case == "one_chain":
-        _compare([wl.qkp(520, 0.5, 51)], [[1.0]], C=1, T=20, beta=10.0, seed=22, it=0,
+        _compare([wl.qkp(n, 0.5, 51)], [[1.0]], C=1, T=20, beta=10.0, seed=22, it=0,
                  block_k=16)
     elif case == "m8":
-        inst = _with_constraints(wl.qkp(600, 0.5, 52), 8, 52)
+        inst = _with_constraints(wl.qkp(n, 0.5, 52), 8, 52)
         _compare([inst], [list(np.linspace(0.2, 1.6, 8))], C=128, T=16, beta=10.0, seed=23,
                  it=1, block_k=16, oracle_chains=(0, 1))
     else:
-        _compare([wl.qkp(470, 0.75, 53)], [[0.9]], C=300, T=16, beta=10.0, seed=24, it=2,
+        _compare([wl.qkp(n, 0.75, 53)], [[0.9]], C=300, T=16, beta=10.0, seed=24, it=2,
                  block_k=16, oracle_chains=(290, 2))
 
 
 def test_blocked_unsupported_cases():
-    cases = ([wl.mkp(40, 3, 1)], [wl.qkp(1100, 0.25, 2)], [wl.qkp(600, 0.5, 3), wl.qkp(40, 0.5, 4)])
-    for insts in cases:
+    cases = ([([wl.mkp(40, 3, 1)], 16), ([wl.qkp(1100, 0.25, 2)], 16),
+              ([wl.qkp(1000, 0.5, 3), wl.qkp(40, 0.5, 4)], 16),
+              ([_with_constraints(wl.qkp(100, 0.5, 5), 3, 5)], 64),
+              ([wl.qkp(1000, 0.5, 6)], 64)])
+    for insts, k in cases:
         prob = sais.Problem(insts)
         lam = torch.zeros(prob.count * prob.m_stride, device="cuda:0")
         with pytest.raises(sais.SaisError) as e:
-            prob.sample(lam, 128, 10, 10.0, 1, 0, variant="blocked")
+            prob.sample(lam, 128, 10, 10.0, 1, 0, variant="blocked", block_k=k)
         assert e.value.status == sais.SAIS_EUNSUPPORTED
         prob.close()
