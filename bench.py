@@ -75,6 +75,16 @@ def parse():
     ap.add_argument("--ws-eval", type=int, default=64)
     ap.add_argument("--ws-epochs", type=int, default=200)
     ap.add_argument("--ragged-iters", type=int, default=3)
+    ap.add_argument("--no-target", action="store_true",
+                    help="skip the target run (warm-started blocked vs cold plain to a 1%% gap)")
+    ap.add_argument("--target-per-density", type=int, default=38)
+    ap.add_argument("--target-iters", type=int, default=40)
+    ap.add_argument("--target-train", type=int, default=3000)
+    ap.add_argument("--best-known", default=os.path.join(ROOT, "best_known_qkp300.json"))
+    ap.add_argument("--make-best-known", action="store_true",
+                    help="compute the best-known table of the target instances and exit")
+    ap.add_argument("--no-ksweep", action="store_true")
+    ap.add_argument("--ksweep-sweeps", type=int, default=200)
     ap.add_argument("--ragged-tune-sweeps", type=int, default=50)
     return ap.parse_args()
 
@@ -253,71 +263,240 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------
-# wall-clock to a 1 % gap (QKP N=300, d=0.5), blocked vs plain
+# the target run: wall-clock to a 1 % gap on QKP N=300, warm-started blocked vs cold plain
 # ------------------------------------------------------------------------------------------
 
-def gap_measurement(a, sais, torch, variants):
-    """Wall-clock to a 1 % gap on QKP N=300 at each density (`gap_instances` instances per
-    density, one batch).  Best-known profit per instance = best feasible sample of runs of the
-    first variant (4 seeds x `gap_iters` iterations; uncertified).  Then, per variant, Algorithm
-    1 from lambda = 0 with a fresh seed, one iteration at a time through the C-ABI; the time to a
-    1 % gap of an instance is the device time (CUDA events) of the iterations until its best
-    feasible profit reaches 0.99 x best-known.  Both variants draw identical samples, so they
-    need the same number of iterations; their times differ by the per-iteration cost."""
-    from paper_2501_04971_gb300 import workloads as wl
-    per = a.gap_instances
-    insts = [wl.qkp(300, d, 5000 + 100 * q + i) for q, d in enumerate(DENSITIES)
-             for i in range(per)]
-    dens = np.repeat(np.array(DENSITIES), per)
-    prob = sais.Problem(insts)
-    C, T, beta, eta = a.chains, a.sweeps, a.beta_max, a.gap_eta
-    best_known = np.full(prob.count, np.iinfo(np.int64).max, np.int64)
-    ref_variant = variants[0]
-    for seed in range(4):
-        r = prob.solve(a.gap_iters, C, T, beta, eta, 777 + seed, variant=ref_variant)
-        best_known = np.minimum(best_known, r["best_cost"])
-    out = {"instances": prob.count, "workload": "QKP N=300, d in {0.25,0.5,0.75,1} x %d, %d "
-           "chains x %d sweeps per iteration, beta_max %g, P = 2dN, eta %g (normalised units)"
-           % (per, C, T, beta, eta),
-           "best_known": "best of 4 seeds x %d iterations (%s), uncertified"
-           % (a.gap_iters, ref_variant)}
-    stream = torch.cuda.current_stream()
-    for v in variants:
-        lam = torch.zeros(prob.count * prob.m_stride, device="cuda")
-        o = prob.alloc_outputs(C)
-        best = prob.alloc_best()
-        reached = np.full(prob.count, np.nan)
-        t_acc = 0.0
-        for k in range(a.gap_iters):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            prob.sample(lam, C, T, beta, 4242, k, variant=v, out=o, stream=stream)
-            prob.track_best(o, C, k, best, stream=stream)
-            prob.update_lambda(o["g"], C, eta, True, lam, stream=stream)
-            e1.record(stream)
-            bc = best["best_cost"].cpu().numpy()     # synchronises
-            t_acc += e0.elapsed_time(e1) / 1e3
-            # costs are negative profits: reach when -bc >= 0.99 * (-best_known)
-            hit = (bc != np.iinfo(np.int64).max) & (-bc >= 0.99 * (-best_known))
-            reached[np.isnan(reached) & hit] = t_acc
-            if not np.isnan(reached).any():
-                break
+INT64_MAX = np.iinfo(np.int64).max
 
-        def stats(mask):
-            rr = reached[mask]
-            ok = ~np.isnan(rr)
-            return {"reached": int(ok.sum()), "of": int(mask.sum()),
-                    "median_s": float(np.median(rr[ok])) if ok.any() else None,
-                    "p90_s": float(np.percentile(rr[ok], 90)) if ok.any() else None}
-        out[v] = {"all": stats(np.ones(prob.count, bool)), "iterations_run": k + 1,
-                  "by_density": {str(d): stats(dens == d) for d in DENSITIES}}
-    if all(out.get(v, {}).get("all", {}).get("median_s") for v in ("blocked", "plain")):
-        out["speedup_median"] = out["plain"]["all"]["median_s"] / out["blocked"]["all"]["median_s"]
-        d5 = [out[v]["by_density"]["0.5"]["median_s"] for v in ("plain", "blocked")]
-        if all(d5):
-            out["speedup_median_d0.5"] = d5[0] / d5[1]
+
+def target_instances(per: int):
+    """QKP N=300 at the four densities, `per` each (seeds 5000 + 100 q + i)."""
+    from paper_2501_04971_gb300 import workloads as wl
+    return [wl.qkp(300, d, 5000 + 100 * q + i) for q, d in enumerate(DENSITIES)
+            for i in range(per)]
+
+
+def target_budget(a):
+    return dict(C=a.chains, T=a.sweeps, beta=a.beta_max, eta=a.gap_eta, K=a.target_iters)
+
+
+def oracle_check(inst, x_bits: np.ndarray, nspins: int):
+    """(cost, feasible) of a bit-packed state by the oracle, in int64 (Sec. IV-A)."""
+    import oracle
+    from paper_2501_04971_gb300 import sais
+    p = oracle.Problem(inst.n, inst.m, inst.W, inst.h, inst.A, inst.b, alpha=inst.alpha,
+                       density=inst.density)
+    x = sais.unpack_bits(np.asarray(x_bits, np.uint32)[None, :], nspins)[0]
+    return p.cost(x), p.feasible(x)
+
+
+def make_best_known(a, sais, torch):
+    """Best-known profit of every target instance: the best feasible sample of 16 seeds x 16 x
+    the target budget (target_iters iterations) of Algorithm 1 from lambda = 0, each kept state
+    checked by the oracle in int64.  The runs use the blocked sampler, whose samples are those
+    of the plain sampler bit for bit.  Not certified optimal."""
+    insts = target_instances(a.target_per_density)
+    prob = sais.Problem(insts)
+    b = target_budget(a)
+    best = np.full(prob.count, INT64_MAX, np.int64)
+    bx = np.zeros((prob.count, prob.words), np.uint32)
+    t0 = time.perf_counter()
+    for seed in range(16):
+        r = prob.solve(16 * b["K"], b["C"], b["T"], b["beta"], b["eta"], 31000 + seed,
+                       variant="blocked", use_graph=True)
+        better = r["best_cost"] < best
+        best[better] = r["best_cost"][better]
+        bx[better] = np.asarray(r["best_x"]).reshape(prob.count, -1)[better].view(np.uint32)
+        print(f"seed {seed}: {int(better.sum())} improved, {time.perf_counter() - t0:.0f} s",
+              file=sys.stderr, flush=True)
+    rows = []
+    for j, inst in enumerate(insts):
+        row = {"density": inst.density,
+               "seed": 5000 + 100 * DENSITIES.index(inst.density) + j % a.target_per_density,
+               "cost": None, "x": None}
+        if best[j] != INT64_MAX:   # else no feasible sample in the whole ensemble
+            cost, feas = oracle_check(inst, bx[j], prob.scalars[j].n_spins)
+            assert feas and cost == best[j], (j, cost, best[j])
+            row["cost"], row["x"] = int(best[j]), "".join(f"{w:08x}" for w in bx[j])
+        rows.append(row)
+    out = {"workload": "QKP N=300, d in {0.25,0.5,0.75,1} x %d (seeds 5000 + 100 q + i)"
+                       % a.target_per_density,
+           "recipe": "best feasible sample of 16 seeds x %d iterations (16 x the target budget) "
+                     "of Algorithm 1 from lambda = 0, %d chains x %d sweeps, beta_max %g, eta "
+                     "%g, P = 2dN; blocked sampler (its samples are the plain sampler's); every "
+                     "state checked by the oracle in int64; not certified optimal"
+                     % (16 * b["K"], b["C"], b["T"], b["beta"], b["eta"]),
+           "seconds": time.perf_counter() - t0, "instances": rows}
+    prob.close()
+    with open(a.best_known, "w") as f:
+        json.dump(out, f, indent=0)
+    print(f"wrote {a.best_known}", file=sys.stderr)
+
+
+def load_best_known(a, insts, nspins):
+    """The stored best-known costs, each state re-checked by the oracle (int64); INT64_MAX where
+    the ensemble found no feasible sample."""
+    d = json.load(open(a.best_known))
+    rows = d["instances"]
+    assert len(rows) == len(insts), "best-known table is for another instance count"
+    best = np.full(len(insts), INT64_MAX, np.int64)
+    for j, (inst, row) in enumerate(zip(insts, rows)):
+        if row["cost"] is None:
+            continue
+        x = np.array([int(row["x"][8 * w:8 * w + 8], 16) for w in range(len(row["x"]) // 8)],
+                     np.uint32)
+        cost, feas = oracle_check(inst, x, nspins[j])
+        assert feas and cost == row["cost"], f"best-known row {j} fails the oracle check"
+        best[j] = row["cost"]
+    return best, d["recipe"]
+
+
+def solve_to_gap(prob, sais, torch, variant, lam0, K, b, best_known, t0):
+    """Algorithm 1 through sais_solve, one iteration per call resumed from the previous call's
+    multipliers (iter0 = k), pinned host buffers.  Per instance: the host wall-clock from t0
+    (taken before the first call, or before the warm start) until its best feasible profit
+    reaches 0.99 x best-known, and the iteration; nan where never within K iterations."""
+    cnt, M, Wd = prob.count, prob.m_stride, prob.words
+    lam_h = torch.zeros(cnt * M, dtype=torch.float32).pin_memory()
+    lam_h.copy_(lam0)
+    pinned = {"best_cost": torch.zeros(cnt, dtype=torch.int64).pin_memory(),
+              "lambda_final": torch.zeros(cnt * M, dtype=torch.float32).pin_memory()}
+    prm = sais.sais_solve_params()
+    prm.iters, prm.chains, prm.sweeps, prm.beta_max = 1, b["C"], b["T"], b["beta"]
+    prm.eta, prm.seed, prm.project_nonneg = b["eta"], 4242, 1
+    prm.variant = sais._VARIANTS[variant]
+    prm.lambda0 = sais._P(lam_h.data_ptr())
+    res = sais.sais_solve_result()
+    for k_, v_ in pinned.items():
+        setattr(res, k_, sais._P(v_.data_ptr()))
+    sp = sais._P(torch.cuda.current_stream().cuda_stream)
+    best = np.full(cnt, INT64_MAX, np.int64)
+    reach_s = np.full(cnt, np.nan)
+    reach_k = np.full(cnt, np.nan)
+    for k in range(K):
+        prm.iter0 = k
+        sais.sais_solve(prob.handle, prm, res, sp)
+        t = time.perf_counter() - t0
+        lam_h.copy_(pinned["lambda_final"])
+        best = np.minimum(best, pinned["best_cost"].numpy())
+        hit = ((best != INT64_MAX) & (best_known != INT64_MAX) & (-best >= 0.99 * (-best_known))
+               & np.isnan(reach_s))
+        reach_s[hit] = t
+        reach_k[hit] = k + 1
+        if not np.isnan(reach_s[best_known != INT64_MAX]).any():
+            break
+    return reach_s, reach_k, best, k + 1
+
+
+def target_measurement(a, sais, torch):
+    """The target comparison: wall-clock from sais_solve entry to a 1 % gap against the stored
+    best-known, on QKP N=300 at the four densities (`target_per_density` each; one batch that
+    fills the GPU), for (1) the BF16 blocked sampler started from the learned multipliers
+    (network trained in this run on `target_train` instances by the project's kernels), (2) the
+    plain FP32 sampler from lambda = 0 as in Algorithm 1, (3) the blocked sampler from lambda =
+    0.  Unreached instances count as never (medians over all instances, infinite where
+    unreached)."""
+    from paper_2501_04971_gb300 import warmstart as ws
+    insts = target_instances(a.target_per_density)
+    prob = sais.Problem(insts)
+    nsp = [s.n_spins for s in prob.scalars]
+    best_known, recipe = load_best_known(a, insts, nsp)
+    b = target_budget(a)
+    dens = np.repeat(np.array(DENSITIES), a.target_per_density)
+    # the warm-start network, trained here
+    t1 = time.perf_counter()
+    tr = ws.training_instances(a.target_train)
+    bud = ws.SolveBudget(iters=30, chains=128, sweeps=200, beta_max=a.beta_max, eta=a.gap_eta)
+    X, y, t_lab, _ = ws.label(tr, bud)
+    net, losses, t_train = ws.train(X, y, epochs=a.ws_epochs)
+    t_ws = time.perf_counter() - t1
+    known = best_known != INT64_MAX
+    out = {"instances": prob.count, "best_known": recipe,
+           "instances_without_best_known": int((~known).sum()),
+           "workload": "QKP N=300, d in {0.25,0.5,0.75,1} x %d, %d chains x %d sweeps per "
+                       "iteration, beta_max %g, P = 2dN, eta %g (normalised units), at most %d "
+                       "iterations" % (a.target_per_density, b["C"], b["T"], b["beta"], b["eta"],
+                                       b["K"]),
+           "time": "host wall-clock from the first sais_solve entry (warm: from the warm-start "
+                   "call), one iteration per call, resumed through lambda0 / iter0",
+           "warm_start_net": {"train_instances": len(tr), "rows": int(X.shape[0]),
+                              "label_seconds": t_lab, "train_device_seconds": t_train,
+                              "seconds_total": t_ws, "loss_first_last": [losses[0], losses[-1]]}}
+
+    def stats(r, mask):
+        rr = np.where(np.isnan(r[mask]), np.inf, r[mask])
+        ok = np.isfinite(rr)
+        med = float(np.median(rr)) if ok.any() else None
+        p90 = float(np.percentile(rr, 90)) if ok.any() else None
+        return {"reached": int(ok.sum()), "of": int(mask.sum()),
+                "median_s": med if med is not None and np.isfinite(med) else None,
+                "p90_s": p90 if p90 is not None and np.isfinite(p90) else None,
+                "median_s_reached": float(np.median(rr[ok])) if ok.any() else None}
+
+    arms = (("warm_blocked", "blocked", True), ("cold_plain", "plain", False),
+            ("cold_blocked", "blocked", False))
+    reach = {}
+    for name, variant, warm in arms:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lam = torch.zeros(prob.count * prob.m_stride, dtype=torch.float32, device="cuda")
+        if warm:
+            prob.warm_start(net, lam)
+        lam0 = lam.cpu()
+        rs, rk, best, kk = solve_to_gap(prob, sais, torch, variant, lam0, b["K"], b, best_known, t0)
+        reach[name] = rs
+        out[name] = {"variant": variant, "lambda0": "learned" if warm else "zero",
+                     "iterations_run": kk, "all": stats(rs, known),
+                     "median_iterations_reached": float(np.nanmedian(rk)) if (~np.isnan(rk)).any()
+                     else None,
+                     "better_than_best_known": int((best < best_known).sum()),
+                     "feasible_where_none_known": int(((best != INT64_MAX) & ~known).sum()),
+                     "by_density": {str(d): stats(rs, (dens == d) & known) for d in DENSITIES}}
+    w, c = out["warm_blocked"]["all"], out["cold_plain"]["all"]
+    if w["median_s"] and c["median_s"]:
+        out["speedup_median_cold_plain_over_warm_blocked"] = c["median_s"] / w["median_s"]
+    both = ~np.isnan(reach["warm_blocked"]) & ~np.isnan(reach["cold_plain"])
+    if both.any():
+        out["per_instance_speedup_median_both_reached"] = float(
+            np.median(reach["cold_plain"][both] / reach["warm_blocked"][both]))
+    net.close()
     prob.close()
     return out
+
+
+def ksweep_measurement(a, sais, torch, insts, sm_mhz):
+    """The blocked sampler at block sizes K = 16, 32, 64 on the bench workload (`ksweep_sweeps`
+    sweeps per launch, one timed launch after a warm-up): spin updates/s and SM cycles per
+    spin-step (one spin of one 128-chain CTA), which kernel ran, and the plain sampler beside."""
+    prob = sais.Problem(insts)
+    C, T = a.chains, a.ksweep_sweeps
+    lam = torch.zeros(prob.count * prob.m_stride, device="cuda")
+    out = prob.alloc_outputs(C)
+    nsp = np.array([s.n_spins for s in prob.scalars])
+    upd = int(nsp.sum()) * C * T
+    res = {"sweeps": T, "sm_mhz": sm_mhz}
+    for k in (16, 32, 64, "plain"):
+        kw = dict(variant="plain") if k == "plain" else dict(variant="blocked", block_k=k)
+        try:
+            prob.sample(lam, C, T, a.beta_max, 1, 0, out=out, **kw)
+            torch.cuda.synchronize()
+        except sais.SaisError as e:
+            res[str(k)] = {"unsupported": str(e)}
+            continue
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        prob.sample(lam, C, T, a.beta_max, 1, 1, out=out, **kw)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        row = {"value": upd / (ms / 1e3), "unit": UNIT, "ms": ms}
+        if k != "plain":
+            steps = int(sum(-(-int(n) // k) * k for n in nsp)) * (-(-C // 128)) * T
+            row["cycles_per_spin_step"] = ms / 1e3 * sm_mhz * 1e6 * SM_COUNT / steps
+            row["kernel"] = prob.blocked_kernel(k)
+        res[str(k)] = row
+    prob.close()
+    return res
 
 
 def penalty_measurement(a, sais, torch):
@@ -464,7 +643,9 @@ def ragged_measurement(a, sais, torch):
     for g in range(tune["groups"]):
         groups.append({"variant": names[tune["variant"][g]], "instances": tune["size"][g],
                        "block_k": tune["block_k"][g], "chains_per_cta": tune["chains_per_cta"][g],
-                       "spin_updates_per_s": tune["spin_updates"][g] / (tune["ms"][g] / 1e3)})
+                       "spin_updates_per_s": tune["spin_updates"][g] / (tune["ms"][g] / 1e3),
+                       "tune_launch_ms": tune["ms"][g],
+                       "tune_launch_spin_updates": int(tune["spin_updates"][g])})
     prob.solve(1, C, a.sweeps, a.beta_max, a.gap_eta, 99, variant="auto", use_graph=True)
     r = prob.solve(a.ragged_iters, C, a.sweeps, a.beta_max, a.gap_eta, 100, variant="auto",
                    use_graph=True)
@@ -573,6 +754,8 @@ def main():
         dist.barrier()
     from paper_2501_04971_gb300 import sais
 
+    if a.make_best_known:
+        return make_best_known(a, sais, torch)
     insts = workload(a.per_density, rank)
     prob = sais.Problem(insts, device=local)
     nspins = np.array([s.n_spins for s in prob.scalars], dtype=np.int64)
@@ -710,10 +893,12 @@ def main():
         pval = upd_all / (pms / 1e3)
         plain_cmp = {"value": pval, "unit": UNIT, "sampler_ms_per_step": pms,
                      "blocked_over_plain": value / pval}
+    ksweep = None
+    if not a.no_ksweep and world == 1 and variant == "blocked":
+        ksweep = ksweep_measurement(a, sais, torch, insts, clk.summary().get("sm_mhz") or SM_MAX_MHZ)
     gap = None
-    if not a.no_gap and world == 1:
-        gap = gap_measurement(a, sais, torch, ["blocked", "plain"] if variant == "blocked"
-                              else ["plain"])
+    if not (a.no_target or a.no_gap) and world == 1 and os.path.exists(a.best_known):
+        gap = target_measurement(a, sais, torch)
     ragged = None
     if not a.no_ragged and world == 1:
         ragged = ragged_measurement(a, sais, torch)
@@ -748,7 +933,8 @@ def main():
                              f"{prob.count * 2 * 2 * 320 * 320 / 1e6:.0f} MB)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": 3 * a.steps, "clocks": clk.summary(),
-            "updates_per_step": upd_step, "plain": plain_cmp, "gap_1pct": gap,
+            "updates_per_step": upd_step, "plain": plain_cmp, "blocked_k": ksweep,
+            "gap_1pct": gap,
             "ragged": ragged}
     if pen is not None:
         line["penalty_vs_saim"] = pen

@@ -570,7 +570,7 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
     // Pool layout: [InstDev x count] then per instance W, Wbf(, Wbf_lo), hF, acol, D, asum, b,
     // slack_off, each 256-byte aligned.
     struct Off {
-        size_t W, Wbf, Wlo, Wd, Wg, Wglo, Wd32, Wd64, hF, acol, D, asum, spinc, b, so;
+        size_t W, Wbf, Wlo, Wd, Wg, Wglo, Wd32, Wd64, hF, acol, acf, D, asum, spinc, b, so;
     };
     int32_t feat_rows = 0;
     for (const HostInst &h : p->host) feat_rows += h.m;
@@ -613,6 +613,8 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
         cur = align_up(cur + (size_t)h.npad * 4, 256);
         o.acol = cur;
         cur = align_up(cur + h.acol.size() * 4, 256);
+        o.acf = cur;
+        cur = align_up(cur + (size_t)h.npad * ((h.m + 3) / 4 * 4) * 4, 256);
         o.D = cur;
         cur = align_up(cur + h.D.size() * 4, 256);
         o.asum = cur;
@@ -712,6 +714,15 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
         }
         std::memcpy(stage.data() + o.hF, h.hF.data(), h.hF.size() * 4);
         std::memcpy(stage.data() + o.acol, h.acol.data(), h.acol.size() * 4);
+        {
+            const int m4 = (h.m + 3) / 4 * 4;
+            float *af = reinterpret_cast<float *>(stage.data() + o.acf);
+            for (int32_t i = 0; i < h.npad; ++i)
+                for (int32_t k = 0; k < h.m; ++k)
+                    af[(size_t)i * m4 + k] = (float)h.acol[(size_t)i * h.m + k];
+            r.acf = reinterpret_cast<const float *>(base + o.acf);
+            r.m4 = m4;
+        }
         std::memcpy(stage.data() + o.D, h.D.data(), h.D.size() * 4);
         std::memcpy(stage.data() + o.asum, h.asum.data(), h.asum.size() * 4);
         std::memcpy(stage.data() + o.spinc, h.spinc.data(), h.spinc.size() * 4);

@@ -45,6 +45,9 @@ struct InstDev {
     const int16_t *W;   // npad x npad row-major pair values, zero padded (NULL if !has_w)
     const float *hF;    // npad: h_i as FP32 (exact integers), 0 for slack/padding
     const int32_t *acol;   // npad x m, spin-major: a_ki of A_ext (zero past N')
+    const float *acf;      // npad x m4, spin-major: a_ki as FP32 (exact), rows padded to
+                           // m4 = m rounded up to 4 with zeros, 16-byte aligned (float4 loads)
+    int32_t m4;
     const float *D;        // npad: fl(P sigma_g^2 sum_k a_ki^2) (zero past N')
     const float *asum;     // npad: sum_k a_ki, exact in FP32 (zero past N')
     const float4 *spinc;   // npad: {a_0i (int bits), D_i, sum_k a_ki, a_1i (int bits)}

@@ -32,13 +32,14 @@ __global__ void __launch_bounds__(128) plain_sampler_kernel(SampleArgs a) {
     const int j = a.work ? a.work[2 * blockIdx.x] : (int)blockIdx.y;
     const int grp = a.work ? a.work[2 * blockIdx.x + 1] : (int)blockIdx.x;
     const InstDev *__restrict__ ip = a.inst + j;
-    const int m = ip->m, nprime = ip->nprime, npad = ip->npad, words = ip->words;
+    const int n = ip->n, m = ip->m, nprime = ip->nprime, npad = ip->npad, words = ip->words;
+    const int m4 = ip->m4;
     const bool has_w = ip->has_w != 0;
     const float sf = ip->sigma_f, sg = ip->sigma_g, kappa = ip->kappa;
     const double psg2 = ip->psg2;
     const int16_t *__restrict__ W = ip->W;
     const float *__restrict__ hF = ip->hF;
-    const int32_t *__restrict__ acol = ip->acol;
+    const float *__restrict__ acf = ip->acf;
     const float *__restrict__ Dv = ip->D;
     const float *__restrict__ asum = ip->asum;
 
@@ -54,19 +55,20 @@ __global__ void __launch_bounds__(128) plain_sampler_kernel(SampleArgs a) {
     uint32_t *xs = reinterpret_cast<uint32_t *>(smem_raw + (has_w ? (size_t)npad * cpb * 4 : 0));
 
     const float *lam = a.lambda + (size_t)j * a.m_stride;
-    int32_t g[MC];
-    float c[MC], cA[MC];
+    // Constraint values g_k as FP32 (exact integers: |g| < 2^24, checked at creation) and
+    // c_k = 2 P sigma_g^2 g_k + sigma_g lambda_k.
+    float gf[MC], c[MC], cA[MC];
     float Mmax = 0.f;
 #pragma unroll
     for (int k = 0; k < MC; ++k) {
         if (k < m) {
             cA[k] = __double2float_rn((double)sg * (double)lam[k]);
-            g[k] = -ip->b[k];
-            c[k] = fmaf(kappa, (float)g[k], cA[k]);
-            Mmax = fmaxf(Mmax, fmaf(fabsf(kappa), fabsf((float)g[k]), fabsf(cA[k])));
+            gf[k] = (float)(-ip->b[k]);
+            c[k] = fmaf(kappa, gf[k], cA[k]);
+            Mmax = fmaxf(Mmax, fmaf(fabsf(kappa), fabsf(gf[k]), fabsf(cA[k])));
         } else {
             cA[k] = 0.f;
-            g[k] = 0;
+            gf[k] = 0.f;
             c[k] = 0.f;
         }
     }
@@ -85,19 +87,35 @@ __global__ void __launch_bounds__(128) plain_sampler_kernel(SampleArgs a) {
         const float hb = 0.5f * beta;
         const float ez = hb * errk;
         uint32_t xw = 0u;
-        for (int i0 = 0; i0 < nprime; i0 += 4) {
-            const uint4 rw = philox4x32_10(
+        uint4 rw = make_uint4(0u, 0u, 0u, 0u);   // noise words of spins 4 (i/4) .. 4 (i/4) + 3
+        // Items, spins 0..n-1: objective field and every constraint.
+        for (int i0 = 0; i0 < n; i0 += 4) {
+            rw = philox4x32_10(
                 make_uint4((uint32_t)(i0 >> 2), (uint32_t)t, (uint32_t)chain, iter), key0, key1);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int i = i0 + q;
-                if (i >= nprime) break;
+                if (i >= n) break;
                 if ((i & 31) == 0) xw = xs[(i >> 5) * cpb + tid];
-                const float rho = rho_of_word(word_of(rw, q));
                 const float theta = theta_of_word(word_of(rw, q));
                 const float Fi = has_w ? Fs[i * cpb + tid] : __ldg(hF + i);
                 const int xi = (xw >> (i & 31)) & 1;
-                int32_t ak[MC];
+                // Row i of A_ext as FP32, four coefficients per load.
+                float akf[MC];
+                if constexpr (MC >= 4) {
+                    const float4 *ap = reinterpret_cast<const float4 *>(acf + (size_t)i * m4);
+#pragma unroll
+                    for (int k4 = 0; k4 < MC / 4; ++k4) {
+                        const float4 v = 4 * k4 < m ? __ldg(ap + k4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        akf[4 * k4] = v.x;
+                        akf[4 * k4 + 1] = v.y;
+                        akf[4 * k4 + 2] = v.z;
+                        akf[4 * k4 + 3] = v.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < MC; ++k) akf[k] = k < m ? __ldg(acf + (size_t)i * m4 + k) : 0.f;
+                }
                 float acc = sf * Fi;
                 const float tabs = fabsf(acc);
                 if constexpr (MC >= 16) {
@@ -107,17 +125,13 @@ __global__ void __launch_bounds__(128) plain_sampler_kernel(SampleArgs a) {
                     float p1 = 0.f, p2 = 0.f, p3 = 0.f;
 #pragma unroll
                     for (int k = 0; k < MC; ++k) {
-                        ak[k] = (k < m) ? __ldg(acol + (size_t)i * m + k) : 0;
                         float &pk = (k & 3) == 0 ? acc : ((k & 3) == 1 ? p1 : ((k & 3) == 2 ? p2 : p3));
-                        pk = fmaf(-(float)ak[k], c[k], pk);
+                        pk = fmaf(-akf[k], c[k], pk);
                     }
                     acc = (acc + p1) + (p2 + p3);
                 } else {
 #pragma unroll
-                    for (int k = 0; k < MC; ++k) {
-                        ak[k] = (k < m) ? __ldg(acol + (size_t)i * m + k) : 0;
-                        acc = fmaf(-(float)ak[k], c[k], acc);
-                    }
+                    for (int k = 0; k < MC; ++k) acc = fmaf(-akf[k], c[k], acc);
                 }
                 const float Di = __ldg(Dv + i);
                 acc = fmaf(xi ? 1.f : -1.f, Di, acc);
@@ -126,21 +140,30 @@ __global__ void __launch_bounds__(128) plain_sampler_kernel(SampleArgs a) {
                 const float bound =
                     ez * (tabs + __ldg(asum + i) * Mmax + Di) + kThetaRelErr * fabsf(theta) + kThetaAbsErr;
                 int xn;
-                if (fabsf(y) > bound)
+                if (fabsf(y) > bound) {
                     xn = y > 0.f;
-                else
-                    xn = decide_exact<MC>(Fi, xi, ak, g, lam, m, sf, sg, psg2, beta, rho);
+                } else {
+                    int32_t ak[MC], g[MC];
+#pragma unroll
+                    for (int k = 0; k < MC; ++k) {
+                        ak[k] = (int32_t)akf[k];
+                        g[k] = (int32_t)gf[k];
+                    }
+                    xn = decide_exact<MC>(Fi, xi, ak, g, lam, m, sf, sg, psg2, beta,
+                                          rho_of_word(word_of(rw, q)));
+                }
                 const int d = xn - xi;
                 if (d != 0) {
+                    const float df = (float)d;
                     xw ^= 1u << (i & 31);
                     ccur -= (long long)(d * __float2int_rz(Fi));   // |F| < 2^24: exact
                     Mmax = 0.f;
 #pragma unroll
                     for (int k = 0; k < MC; ++k) {
                         if (k < m) {
-                            g[k] += ak[k] * d;
-                            c[k] = fmaf(kappa, (float)g[k], cA[k]);
-                            Mmax = fmaxf(Mmax, fmaf(fabsf(kappa), fabsf((float)g[k]), fabsf(cA[k])));
+                            gf[k] = fmaf(akf[k], df, gf[k]);   // exact integers
+                            c[k] = fmaf(kappa, gf[k], cA[k]);
+                            Mmax = fmaxf(Mmax, fmaf(fabsf(kappa), fabsf(gf[k]), fabsf(cA[k])));
                         }
                     }
                 }
@@ -165,6 +188,56 @@ __global__ void __launch_bounds__(128) plain_sampler_kernel(SampleArgs a) {
                 if ((i & 31) == 31 || i == nprime - 1) xs[(i >> 5) * cpb + tid] = xw;
             }
         }
+        // Slack spins of constraint k: spins o_k .. o_{k+1} - 1, bit q with coefficient 2^q in
+        // row k of A_ext only (Sec. IV-A).  No pair values and h = 0, so F_i = 0: the field is
+        // 2 I_i = -2^q c_k - (1 - 2 x_i) D_i, and a flip changes g_k alone.  Mmax then stays an
+        // upper bound of max_k M_k (M_k of the one changed constraint folded in), which keeps the
+        // error bound valid; the next item flip recomputes it.
+#pragma unroll
+        for (int k = 0; k < MC; ++k) {
+            if (k >= m) break;
+            const int o0 = ip->slack_off[k], o1 = ip->slack_off[k + 1];
+            float coef = 1.f;
+            for (int i = o0; i < o1; ++i, coef *= 2.f) {
+                if ((i & 3) == 0)
+                    rw = philox4x32_10(
+                        make_uint4((uint32_t)(i >> 2), (uint32_t)t, (uint32_t)chain, iter), key0,
+                        key1);
+                if ((i & 31) == 0) xw = xs[(i >> 5) * cpb + tid];
+                const uint32_t word = word_of(rw, i & 3);
+                const float theta = theta_of_word(word);
+                const int xi = (xw >> (i & 31)) & 1;
+                float acc = sf * 0.f;
+                acc = fmaf(-coef, c[k], acc);
+                const float Di = __ldg(Dv + i);
+                acc = fmaf(xi ? 1.f : -1.f, Di, acc);
+                const float z = hb * acc;
+                const float y = z + theta;
+                const float bound =
+                    ez * (coef * Mmax + Di) + kThetaRelErr * fabsf(theta) + kThetaAbsErr;
+                int xn;
+                if (fabsf(y) > bound) {
+                    xn = y > 0.f;
+                } else {
+                    int32_t ak[MC], g[MC];
+#pragma unroll
+                    for (int kk = 0; kk < MC; ++kk) {
+                        ak[kk] = kk == k ? (int32_t)coef : 0;
+                        g[kk] = (int32_t)gf[kk];
+                    }
+                    xn = decide_exact<MC>(0.f, xi, ak, g, lam, m, sf, sg, psg2, beta,
+                                          rho_of_word(word));
+                }
+                const int d = xn - xi;
+                if (d != 0) {
+                    xw ^= 1u << (i & 31);
+                    gf[k] = fmaf(coef, (float)d, gf[k]);   // exact integers
+                    c[k] = fmaf(kappa, gf[k], cA[k]);
+                    Mmax = fmaxf(Mmax, fmaf(fabsf(kappa), fabsf(gf[k]), fabsf(cA[k])));
+                }
+                if ((i & 31) == 31 || i == nprime - 1) xs[(i >> 5) * cpb + tid] = xw;
+            }
+        }
         if (track) {
             bool feas = true;
 #pragma unroll
@@ -174,7 +247,7 @@ __global__ void __launch_bounds__(128) plain_sampler_kernel(SampleArgs a) {
                     long long sv = 0;
                     for (int s = o0; s < o1; ++s)
                         if ((xs[(s >> 5) * cpb + tid] >> (s & 31)) & 1u) sv += 1LL << (s - o0);
-                    if ((long long)g[k] - sv > (long long)ip->fmargin[k]) feas = false;
+                    if ((long long)gf[k] - sv > (long long)ip->fmargin[k]) feas = false;
                 }
             }
             if (feas) {
@@ -220,8 +293,8 @@ __global__ void __launch_bounds__(128) plain_sampler_kernel(SampleArgs a) {
             long long sv = 0;
             for (int s = o0; s < o1; ++s)
                 if ((xs[(s >> 5) * cpb + tid] >> (s & 31)) & 1u) sv += 1LL << (s - o0);
-            if ((long long)g[k] - sv > (long long)ip->fmargin[k]) feas = false;
-            a.g[cidx * a.m_stride + k] = g[k];
+            if ((long long)gf[k] - sv > (long long)ip->fmargin[k]) feas = false;
+            a.g[cidx * a.m_stride + k] = (long long)gf[k];
         }
     }
     for (int k = m; k < a.m_stride; ++k) a.g[cidx * a.m_stride + k] = 0;
