@@ -451,6 +451,25 @@ SAIS_API sais_status sais_mlp_status(sais_mlp *m);
 SAIS_API sais_status sais_warm_start(sais_problem *p, const sais_mlp *m, float *lambda,
                                      void *stream);
 
+/* ---- Device memory of the library's own buffers -------------------------------------------
+ * The library allocates device memory for problem data (sais_create_*), the per-call scratch of
+ * sais_solve and sais_autotune, SAIS_AUTO work lists, per-instance chain counts and the
+ * warm-start network's buffers.  By default these come from cudaMalloc / cudaFree.  A caller
+ * that manages device memory itself (a memory pool, a framework's caching allocator, a budget
+ * that must account for every byte) installs its own pair here; the paper has no counterpart.
+ *   alloc(bytes, device, ctx) returns device memory of `device` (the current device when it is
+ *     called), at least 256-byte aligned, or NULL on failure (the calling entry point then
+ *     returns SAIS_ENOMEM);
+ *   free(ptr, bytes, device, ctx) releases a block alloc returned.
+ * Process-wide; both NULL restores cudaMalloc / cudaFree.  Every block is freed with the pair
+ * that allocated it, whatever is installed by then.  The functions may be called from any
+ * thread that calls the library, and must not call back into it.  sais_solve_noalloc makes no
+ * allocation either way.  Errors: SAIS_EINVAL when exactly one of the two is NULL. */
+typedef void *(*sais_device_alloc_fn)(size_t bytes, int32_t device, void *ctx);
+typedef void (*sais_device_free_fn)(void *ptr, size_t bytes, int32_t device, void *ctx);
+SAIS_API sais_status sais_set_device_allocator(sais_device_alloc_fn alloc_fn,
+                                               sais_device_free_fn free_fn, void *ctx);
+
 /* Static text for a status code. */
 SAIS_API const char *sais_status_string(sais_status s);
 

@@ -6,8 +6,10 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <mutex>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -59,7 +61,7 @@ struct HostInst {
     std::vector<int32_t> Q, slack_off;     // m, m+1
     std::vector<int32_t> acol;             // nprime x m (spin-major)
     std::vector<float> D, asum;            // npad
-    std::vector<float> spinc;              // npad x 4: a_0 (int bits), D, sum a, a_1 (int bits)
+    std::vector<float> spinc;              // npad x 4: a_0, D, sum a, a_1 (FP32, exact)
     std::vector<int32_t> b;                // m capacities of the sampled problem (B' if tightened)
     std::vector<int32_t> margin;           // m: b_k - B'_k capped at sum_i a_ki (0 untightened)
     std::vector<float> hF;                 // npad
@@ -188,11 +190,10 @@ sais_status build_host(const sais_problem_desc *d, HostInst &h) {
     }
     h.spinc.assign((size_t)h.npad * 4, 0.f);
     for (int32_t i = 0; i < nprime; ++i) {
-        int32_t a0 = m > 0 ? h.acol[(size_t)i * m] : 0, a1 = m > 1 ? h.acol[(size_t)i * m + 1] : 0;
-        std::memcpy(&h.spinc[(size_t)i * 4 + 0], &a0, 4);
+        h.spinc[(size_t)i * 4 + 0] = m > 0 ? (float)h.acol[(size_t)i * m] : 0.f;
         h.spinc[(size_t)i * 4 + 1] = h.D[i];
         h.spinc[(size_t)i * 4 + 2] = h.asum[i];
-        std::memcpy(&h.spinc[(size_t)i * 4 + 3], &a1, 4);
+        h.spinc[(size_t)i * 4 + 3] = m > 1 ? (float)h.acol[(size_t)i * m + 1] : 0.f;
     }
     h.hF.assign(h.npad, 0.f);
     for (int32_t i = 0; i < n; ++i) h.hF[i] = (float)d->h[i];
@@ -446,12 +447,15 @@ sais_status ensure_work(sais_problem *p, int chains, cudaStream_t st) {
         if (e != cudaSuccess) return fail(SAIS_ECUDA, "work list event: %s", cudaGetErrorString(e));
     }
     if (w.size() / 2 > p->work_cap) {
-        if (p->d_work) cudaFree(p->d_work);   // synchronises: queued launches may read it
+        if (p->d_work) {   // synchronise first: queued launches may still read it
+            cudaDeviceSynchronize();
+            dev_free(p->d_work);
+        }
         if (p->h_work) cudaFreeHost(p->h_work);
         p->d_work = nullptr;
         p->h_work = nullptr;
         p->work_cap = 0;
-        e = cudaMalloc(&p->d_work, w.size() * 4);
+        e = dev_alloc(reinterpret_cast<void **>(&p->d_work), w.size() * 4);
         if (e != cudaSuccess) return fail(SAIS_ENOMEM, "work list: %s", cudaGetErrorString(e));
         e = cudaMallocHost(&p->h_work, w.size() * 4);
         if (e != cudaSuccess) return fail(SAIS_ENOMEM, "work list staging: %s", cudaGetErrorString(e));
@@ -640,12 +644,12 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(device);
-    cudaError_t ce = cudaMalloc(&p->pool, cur);
+    cudaError_t ce = dev_alloc(&p->pool, cur);
     if (ce != cudaSuccess) {
         cudaSetDevice(prev);
         delete p;
         return fail(ce == cudaErrorMemoryAllocation ? SAIS_ENOMEM : SAIS_ECUDA,
-                    "cudaMalloc(%zu): %s", cur, cudaGetErrorString(ce));
+                    "device allocation of %zu bytes: %s", cur, cudaGetErrorString(ce));
     }
     unsigned char *base = static_cast<unsigned char *>(p->pool);
     InstDev *recs = reinterpret_cast<InstDev *>(stage.data());
@@ -758,7 +762,7 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
     ce = cudaMemcpy(p->pool, stage.data(), cur, cudaMemcpyHostToDevice);
     cudaSetDevice(prev);
     if (ce != cudaSuccess) {
-        cudaFree(p->pool);
+        dev_free(p->pool);
         delete p;
         return fail(SAIS_ECUDA, "copy of problem data: %s", cudaGetErrorString(ce));
     }
@@ -784,11 +788,11 @@ sais_status sais_destroy_problem(sais_problem *p) {
     cudaGetDevice(&prev);
     cudaSetDevice(p->device);
     cudaError_t e = cudaDeviceSynchronize();
-    if (p->pool) cudaFree(p->pool);
-    if (p->d_work) cudaFree(p->d_work);
+    if (p->pool) dev_free(p->pool);
+    if (p->d_work) dev_free(p->d_work);
     if (p->h_work) cudaFreeHost(p->h_work);
     if (p->work_copied) cudaEventDestroy(p->work_copied);
-    if (p->d_inst_chains) cudaFree(p->d_inst_chains);
+    if (p->d_inst_chains) dev_free(p->d_inst_chains);
     for (cudaStream_t x : p->side)
         if (x) cudaStreamDestroy(x);
     for (cudaEvent_t x : p->join)
@@ -1259,11 +1263,15 @@ sais_status sais_solve(sais_problem *p, const sais_solve_params *prm, sais_solve
         cur = align_up(cur + sizes[i], 256);
     }
     unsigned char *scr = nullptr;
-    SAIS_CUDA(cudaMalloc(&scr, cur));
-    struct Free {
+    SAIS_CUDA(dev_alloc(reinterpret_cast<void **>(&scr), cur));
+    struct Free {   // on every return: the call's work done, then the scratch released
         unsigned char *q;
-        ~Free() { cudaFree(q); }
-    } free_scr{scr};
+        cudaStream_t s;
+        ~Free() {
+            cudaStreamSynchronize(s);
+            dev_free(q);
+        }
+    } free_scr{scr, st};
     float *d_lam = reinterpret_cast<float *>(scr + offs[0]);
     uint32_t *d_x = reinterpret_cast<uint32_t *>(scr + offs[1]);
     int64_t *d_cost = reinterpret_cast<int64_t *>(scr + offs[2]);
@@ -1428,7 +1436,10 @@ sais_status sais_set_instance_chains(sais_problem *p, const int32_t *counts) {
     DeviceGuard dg(p->device);
     if (!counts) {
         p->inst_chains.clear();
-        if (p->d_inst_chains) cudaFree(p->d_inst_chains);
+        if (p->d_inst_chains) {
+            cudaDeviceSynchronize();   // queued launches may still read the counts
+            dev_free(p->d_inst_chains);
+        }
         p->d_inst_chains = nullptr;
         p->work_valid = false;
         return SAIS_OK;
@@ -1436,7 +1447,8 @@ sais_status sais_set_instance_chains(sais_problem *p, const int32_t *counts) {
     for (int j = 0; j < p->count; ++j)
         if (counts[j] < 1) return fail(SAIS_EINVAL, "counts[%d] = %d: need >= 1", j, counts[j]);
     if (!p->d_inst_chains) {
-        cudaError_t e = cudaMalloc(&p->d_inst_chains, (size_t)p->count * 4);
+        cudaError_t e = dev_alloc(reinterpret_cast<void **>(&p->d_inst_chains),
+                                  (size_t)p->count * 4);
         if (e != cudaSuccess) return fail(SAIS_ENOMEM, "chain counts: %s", cudaGetErrorString(e));
     }
     cudaError_t e = cudaMemcpy(p->d_inst_chains, counts, (size_t)p->count * 4,
@@ -1463,11 +1475,15 @@ sais_status sais_autotune(sais_problem *p, int32_t chains, int32_t sweeps, sais_
         cur = align_up(cur + sz[i], 256);
     }
     unsigned char *buf = nullptr;
-    SAIS_CUDA(cudaMalloc(&buf, cur));
-    struct Free {
+    SAIS_CUDA(dev_alloc(reinterpret_cast<void **>(&buf), cur));
+    struct Free {   // on every return: the timing launches done, then the buffer released
         unsigned char *q;
-        ~Free() { cudaFree(q); }
-    } fr{buf};
+        cudaStream_t s;
+        ~Free() {
+            cudaStreamSynchronize(s);
+            dev_free(q);
+        }
+    } fr{buf, st};
     SAIS_CUDA(cudaMemsetAsync(buf, 0, cur, st));
     cudaEvent_t e0, e1;
     SAIS_CUDA(cudaEventCreate(&e0));
@@ -1644,6 +1660,68 @@ sais_status check_step_rule_internal(double eta_decay, double momentum) {
     return check_step_rule(eta_decay, momentum);
 }
 
+namespace {
+
+struct DevAllocator {
+    sais_device_alloc_fn alloc = nullptr;   // NULL: cudaMalloc / cudaFree
+    sais_device_free_fn free = nullptr;
+    void *ctx = nullptr;
+};
+struct DevBlock {
+    DevAllocator by;
+    size_t bytes;
+    int device;
+};
+std::mutex g_alloc_lock;
+DevAllocator g_allocator;
+std::unordered_map<void *, DevBlock> g_blocks;   // blocks of the caller's allocators
+
+}  // namespace
+
+cudaError_t dev_alloc(void **ptr, size_t bytes) {
+    *ptr = nullptr;
+    DevAllocator a;
+    {
+        std::lock_guard<std::mutex> lock(g_alloc_lock);
+        a = g_allocator;
+    }
+    if (!a.alloc) return cudaMalloc(ptr, bytes);
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return e;
+    void *p = a.alloc(bytes, device, a.ctx);
+    if (!p) return cudaErrorMemoryAllocation;
+    if (reinterpret_cast<uintptr_t>(p) % 256 != 0) {
+        a.free(p, bytes, device, a.ctx);
+        return cudaErrorMemoryAllocation;
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_alloc_lock);
+        g_blocks[p] = DevBlock{a, bytes, device};
+    }
+    *ptr = p;
+    return cudaSuccess;
+}
+
+void dev_free(void *ptr) {
+    if (!ptr) return;
+    DevBlock b{};
+    bool mine = false;
+    {
+        std::lock_guard<std::mutex> lock(g_alloc_lock);
+        auto it = g_blocks.find(ptr);
+        if (it != g_blocks.end()) {
+            b = it->second;
+            g_blocks.erase(it);
+            mine = true;
+        }
+    }
+    if (mine)
+        b.by.free(ptr, b.bytes, b.device, b.by.ctx);
+    else
+        cudaFree(ptr);
+}
+
 sais_status set_error(sais_status s, const char *fmt, ...) {
     char buf[512];
     va_list ap;
@@ -1655,3 +1733,13 @@ sais_status set_error(sais_status s, const char *fmt, ...) {
 }
 
 }  // namespace sais
+
+extern "C" sais_status sais_set_device_allocator(sais_device_alloc_fn alloc_fn,
+                                                 sais_device_free_fn free_fn, void *ctx) {
+    using namespace sais;
+    if ((alloc_fn == nullptr) != (free_fn == nullptr))
+        return set_error(SAIS_EINVAL, "give both an alloc and a free function, or neither");
+    std::lock_guard<std::mutex> lock(g_alloc_lock);
+    g_allocator = DevAllocator{alloc_fn, free_fn, alloc_fn ? ctx : nullptr};
+    return SAIS_OK;
+}

@@ -324,14 +324,14 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
                 // and before the wait for the previous block's MMAs, which they overlap
                 // (spins past N' read the zero padding of the arrays).
                 float Dp[K], Sp[K];
-                int32_t Ap[K][kPreM];
+                float Ap[K][kPreM];
 #pragma unroll
                 for (int ii = 0; ii < K; ++ii) {
                     const float4 sc = __ldg(ip->spinc + s0 + ii);
-                    Ap[ii][0] = __float_as_int(sc.x);
+                    Ap[ii][0] = sc.x;
                     Dp[ii] = sc.y;
                     Sp[ii] = sc.z;
-                    if (kPreM > 1) Ap[ii][kPreM > 1 ? 1 : 0] = __float_as_int(sc.w);
+                    if (kPreM > 1) Ap[ii][kPreM > 1 ? 1 : 0] = sc.w;
                 }
                 if (it > 0) {
                     // This block's fields: the previous block's MMAs are done (MMAs complete in
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
 #pragma unroll
                         for (int k = 0; k < MC; ++k) {
                             if (k < kPreM)
-                                akf[k] = (float)Ap[ii][k < kPreM ? k : 0];
+                                akf[k] = Ap[ii][k < kPreM ? k : 0];
                             else
                                 akf[k] = (k < m) ? (float)__ldg(acol + (size_t)s * m + k) : 0.f;
                             acc = fmaf(-akf[k], c[k], acc);

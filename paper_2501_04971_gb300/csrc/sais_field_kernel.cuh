@@ -451,9 +451,9 @@ __global__ void __launch_bounds__(kFThreads, 2)
 #pragma unroll
                 for (int k = 0; k < MC; ++k) {
                     if (k == 0)
-                        akf[k] = (float)__float_as_int(sc.x);
+                        akf[k] = sc.x;
                     else if (k == 1)
-                        akf[k] = (float)__float_as_int(sc.w);
+                        akf[k] = sc.w;
                     else
                         akf[k] = (k < m) ? (float)__ldg(acol + (size_t)s * m + k) : 0.f;
                     acc = fmaf(-akf[k], c[k], acc);

@@ -50,7 +50,7 @@ struct InstDev {
     int32_t m4;
     const float *D;        // npad: fl(P sigma_g^2 sum_k a_ki^2) (zero past N')
     const float *asum;     // npad: sum_k a_ki, exact in FP32 (zero past N')
-    const float4 *spinc;   // npad: {a_0i (int bits), D_i, sum_k a_ki, a_1i (int bits)}
+    const float4 *spinc;   // npad: {a_0i, D_i, sum_k a_ki, a_1i}, FP32 (exact integers)
     const int32_t *b;      // m capacities of the sampled problem (B' when tightened)
     const int32_t *fmargin;    // m: a sample is feasible iff g_k - (slack value)_k <= fmargin[k]
                                // (items load <= the caller's capacity; 0 unless tightened)
@@ -167,6 +167,13 @@ cudaError_t launch_pair_sampler(const SampleArgs &a, int max_m, int max_n, int m
 constexpr size_t kMaxSmemPerBlock = 232448;   // 227 KB opt-in per CTA on sm_103
 cudaError_t launch_post(const PostArgs &a, cudaStream_t stream);
 cudaError_t launch_advance_iter(uint32_t *iter_dev, cudaStream_t stream);
+
+// Device allocations of the library's own buffers: cudaMalloc / cudaFree, or the caller's pair
+// installed with sais_set_device_allocator.  dev_alloc returns cudaErrorMemoryAllocation when
+// the caller's alloc returns NULL (or memory that is not 256-byte aligned); dev_free releases a
+// block with the pair that allocated it (NULL is ignored).
+cudaError_t dev_alloc(void **ptr, size_t bytes);
+void dev_free(void *ptr);
 
 // Read-only view of a problem handle and access to the sampler dispatch of sais_api.cpp, for
 // entry points defined in other translation units.

@@ -580,10 +580,14 @@ sais_status mlp_launch(const sais_mlp *m, bool train, const float *X, const floa
 sais_status ensure_parts(sais_mlp *m, int32_t rows) {
     const int32_t need = (rows + kRows - 1) / kRows;
     if (need <= m->part_cap) return SAIS_OK;
-    if (m->part) cudaFree(m->part);
+    if (m->part) {
+        cudaDeviceSynchronize();   // queued launches may still write the old partials
+        dev_free(m->part);
+    }
     m->part = nullptr;
     m->part_cap = 0;
-    cudaError_t e = cudaMalloc(&m->part, (size_t)need * kParams * sizeof(float));
+    cudaError_t e = dev_alloc(reinterpret_cast<void **>(&m->part),
+                              (size_t)need * kParams * sizeof(float));
     if (e != cudaSuccess) return set_error(SAIS_ENOMEM, "MLP partial gradients: %s", cudaGetErrorString(e));
     m->part_cap = need;
     return SAIS_OK;
@@ -607,9 +611,9 @@ sais_status sais_mlp_create(int32_t device, uint64_t seed, sais_mlp **out) {
     sais_mlp *m = new (std::nothrow) sais_mlp;
     if (!m) return set_error(SAIS_ENOMEM, "host allocation failed");
     m->device = device;
-    cudaError_t e = cudaMalloc(&m->theta, kParams * sizeof(float) * 3);
-    if (e == cudaSuccess) e = cudaMalloc(&m->img, kImgBytes);
-    if (e == cudaSuccess) e = cudaMalloc(&m->status, sizeof(int32_t));
+    cudaError_t e = dev_alloc(reinterpret_cast<void **>(&m->theta), kParams * sizeof(float) * 3);
+    if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&m->img), kImgBytes);
+    if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&m->status), sizeof(int32_t));
     if (e != cudaSuccess) {
         sais_mlp_destroy(m);
         return set_error(SAIS_ENOMEM, "MLP buffers: %s", cudaGetErrorString(e));
@@ -648,10 +652,11 @@ sais_status sais_mlp_create(int32_t device, uint64_t seed, sais_mlp **out) {
 sais_status sais_mlp_destroy(sais_mlp *m) {
     if (!m) return SAIS_OK;
     Guard g(m->device);
-    cudaFree(m->theta);
-    cudaFree(m->img);
-    cudaFree(m->part);
-    cudaFree(m->status);
+    cudaDeviceSynchronize();   // the handle's queued launches finish before its buffers go
+    dev_free(m->theta);
+    dev_free(m->img);
+    dev_free(m->part);
+    dev_free(m->status);
     delete m;
     return SAIS_OK;
 }

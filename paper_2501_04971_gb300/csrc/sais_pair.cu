@@ -348,14 +348,14 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 // the waits below, which they overlap) for the decisions or for following the
                 // peer's flips.
                 float Dp[kPK], Sp[kPK];
-                int32_t Ap[kPK][kPreM];
+                float Ap[kPK][kPreM];
 #pragma unroll
                 for (int ii = 0; ii < kPK; ++ii) {
                     const float4 sc = __ldg(ip->spinc + s0 + ii);
-                    Ap[ii][0] = __float_as_int(sc.x);
+                    Ap[ii][0] = sc.x;
                     Dp[ii] = sc.y;
                     Sp[ii] = sc.z;
-                    if (kPreM > 1) Ap[ii][kPreM > 1 ? 1 : 0] = __float_as_int(sc.w);
+                    if (kPreM > 1) Ap[ii][kPreM > 1 ? 1 : 0] = sc.w;
                 }
                 if (item && ib >= 1 &&
                     (!p_wait_warp<false>(&bars[kBarMma], (ib - 1u) & 1u, abort_flag, status, polls) ||
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
 #pragma unroll
                         for (int k = 0; k < MC; ++k) {
                             if (k < kPreM)
-                                akf[k] = (float)Ap[ii][k < kPreM ? k : 0];
+                                akf[k] = Ap[ii][k < kPreM ? k : 0];
                             else
                                 akf[k] = (k < m) ? (float)__ldg(acol + (size_t)s * m + k) : 0.f;
                             acc = fmaf(-akf[k], c[k], acc);
@@ -588,7 +588,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
 #pragma unroll
                         for (int k = 0; k < MC; ++k) {
                             if (k < kPreM)
-                                gf[k] = fmaf((float)Ap[ii][k < kPreM ? k : 0], (float)d, gf[k]);
+                                gf[k] = fmaf(Ap[ii][k < kPreM ? k : 0], (float)d, gf[k]);
                             else if (k < m && d != 0)
                                 gf[k] = fmaf((float)__ldg(acol + (size_t)(s0 + ii) * m + k),
                                              (float)d, gf[k]);

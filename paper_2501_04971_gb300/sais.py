@@ -77,6 +77,9 @@ class sais_solve_result(ctypes.Structure):
                 ("elapsed_ms", _f64), ("spin_updates", _i64)]
 
 
+DEVICE_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, _i32, ctypes.c_void_p)
+DEVICE_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, _i32, ctypes.c_void_p)
+
 _SIGS = {
     "sais_describe": [ctypes.POINTER(sais_problem_desc), ctypes.POINTER(sais_problem_scalars)],
     "sais_create_problem": [ctypes.POINTER(sais_problem_desc), _i32, ctypes.POINTER(_P)],
@@ -109,6 +112,7 @@ _SIGS = {
     "sais_mlp_train_step": [_P, _P, _P, _i32, _f32, _P, _P],
     "sais_mlp_status": [_P],
     "sais_warm_start": [_P, _P, _P, _P],
+    "sais_set_device_allocator": [DEVICE_ALLOC_FN, DEVICE_FREE_FN, _P],
 }
 MLP_PARAMS, MLP_FEATURES = 20612, 8
 EXPORTS = list(_SIGS) + ["sais_status_string", "sais_last_error"]
@@ -240,6 +244,23 @@ def sais_sample_plan(h, prm) -> sais_plan:
     out = sais_plan()
     _check(lib().sais_sample_plan(h, ctypes.byref(prm), ctypes.byref(out)), "sais_sample_plan")
     return out
+
+
+_allocator_keep: list = []
+
+
+def sais_set_device_allocator(alloc=None, free=None):
+    """Install Python callables alloc(bytes, device) -> int pointer (0 on failure) and
+    free(ptr, bytes, device) as the library's device allocator; no arguments restores
+    cudaMalloc / cudaFree.  The callables are kept alive here."""
+    if alloc is None and free is None:
+        _check(lib().sais_set_device_allocator(DEVICE_ALLOC_FN(), DEVICE_FREE_FN(), None),
+               "sais_set_device_allocator")
+        return
+    fa = DEVICE_ALLOC_FN(lambda n, dev, ctx: alloc(n, dev) or None)
+    ff = DEVICE_FREE_FN(lambda p, n, dev, ctx: free(p, n, dev))
+    _allocator_keep.append((fa, ff))
+    _check(lib().sais_set_device_allocator(fa, ff, None), "sais_set_device_allocator")
 
 
 def sais_set_instance_chains(h, counts_ptr):
