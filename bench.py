@@ -629,8 +629,10 @@ def ragged_measurement(a, sais, torch):
     """The ragged batch: 384 QKP (N uniform in [100, 1000], profits up to 10^4) + 128 MKP
     (N in {250, 500}, m in {5, 10, 30}) with 64..256 chains each, in one SAIS_AUTO problem.
     The autotuner picks each launch group's sampler and CTA shape (its timing launches also
-    give per-class rates), then Algorithm 1 runs `ragged_iters` iterations of `sweeps` sweeps as
-    one captured CUDA graph (sais_solve, use_graph); rate = spin updates / solve device time."""
+    give per-class rates) and then between one persistent launch over the batch's items and the
+    concurrent group launches; Algorithm 1 runs `ragged_iters` iterations of `sweeps` sweeps as
+    one captured CUDA graph (sais_solve, use_graph) in both modes; rate = spin updates / solve
+    device time of the mode the autotuner kept."""
     from paper_2501_04971_gb300 import workloads as wl
     insts = wl.ragged_batch()
     prob = sais.Problem(insts)
@@ -646,16 +648,39 @@ def ragged_measurement(a, sais, torch):
                        "spin_updates_per_s": tune["spin_updates"][g] / (tune["ms"][g] / 1e3),
                        "tune_launch_ms": tune["ms"][g],
                        "tune_launch_spin_updates": int(tune["spin_updates"][g])})
-    prob.solve(1, C, a.sweeps, a.beta_max, a.gap_eta, 99, variant="auto", use_graph=True)
-    r = prob.solve(a.ragged_iters, C, a.sweeps, a.beta_max, a.gap_eta, 100, variant="auto",
-                   use_graph=True)
+    # Both SAIS_AUTO modes on the same solve (identical samples); the headline is the one the
+    # autotuner kept.
+    modes = {}
+    for mode in (("persistent", "groups") if tune["persistent_ok"] else ("groups",)):
+        prob.set_auto_mode(mode)
+        prob.solve(1, C, a.sweeps, a.beta_max, a.gap_eta, 99, variant="auto", use_graph=True)
+        rm = prob.solve(a.ragged_iters, C, a.sweeps, a.beta_max, a.gap_eta, 100, variant="auto",
+                        use_graph=True)
+        modes[mode] = {"value": rm["spin_updates"] / (rm["elapsed_ms"] / 1e3),
+                       "elapsed_ms": rm["elapsed_ms"], "result": rm}
+        if mode == "persistent":   # the last iteration's launch: how evenly the SMs were busy
+            st = prob.persistent_stats()
+            bf = st["busy_fraction"]
+            modes[mode]["last_launch"] = {
+                "ctas": st["ctas"], "span_ms": st["span_ns"] / 1e6,
+                "busy_fraction_mean": float(bf.mean()), "busy_fraction_min": float(bf.min()),
+                "busy_fraction_p10": float(np.percentile(bf, 10)),
+                "items_per_cta_max": int(st["items"].max()),
+                "items_per_cta_min": int(st["items"].min()),
+                "tail_ms": float((st["end_ns"].max() - np.median(st["end_ns"])) / 1e6)}
+    kept = "persistent" if tune["persistent"] else "groups"
+    r = modes[kept]["result"]
     nsp = np.array([s.n_spins for s in prob.scalars])
     out = {"workload": "384 QKP N~U[100,1000] (profits <= 1e4) + 128 MKP N in {250,500}, "
                        "m in {5,10,30}; chains U[64,256] per instance; %d sweeps; %d graph-"
                        "captured iterations of Algorithm 1" % (a.sweeps, a.ragged_iters),
            "value": r["spin_updates"] / (r["elapsed_ms"] / 1e3), "unit": UNIT,
            "elapsed_ms": r["elapsed_ms"], "spin_updates": int(r["spin_updates"]),
-           "max_spins": int(nsp.max()), "groups": groups,
+           "max_spins": int(nsp.max()), "groups": groups, "mode": kept,
+           "modes": {k: {kk: vv for kk, vv in dict(v, unit=UNIT).items() if kk != "result"}
+                     for k, v in modes.items()},
+           "autotune_launch_ms": {"persistent": tune["persistent_ms"],
+                                  "groups": tune["groups_ms"]},
            "feasible_instances": int((r["best_cost"] != np.iinfo(np.int64).max).sum())}
     prob.close()
     return out

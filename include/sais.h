@@ -115,11 +115,16 @@ typedef struct sais_layout {
  * SAIS_AUTO takes any number. */
 typedef enum sais_variant {
     SAIS_PLAIN = 0,          /* per-spin sampler: FP32 fields, rank-1 update on every flip  */
-    SAIS_BLOCKED = 1,        /* k spins per block, rank-k field update on the tensor cores  */
-    SAIS_AUTO = 2            /* per launch group of the batch: the blocked sampler where an
-                                instance allows it (quadratic objective, m <= 8, N' <= 448),
-                                the plain sampler otherwise, or the choices sais_autotune
-                                made; ragged work lists, most expensive instances first      */
+    SAIS_BLOCKED = 1,        /* k spins per block, field updates on the tensor cores        */
+    SAIS_AUTO = 2            /* ragged batches: by default one persistent launch whose CTAs
+                                take (instance, chain group) items, most expensive first,
+                                from a device counter: the blocked sampler (block fields by
+                                GEMM, K = 16) for quadratic objectives with m <= 8 and
+                                n <= 1024, the plain sampler for linear ones with m <= 32.
+                                Batches outside that (or when sais_autotune measured them
+                                faster) run as concurrent launch groups: per group the
+                                blocked sampler where an instance allows it, the plain one
+                                otherwise, or sais_autotune's choices                       */
 } sais_variant;
 
 /* What sais_autotune chose for each launch group of SAIS_AUTO (first 16 groups). */
@@ -134,6 +139,11 @@ typedef struct sais_tuning {
     int32_t group_size[16];          /* instances per group                                */
     double group_ms[16];             /* measured time of the chosen configuration          */
     int64_t group_spin_updates[16];  /* spin updates of one timed launch of the group      */
+    int32_t persistent_ok;           /* 1: the batch fits one persistent launch            */
+    int32_t persistent;              /* 1: SAIS_AUTO now runs the persistent launch, 0: the
+                                        group launches (the faster of the two timings)     */
+    double persistent_ms;            /* one timed SAIS_AUTO launch, persistent (0 if n/a)  */
+    double groups_ms;                /* the same with the concurrent group launches        */
 } sais_tuning;
 
 /* One annealing run per chain (Sec. III-B): every chain starts at x = 0 and performs `sweeps`
@@ -350,10 +360,11 @@ SAIS_API sais_status sais_solve_noalloc(sais_problem *p, const sais_solve_params
 SAIS_API sais_status sais_set_instance_chains(sais_problem *p, const int32_t *counts);
 
 /* Autotuner of SAIS_AUTO: for every launch group, times one launch of `sweeps` sweeps with
- * `chains` chains for each candidate (blocked with block_k 16 / 32 where W allows it, plain with
- * 32 / 64 / 128 chains per CTA) and keeps the fastest for later SAIS_AUTO launches.  Allocates
- * and frees temporary device buffers; synchronises `stream`.  Errors: SAIS_EINVAL, SAIS_ENOMEM,
- * SAIS_ECUDA. */
+ * `chains` chains for each candidate (blocked with block_k 16 / 32 / 64 where W allows it,
+ * plain with 32 / 64 / 128 chains per CTA) and keeps the fastest; then times one SAIS_AUTO
+ * launch as concurrent group launches and one as the persistent launch (when the batch fits
+ * it) and keeps the faster mode for later SAIS_AUTO launches.  Allocates and frees temporary
+ * device buffers; synchronises `stream`.  Errors: SAIS_EINVAL, SAIS_ENOMEM, SAIS_ECUDA. */
 SAIS_API sais_status sais_autotune(sais_problem *p, int32_t chains, int32_t sweeps,
                                    sais_tuning *out, void *stream);
 
@@ -366,19 +377,43 @@ typedef enum sais_kernel {
     SAIS_KERNEL_RANKK_RESIDENT = 1, /* blocked, rank-k field update, W resident in SMEM       */
     SAIS_KERNEL_RANKK_STREAMED = 2, /* blocked, rank-k field update, W tiles streamed          */
     SAIS_KERNEL_BLOCK_FIELD = 3,    /* blocked, each block's fields from a GEMM over the states */
-    SAIS_KERNEL_CTA_PAIR = 4,       /* blocked, fields split over a cluster of two CTAs        */
-    SAIS_KERNEL_GROUPS = 5          /* SAIS_AUTO: one launch per group (see sais_autotune)     */
+    SAIS_KERNEL_GROUPS = 4,         /* SAIS_AUTO: one launch per group (see sais_autotune)     */
+    SAIS_KERNEL_PERSISTENT = 5      /* SAIS_AUTO: one persistent launch over the batch's items  */
 } sais_kernel;
 
 typedef struct sais_plan {
     int32_t kernel;          /* sais_kernel                                                  */
     int32_t block_k;         /* spins per block (blocked kernels), else 0                    */
-    int32_t chains_per_cta;  /* chains per CTA (per cluster for the CTA pair)                */
+    int32_t chains_per_cta;  /* chains per CTA (0 for SAIS_AUTO)                              */
     int32_t hilo;            /* 1 when W is applied as two BF16 terms (pair values > 256)    */
 } sais_plan;
 
 SAIS_API sais_status sais_sample_plan(const sais_problem *p, const sais_sample_params *prm,
                                       sais_plan *out);
+
+/* How SAIS_AUTO runs this handle's batch from now on: SAIS_AUTO_PERSISTENT (the default) makes
+ * one persistent launch when the batch fits it (see sais_variant) and the group launches
+ * otherwise; SAIS_AUTO_GROUPS always makes the group launches.  Both draw identical samples.
+ * Overrides the mode sais_autotune chose (and a later sais_autotune overrides this).  No
+ * counterpart in the paper: a launch-shape choice for the batched sampler of Sec. III-B.
+ * Errors: SAIS_EINVAL (NULL handle or unknown mode). */
+typedef enum sais_auto_mode {
+    SAIS_AUTO_PERSISTENT = 0,
+    SAIS_AUTO_GROUPS = 1
+} sais_auto_mode;
+
+SAIS_API sais_status sais_set_auto_mode(sais_problem *p, int32_t mode);
+
+/* Per-CTA record of the most recent persistent launch of this handle (one CTA per SM, at most
+ * one per item): waits for `stream`, then copies 4 uint64 per CTA into `out` (host, room for
+ * `cap` CTAs): start and end of the CTA on the GPU's global timer (ns), the time it spent
+ * running items (ns), and the number of items it ran.  *ctas receives the launch's CTA count
+ * (records beyond `cap` are not copied).  Before any persistent launch the records are zero.
+ * No counterpart in the paper: load-balance instrumentation of the batched sampler.
+ * Errors: SAIS_EINVAL (NULL argument, or no persistent launch prepared for this handle),
+ * SAIS_ECUDA. */
+SAIS_API sais_status sais_persistent_stats(sais_problem *p, uint64_t *out, int32_t cap,
+                                           int32_t *ctas, void *stream);
 
 /* Wait for the work queued on `stream` and report device-side failures of this problem's
  * kernels since the last call: SAIS_ETIMEOUT if a bounded wait inside a kernel gave up (the

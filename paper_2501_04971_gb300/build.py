@@ -22,7 +22,7 @@ LIB = os.path.join(BUILD, "libsais.so")
 
 SOURCES = ["sais_api.cpp", "sais_plain.cu", "sais_post.cu", "sais_blocked.cu",
            "sais_blocked_stream.cu", "sais_field.cu", "sais_field_k.cu", "sais_noalloc.cu",
-           "sais_mlp.cu", "sais_pair.cu"]
+           "sais_mlp.cu", "sais_ragged.cu", "sais_ragged_hilo.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
          "-fvisibility=hidden", "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -300,7 +300,6 @@ struct sais_problem {
         bool any_w = false;
         bool blocked_ok = false;   // every member fits the blocked sampler
         bool field = false;        // blocked sampler with per-block field GEMMs (one CTA)
-        bool pair = false;         // blocked sampler on CTA pairs (items beyond one SM's TMEM)
         std::vector<int> members;
         size_t work_off = 0, nwork = 0;
         double tuned_ms = 0.0;
@@ -310,7 +309,7 @@ struct sais_problem {
     int32_t *d_inst_chains = nullptr;   // device copy (own allocation)
     int32_t *d_work = nullptr;          // device work list (own allocation)
     // Launch groups run concurrently: fork from the caller's stream, one side stream per group
-    // (CTA-pair groups share side[0], so two cluster kernels never run at once), join back.
+    // (the extra stream side[0] is spare), join back.
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> join;
     cudaEvent_t fork = nullptr;
@@ -319,6 +318,15 @@ struct sais_problem {
     bool work_valid = false;
     int32_t *h_work = nullptr;          // pinned staging copy of the work list (own allocation)
     cudaEvent_t work_copied = nullptr;  // the last upload from h_work has completed
+    // The persistent launch of SAIS_AUTO (sais_ragged_kernel.cuh): its items follow the group
+    // pairs in the work list, 3 ints each (instance, chain group, kind), most expensive first,
+    // then the device work counter.
+    bool ragged_ok = false;             // every instance fits the persistent launch
+    bool use_ragged = false;            // SAIS_AUTO runs it (else the per-group launches)
+    size_t ragged_off = 0, ragged_n = 0, head_off = 0;   // in ints of the work list
+    size_t stats_off = 0;   // per-CTA records of the persistent launch (4 uint64 per CTA)
+    int ragged_ctas = 0;    // CTAs of the persistent launch
+    int sms = 0;                        // multiprocessors of the device
 };
 
 namespace {
@@ -328,11 +336,9 @@ namespace {
 //    N'_pad + K <= 512; two MMAs per block of K = 16 spins, the fewest tensor-core
 //    instructions per spin;
 //  * block fields from a GEMM over the states (sais_field_kernel.cuh), one CTA per SM up to
-//    n = 992 items: for instances beyond the first, and for K = 32 streamed or hi/lo and K = 64;
-//  * a CTA pair with the fields split over two SMs (sais_pair.cu) beyond that (n <= 1024).
+//    n = 1024 items: for instances beyond the first, and for K = 32 streamed or hi/lo and K = 64.
 bool field_fits(int n16, int words, int m, bool has_w, int k, bool hilo) {
-    return has_w && m <= kMaxBlockedConstraints && (k == 16 || m <= 2) &&
-           field_tmem_cols(n16, k) <= 512 &&
+    return has_w && m <= kMaxBlockedConstraints && (k == 16 || m <= 2) && n16 <= 1024 &&
            field_smem_bytes(n16, words, k, hilo) <= kMaxSmemPerBlock;
 }
 
@@ -341,10 +347,9 @@ bool field_fits(int n16, int words, int m, bool has_w, int k, bool hilo) {
 int field_default_k(int m) { return m <= 2 ? 32 : 16; }
 
 // SAIS_AUTO grouping (see struct sais_problem).  Keys: 1 rank-k blocked with W resident, 2
-// streamed, 3 streamed hi/lo; 4 CTA-pair blocked, 5 CTA-pair hi/lo (6, 7: the same with n >
-// 992, whose pair kernels take the A operand from shared memory); 10 block-field, 11 block-field
-// hi/lo; plain instances split by whether they have W and by padded N' (bucket of 128 spins), so
-// each plain group sizes its shared memory for its own largest member.
+// streamed, 3 streamed hi/lo; 10 block-field, 11 block-field hi/lo; plain instances split by
+// whether they have W and by padded N' (bucket of 128 spins), so each plain group sizes its
+// shared memory for its own largest member.
 
 void build_groups(sais_problem *p) {
     p->groups.clear();
@@ -356,8 +361,6 @@ void build_groups(sais_problem *p) {
         }
         if (field_fits(n16_of(h.n), h.words, h.m, h.has_w, 16, h.lo_own))
             return h.lo_own ? 11 : 10;
-        if (pair_eligible(h.n, h.m, h.has_w))
-            return (h.lo_own ? 5 : 4) + (pair_a_tmem(h.n) ? 0 : 2);
         return 100 + (h.has_w ? 1000 : 0) + (h.npad + 127) / 128;
     };
     std::vector<int> keys;
@@ -387,10 +390,9 @@ void build_groups(sais_problem *p) {
         }
         g.variant = key >= 100 ? SAIS_PLAIN : SAIS_BLOCKED;
         g.blocked_ok = key < 100;
-        g.pair = key >= 4 && key <= 7;
         g.field = key == 10 || key == 11;
         g.stream_w = key >= 2 && key <= 11;
-        g.hilo = key == 3 || key == 5 || key == 7 || key == 11;
+        g.hilo = key == 3 || key == 11;
         if (g.field) g.block_k = field_default_k(g.max_m);
         auto cost = [&](int j) {
             const HostInst &h = p->host[j];
@@ -401,6 +403,22 @@ void build_groups(sais_problem *p) {
         p->groups.push_back(std::move(g));
     }
     p->work_valid = false;
+    // The persistent launch: quadratic instances on the block-field sampler (m <= 8, n <= 1024),
+    // linear ones on the plain sampler (m <= 32), the whole batch's shared memory in one CTA.
+    p->ragged_ok = p->count > 0;
+    int max_n16_w = 0;
+    for (const HostInst &h : p->host) {
+        if (h.has_w) {
+            max_n16_w = std::max(max_n16_w, n16_of(h.n));
+            p->ragged_ok = p->ragged_ok && h.m <= kMaxBlockedConstraints && n16_of(h.n) <= 1024;
+        } else {
+            p->ragged_ok = p->ragged_ok && h.m <= kMaxConstraints;
+        }
+    }
+    int ring = 0;
+    p->ragged_ok = p->ragged_ok &&
+                   ragged_smem_bytes(max_n16_w, p->words, p->any_lo, &ring) <= kMaxSmemPerBlock;
+    p->use_ragged = p->ragged_ok;
     if (p->groups.size() > 1) {
         const size_t ns = p->groups.size() + 1;
         p->side.assign(ns, nullptr);
@@ -435,6 +453,41 @@ sais_status ensure_work(sais_problem *p, int chains, cudaStream_t st) {
             }
         }
         g.nwork = w.size() / 2 - g.work_off;
+    }
+    if (p->ragged_ok) {
+        // Items of the persistent launch, most expensive first by an estimate of SM cycles per
+        // sweep: the block-field sampler ~150 per spin plus ~7.5 per spin for each 16-spin
+        // GEMM step (twice with hi/lo); the plain sampler on 256 chains ~(120 + 6 m) per spin.
+        struct Item {
+            double cost;
+            int32_t j, q, kind;
+        };
+        std::vector<Item> items;
+        for (int j = 0; j < p->count; ++j) {
+            const HostInst &h = p->host[j];
+            const int cj = p->inst_chains.empty() ? chains : p->inst_chains[j];
+            const int per = h.has_w ? kRaggedFieldChains : kRaggedPlainItemChains;
+            const int kind = h.has_w ? (h.m <= 1 ? 0 : 1) : (h.m <= 8 ? 2 : 3);
+            const double cost =
+                h.has_w ? (double)h.nprime * (150.0 + 7.5 * (n16_of(h.n) / 16) * (p->any_lo ? 2 : 1))
+                        : (double)h.nprime * (120.0 + 6.0 * h.m);
+            for (int q = 0; q < (cj + per - 1) / per; ++q) items.push_back({cost, j, q, kind});
+        }
+        std::stable_sort(items.begin(), items.end(),
+                         [](const Item &x, const Item &y) { return x.cost > y.cost; });
+        p->ragged_off = w.size();
+        p->ragged_n = items.size();
+        for (const Item &it : items) {
+            w.push_back(it.j);
+            w.push_back(it.q);
+            w.push_back(it.kind);
+        }
+        while (w.size() % 64) w.push_back(0);   // the counter on its own 256 bytes
+        p->head_off = w.size();
+        for (int i = 0; i < 64; ++i) w.push_back(0);
+        p->stats_off = w.size();
+        p->ragged_ctas = ragged_grid((int)items.size(), p->sms);
+        for (int i = 0; i < 8 * p->ragged_ctas; ++i) w.push_back(0);
     }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(st, &cs);
@@ -479,8 +532,6 @@ cudaError_t launch_group(const sais_problem *p, const sais_problem::Group &g, co
     SampleArgs ga = a;
     ga.work = p->d_work + 2 * g.work_off;
     ga.nwork = (int32_t)g.nwork;
-    if (g.variant == SAIS_BLOCKED && g.pair)
-        return launch_pair_sampler(ga, g.max_m, g.max_n, g.words, g.hilo, p->d_status, polls, st);
     if (g.variant == SAIS_BLOCKED && g.field)
         return launch_field_sampler(ga, g.max_m, g.max_n16, g.words, g.block_k, g.hilo,
                                     p->d_status, polls, st);
@@ -770,6 +821,7 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
     p->d_status = reinterpret_cast<int32_t *>(base + status_off);
     {
         DeviceGuard dg(device);   // the groups' side streams belong to the problem's device
+        cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, device);
         build_groups(p);
     }
     noalloc_prepare(device);
@@ -891,7 +943,6 @@ sais_status check_step_rule(double eta_decay, double momentum) {
 // every size and variant check happens before anything is queued on a stream.
 struct SamplePlan {
     int variant = SAIS_PLAIN;   // SAIS_PLAIN, SAIS_BLOCKED or SAIS_AUTO
-    bool pair = false;          // blocked on CTA pairs (fields split over two SMs)
     bool field = false;         // blocked with per-block field GEMMs on one CTA
     bool stream_w = false;      // rank-k blocked with W tiles streamed instead of resident
     bool hilo = false;          // BF16 hi/lo split of W
@@ -947,26 +998,14 @@ sais_status plan_sample(const sais_problem *p, const sais_sample_params *prm, Sa
         return fail(SAIS_EUNSUPPORTED,
                     "blocked sampler: block_k = %d takes at most 2 constraints (m = %d)", k,
                     p->max_m);
-    if (k != 16 && field_tmem_cols(p->max_n16, k) <= 512)
+    if (p->max_n16 > 1024)
         return fail(SAIS_EUNSUPPORTED,
-                    "blocked sampler: block_k = %d with n = %d needs %zu bytes of shared memory "
-                    "(max %zu)", k, p->max_n, field_smem_bytes(p->max_n16, p->words, k, pl->hilo),
-                    kMaxSmemPerBlock);
-    // Beyond one SM (n > 992): fields split over a CTA pair (thread-block cluster of two).
-    for (int jj = 0; jj < p->count; ++jj) {
-        const HostInst &h = p->host[jj];
-        if (!pair_eligible(h.n, h.m, h.has_w))
-            return fail(SAIS_EUNSUPPORTED,
-                        "blocked sampler: n = %d items exceed what one SM holds and instance %d "
-                        "(n=%d) is outside the CTA-pair range (128 <= n rounded up to 64 <= 1024)",
-                        p->max_n, jj, h.n);
-    }
-    if (k != 16)
-        return fail(SAIS_EUNSUPPORTED,
-                    "blocked sampler: n = %d exceeds one SM at block_k = %d; CTA pairs run "
-                    "block_k = 16 only", p->max_n, k);
-    pl->pair = true;
-    return SAIS_OK;
+                    "blocked sampler: n = %d items, more than the 1024 its kernels hold (use "
+                    "SAIS_PLAIN)", p->max_n);
+    return fail(SAIS_EUNSUPPORTED,
+                "blocked sampler: block_k = %d with n = %d needs %zu bytes of shared memory (max "
+                "%zu)", k, p->max_n, field_smem_bytes(p->max_n16, p->words, k, pl->hilo),
+                kMaxSmemPerBlock);
 }
 
 sais_status enqueue_sample(sais_problem *p, const sais_sample_params *prm, const float *lambda,
@@ -1004,6 +1043,16 @@ sais_status enqueue_sample(sais_problem *p, const sais_sample_params *prm, const
     if (pl.variant == SAIS_AUTO) {
         sais_status s = ensure_work(p, prm->chains, st);
         if (s != SAIS_OK) return s;
+        if (p->use_ragged) {   // one persistent launch over every instance
+            e = launch_ragged(a, p->d_work + p->ragged_off, (int32_t)p->ragged_n,
+                              p->d_work + p->head_off,
+                              reinterpret_cast<unsigned long long *>(p->d_work + p->stats_off),
+                              p->max_n16, p->words, p->any_lo,
+                              p->d_status, polls, p->sms, st);
+            if (e != cudaSuccess)
+                return fail(SAIS_ECUDA, "sampler launch (persistent): %s", cudaGetErrorString(e));
+            return SAIS_OK;
+        }
         if (p->groups.size() == 1) {
             e = launch_group(p, p->groups[0], a, polls, st);
             if (e != cudaSuccess)
@@ -1015,7 +1064,7 @@ sais_status enqueue_sample(sais_problem *p, const sais_sample_params *prm, const
         for (size_t gi = 0; e == cudaSuccess && gi < p->groups.size(); ++gi) {
             const auto &g = p->groups[gi];
             if (g.nwork == 0) continue;
-            const size_t si = g.pair ? 0 : gi + 1;
+            const size_t si = gi + 1;
             if (!used[si]) e = cudaStreamWaitEvent(p->side[si], p->fork, 0);
             used[si] = 1;
             if (e == cudaSuccess) e = launch_group(p, g, a, polls, p->side[si]);
@@ -1029,9 +1078,7 @@ sais_status enqueue_sample(sais_problem *p, const sais_sample_params *prm, const
             return fail(SAIS_ECUDA, "sampler launch (groups): %s", cudaGetErrorString(e));
         return SAIS_OK;
     }
-    if (pl.variant == SAIS_BLOCKED && pl.pair)
-        e = launch_pair_sampler(a, p->max_m, p->max_n, p->words, pl.hilo, p->d_status, polls, st);
-    else if (pl.variant == SAIS_BLOCKED && pl.field)
+    if (pl.variant == SAIS_BLOCKED && pl.field)
         e = launch_field_sampler(a, p->max_m, p->max_n16, p->words, pl.k, pl.hilo, p->d_status,
                                  polls, st);
     else if (pl.variant == SAIS_BLOCKED)
@@ -1099,19 +1146,42 @@ sais_status sais_sample_plan(const sais_problem *p, const sais_sample_params *pr
     if (s != SAIS_OK) return s;
     *out = sais_plan{};
     if (pl.variant == SAIS_AUTO) {
-        out->kernel = SAIS_KERNEL_GROUPS;
+        out->kernel = p->use_ragged ? SAIS_KERNEL_PERSISTENT : SAIS_KERNEL_GROUPS;
+        out->hilo = p->any_lo ? 1 : 0;
     } else if (pl.variant == SAIS_PLAIN) {
         out->kernel = SAIS_KERNEL_PLAIN;
         out->chains_per_cta = pl.cpb;
     } else {
-        out->kernel = pl.pair ? SAIS_KERNEL_CTA_PAIR
-                              : (pl.field ? SAIS_KERNEL_BLOCK_FIELD
-                                          : (pl.stream_w ? SAIS_KERNEL_RANKK_STREAMED
-                                                         : SAIS_KERNEL_RANKK_RESIDENT));
+        out->kernel = pl.field ? SAIS_KERNEL_BLOCK_FIELD
+                               : (pl.stream_w ? SAIS_KERNEL_RANKK_STREAMED
+                                              : SAIS_KERNEL_RANKK_RESIDENT);
         out->block_k = pl.k;
         out->chains_per_cta = 128;
         out->hilo = pl.hilo ? 1 : 0;
     }
+    return SAIS_OK;
+}
+
+sais_status sais_set_auto_mode(sais_problem *p, int32_t mode) {
+    if (!p) return fail(SAIS_EINVAL, "NULL problem");
+    if (mode != SAIS_AUTO_PERSISTENT && mode != SAIS_AUTO_GROUPS)
+        return fail(SAIS_EINVAL, "unknown SAIS_AUTO mode %d", mode);
+    p->use_ragged = mode == SAIS_AUTO_PERSISTENT && p->ragged_ok;
+    return SAIS_OK;
+}
+
+sais_status sais_persistent_stats(sais_problem *p, uint64_t *out, int32_t cap, int32_t *ctas,
+                                  void *stream) {
+    if (!p || !out || !ctas || cap < 0) return fail(SAIS_EINVAL, "NULL argument or cap < 0");
+    if (!p->ragged_ok || !p->work_valid || p->ragged_ctas == 0)
+        return fail(SAIS_EINVAL, "no persistent launch prepared for this problem");
+    DeviceGuard dg(p->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    *ctas = p->ragged_ctas;
+    const size_t n = (size_t)std::min(cap, p->ragged_ctas) * 4;
+    SAIS_CUDA(cudaMemcpyAsync(out, p->d_work + p->stats_off, n * sizeof(uint64_t),
+                              cudaMemcpyDeviceToHost, st));
+    SAIS_CUDA(cudaStreamSynchronize(st));
     return SAIS_OK;
 }
 
@@ -1579,6 +1649,40 @@ sais_status sais_autotune(sais_problem *p, int32_t chains, int32_t sweeps, sais_
             (int32_t)g.members.size();
     }
     out->groups = (int32_t)p->groups.size();
+    // The two ways SAIS_AUTO can run the batch: the concurrent group launches (with the
+    // choices above) and, when the batch fits it, one persistent launch; the faster is kept.
+    {
+        sais_sample_params sa = sp;
+        sa.variant = SAIS_AUTO;
+        auto time_auto = [&](bool ragged, double *ms) -> sais_status {
+            p->use_ragged = ragged;
+            p->work_valid = false;
+            for (int rep = 0; rep < 2; ++rep) {   // warm-up, then the timed launch
+                if (rep == 1) SAIS_CUDA(cudaEventRecord(e0, st));
+                sais_status r = enqueue_sample(p, &sa, a.lambda, nullptr, a.x, a.cost, a.g,
+                                               a.feasible, nullptr, st);
+                if (r != SAIS_OK) return r;
+            }
+            SAIS_CUDA(cudaEventRecord(e1, st));
+            SAIS_CUDA(cudaEventSynchronize(e1));
+            float f = 0.f;
+            cudaEventElapsedTime(&f, e0, e1);
+            *ms = f;
+            return SAIS_OK;
+        };
+        double gms = 0.0, rms = 0.0;
+        sais_status r = time_auto(false, &gms);
+        if (r != SAIS_OK) return r;
+        if (p->ragged_ok) {
+            r = time_auto(true, &rms);
+            if (r != SAIS_OK) return r;
+        }
+        p->use_ragged = p->ragged_ok && rms < gms;
+        out->persistent_ok = p->ragged_ok ? 1 : 0;
+        out->persistent = p->use_ragged ? 1 : 0;
+        out->persistent_ms = rms;
+        out->groups_ms = gms;
+    }
     p->work_valid = false;
     int32_t v = 0;
     SAIS_CUDA(cudaMemcpy(&v, p->d_status, 4, cudaMemcpyDeviceToHost));

@@ -9,18 +9,35 @@ cudaError_t launch_field_wide(const SampleArgs &a, int max_m, int block_k, bool 
                               int32_t *status, long long polls, const FieldLaunch &L,
                               cudaStream_t st);
 
-size_t field_smem_bytes(int max_n16, int max_words, int block_k, bool hilo) {
-    const size_t slot = (size_t)block_k * max_n16 * 2 * (hilo ? 2 : 1) + (size_t)block_k * block_k * 4;
-    const size_t xwords = (size_t)((max_words + 1) & ~1);   // as the kernel rounds them
-    return f_ring(block_k) * slot + xwords * kFLanes * 4 + (size_t)2 * block_k * kFLanes * 4 +
-           kFBars * 8 + 32;
-}
-
-// TMEM columns: the power of two >= the state columns (8 per 16 item spins) plus K fields.
+// TMEM columns: the power of two >= the state columns (8 per 16 item spins) plus K fields, at
+// most 512 (state chunks beyond them live in shared memory).
 uint32_t field_tmem_cols(int max_n16, int block_k) {
     uint32_t cols = 32;
-    while (cols < (uint32_t)(max_n16 / 2 + block_k)) cols <<= 1;
+    while (cols < 512u && cols < (uint32_t)(max_n16 / 2 + block_k)) cols <<= 1;
     return cols;
+}
+
+// 16-spin state chunks that do not fit TMEM beside the K field columns.
+int field_xs_chunks(int max_n16, int block_k) {
+    const int in_tmem = (int)(field_tmem_cols(max_n16, block_k) - (uint32_t)block_k) / 8;
+    return std::max(0, max_n16 / 16 - in_tmem);
+}
+
+size_t field_smem_ring(int max_n16, int max_words, int block_k, bool hilo, int ring) {
+    const size_t slot = (size_t)block_k * max_n16 * 2 * (hilo ? 2 : 1) + (size_t)block_k * block_k * 4;
+    const size_t xwords = (size_t)((max_words + 1) & ~1);   // as the kernel rounds them
+    return ring * slot + (size_t)field_xs_chunks(max_n16, block_k) * kFXChunkBytes +
+           xwords * kFLanes * 4 + (size_t)2 * block_k * kFLanes * 4 + kFBars * 8 + 32;
+}
+
+// Three W tile slots when they fit (the stager may run two blocks ahead), else two.
+int field_ring(int max_n16, int max_words, int block_k, bool hilo) {
+    return field_smem_ring(max_n16, max_words, block_k, hilo, 3) <= kMaxSmemPerBlock ? 3 : 2;
+}
+
+size_t field_smem_bytes(int max_n16, int max_words, int block_k, bool hilo) {
+    return field_smem_ring(max_n16, max_words, block_k, hilo,
+                           field_ring(max_n16, max_words, block_k, hilo));
 }
 
 cudaError_t launch_field_sampler(const SampleArgs &a, int max_m, int max_n16, int max_words,
@@ -32,6 +49,8 @@ cudaError_t launch_field_sampler(const SampleArgs &a, int max_m, int max_n16, in
     FieldLaunch L;
     L.cols = field_tmem_cols(max_n16, block_k);
     L.max_n16 = max_n16;
+    L.ring = field_ring(max_n16, max_words, block_k, hilo);
+    L.xs_chunks = field_xs_chunks(max_n16, block_k);
     const size_t per_sm = 228 * 1024, max_ctas = std::min<size_t>(2, 512 / L.cols);
     L.smem = field_smem_bytes(max_n16, max_words, block_k, hilo);
     const size_t floor_smem = per_sm / (max_ctas + 1) + 1;

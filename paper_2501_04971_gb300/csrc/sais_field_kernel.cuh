@@ -46,8 +46,10 @@ namespace sais {
 // Launch shape shared by every instantiation of the block-field sampler.
 struct FieldLaunch {
     size_t smem;
-    uint32_t cols;
-    int32_t max_n16;
+    uint32_t cols;       // TMEM columns of a CTA
+    int32_t max_n16;     // largest n rounded up to 16 in the launch
+    int32_t ring;        // W tile slots (2 or 3)
+    int32_t xs_chunks;   // 16-spin state chunks kept in shared memory (beyond TMEM), at most
 };
 
 namespace {
@@ -55,9 +57,7 @@ namespace {
 constexpr int kFLanes = 128;
 constexpr int kFThreads = 256;
 constexpr int kFNoiseWarp0 = 4;
-// W tile slots: three for K = 16 (the tile stager may run two blocks ahead), two for K >= 32
-// (one block ahead, which is all a block's GEMM needs; the larger tiles fit shared memory).
-__host__ __device__ constexpr uint32_t f_ring(int K) { return K == 16 ? 3u : 2u; }
+constexpr uint32_t kFXChunkBytes = 128 * 16 * 2;   // one 16-spin state chunk, 128 chains, BF16
 constexpr long long kFWaitCycles = 8000000000ll;   // about 4 s at 2 GHz
 // bars: 0 never completed (timeout test), 1 the block's field GEMM done (one phase per block),
 // 2..5 drain of decision warp 0..3, 6..13 noise slot written (2 q + slot), 14..21 noise slot
@@ -127,18 +127,24 @@ __device__ __forceinline__ const float *f_diag_image(const InstDev *ip) {
     return K == 16 ? ip->Wdiag : (K == 32 ? ip->Wd32 : ip->Wd64);
 }
 
-template <int MC, int K, bool kHiLo, bool kTrack>
-__global__ void __launch_bounds__(kFThreads, 2)
-    field_sampler_kernel(SampleArgs a, int32_t *status, long long dec_wait_polls,
-                         uint32_t tmem_cols, int32_t max_n16) {
-    extern __shared__ __align__(1024) unsigned char smem[];
+// One work item: 128 chains (group `grp`) of instance j, on a CTA of 256 threads that holds
+// `tmem` (L.cols columns) and the dynamic shared memory `smem` sized for the launch.  Returns
+// false when a bounded wait gave up (SAIS_ETIMEOUT recorded).  kSplit: the decision / noise
+// warpgroups move to 192 / 64 registers (a CTA launched with 128 per thread; once per CTA).
+template <int MC, int K, bool kHiLo, bool kTrack, bool kSplit>
+__device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp,
+                                           unsigned char *smem, uint32_t tmem,
+                                           const FieldLaunch &L, int32_t *status,
+                                           long long dec_wait_polls) {
     constexpr int kXW = K >= 32 ? K / 32 : 1;   // state words a block spans
-    constexpr uint32_t kFRing = f_ring(K);
-    const int j = a.work ? a.work[2 * blockIdx.x] : (int)blockIdx.y;
-    const int grp = a.work ? a.work[2 * blockIdx.x + 1] : (int)blockIdx.x;
+    const uint32_t kFRing = (uint32_t)L.ring;
+    const uint32_t tmem_cols = L.cols;
+    const int32_t max_n16 = L.max_n16;
     const InstDev *__restrict__ ip = a.inst + j;
     const int m = ip->m, nprime = ip->nprime, words = ip->words, n16 = ip->n16;
     const int kx = n16 / 16;                   // GEMM steps per block
+    // State chunks in TMEM (columns 8 kc); the rest in shared memory as SMEM A operands.
+    const int kxt = min(kx, (int)((tmem_cols - (uint32_t)K) / 8u));
     const int nb = (nprime + K - 1) / K;       // blocks per sweep
     const uint32_t tile_bytes = (uint32_t)K * (uint32_t)n16 * 2u;   // one BF16 term, one block
     const uint32_t diag_off = tile_bytes * (kHiLo ? 2u : 1u);
@@ -153,13 +159,17 @@ __global__ void __launch_bounds__(kFThreads, 2)
     // span one word past ceil(N'/32) (padding spins, always 0).
     const int xwords = (words + 1) & ~1;
     unsigned char *ring = smem;
-    uint32_t *xs = reinterpret_cast<uint32_t *>(smem + kFRing * slot_stride);
+    // State chunks beyond TMEM: chain c's 16 values of a chunk at (c/8) 256 + (c%8) 16 bytes
+    // (spins 0-7) and 128 bytes further (spins 8-15), the no-swizzle K-major A operand (LBO 128,
+    // SBO 256 bytes).
+    unsigned char *xsm = smem + kFRing * slot_stride;
+    uint32_t *xs = reinterpret_cast<uint32_t *>(xsm + (size_t)L.xs_chunks * kFXChunkBytes);
     float *thbuf = reinterpret_cast<float *>(xs + xwords * kFLanes);   // [2][K][128] noise
     uint64_t *bars = reinterpret_cast<uint64_t *>(thbuf + 2 * K * kFLanes);
     uint32_t *arrivals = reinterpret_cast<uint32_t *>(bars + kFBars);   // [3]
-    uint32_t *tmem_slot = arrivals + 3;
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(arrivals + 4);
 
+    // The barriers start afresh for every item (the previous item's waits are all over).
     if (threadIdx.x == 0) {
         for (int i = 0; i < kFBars; ++i)
             tc::mbar_init(&bars[i], (i >= kFBarTileFree && i < kFBarTileFree + 3) ? 4u : 1u);
@@ -168,18 +178,11 @@ __global__ void __launch_bounds__(kFThreads, 2)
         tc::fence_mbar_init();
         tc::fence_proxy_async_smem();
     }
-    if (warp == 0) {
-        tc::tmem_alloc(tmem_slot, tmem_cols);
-        tc::tmem_relinquish();
-    }
-    tc::tc_fence_before();
     __syncthreads();
-    tc::tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
     const uint32_t iter = a.iter_dev ? *a.iter_dev : a.iter;
 
     if (warp >= kFNoiseWarp0) {
-        asm volatile("setmaxnreg.dec.sync.aligned.u32 64;");
+        if (kSplit) asm volatile("setmaxnreg.dec.sync.aligned.u32 64;");
         // Noise warps: warp 4+q produces theta = atanh(rho) for the chains of decision warp q, up
         // to two blocks ahead, into a two-slot ring.  Lane 0 of warp 4 streams the W tiles.
         const int q = warp - kFNoiseWarp0;
@@ -253,7 +256,7 @@ __global__ void __launch_bounds__(kFThreads, 2)
             }
         __syncwarp();
     } else {
-        asm volatile("setmaxnreg.inc.sync.aligned.u32 192;");
+        if (kSplit) asm volatile("setmaxnreg.inc.sync.aligned.u32 192;");
         const int r = threadIdx.x;
         const int chain = grp * kFLanes + r;
         const bool valid = chain < (a.inst_chains ? a.inst_chains[j] : a.chains);
@@ -284,8 +287,14 @@ __global__ void __launch_bounds__(kFThreads, 2)
                 // descriptor's address field, which stays below 2^14 in shared memory)
                 uint64_t bd = tc::smem_desc(base + (uint32_t)term * tile_bytes, 128u, sbo);
                 for (int kc = 0; kc < kx; ++kc) {
-                    tc::mma_bf16_tmem_a(tmem + dcol, tmem + 8u * (uint32_t)kc, bd, idesc,
-                                        (term | kc) != 0 ? 1u : 0u);
+                    const uint32_t acc = (term | kc) != 0 ? 1u : 0u;
+                    if (kc < kxt) {
+                        tc::mma_bf16_tmem_a(tmem + dcol, tmem + 8u * (uint32_t)kc, bd, idesc, acc);
+                    } else {
+                        const uint64_t ad = tc::smem_desc(
+                            tc::smem_u32(xsm) + (uint32_t)(kc - kxt) * kFXChunkBytes, 128u, 256u);
+                        tc::mma_bf16(tmem + dcol, ad, bd, idesc, acc);
+                    }
                     bd += 16u;
                 }
             }
@@ -314,7 +323,14 @@ __global__ void __launch_bounds__(kFThreads, 2)
         for (int w = 0; w < xwords; ++w) xs[w * kFLanes + r] = 0u;
         {
             const uint32_t zero8[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-            for (int c0 = 0; c0 < 8 * kx; c0 += 8) tc::tmem_st8(lane_addr + (uint32_t)c0, zero8);
+            for (int c0 = 0; c0 < 8 * kxt; c0 += 8) tc::tmem_st8(lane_addr + (uint32_t)c0, zero8);
+            for (int c = kxt; c < kx; ++c) {
+                unsigned char *row = xsm + (size_t)(c - kxt) * kFXChunkBytes + (r >> 3) * 256 +
+                                     (r & 7) * 16;
+                *reinterpret_cast<uint4 *>(row) = make_uint4(0u, 0u, 0u, 0u);
+                *reinterpret_cast<uint4 *>(row + 128) = make_uint4(0u, 0u, 0u, 0u);
+            }
+            if (kx > kxt) tc::fence_proxy_async_smem();
         }
         bool ok = arrive_and_issue(&arrivals[2], 0u);
 
@@ -599,7 +615,17 @@ __global__ void __launch_bounds__(kFThreads, 2)
                             v8[e] = (((w0 >> sh) & 1u) ? 0x3F80u : 0u) |
                                     (((w0 >> (sh + 1)) & 1u) ? 0x3F800000u : 0u);
                         }
-                        tc::tmem_st8(lane_addr + (uint32_t)((s0 >> 1) + 8 * h8), v8);
+                        const int c = (s0 >> 4) + h8;   // the 16-spin chunk
+                        if (c < kxt) {
+                            tc::tmem_st8(lane_addr + (uint32_t)(8 * c), v8);
+                        } else {
+                            unsigned char *row = xsm + (size_t)(c - kxt) * kFXChunkBytes +
+                                                 (r >> 3) * 256 + (r & 7) * 16;
+                            *reinterpret_cast<uint4 *>(row) = make_uint4(v8[0], v8[1], v8[2], v8[3]);
+                            *reinterpret_cast<uint4 *>(row + 128) =
+                                make_uint4(v8[4], v8[5], v8[6], v8[7]);
+                            tc::fence_proxy_async_smem();   // for the next block's MMAs
+                        }
                     }
                 }
             }
@@ -685,12 +711,37 @@ __global__ void __launch_bounds__(kFThreads, 2)
             }
         }
     }
+    // Every TMEM access and copy of the item is over before the next item or the release.
     tc::tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
-        tc::tc_fence_after();
-        tc::tmem_dealloc(tmem, tmem_cols);
+    tc::tc_fence_after();
+    const bool done = *abort_flag == 0;
+    // A completed item's barriers have no operation pending: end them, so that the next item
+    // may initialise barriers or keep plain data there.  (After an abort the CTA stops.)
+    if (done && threadIdx.x == 0)
+        for (int i = 0; i < kFBars; ++i) tc::mbar_inval(&bars[i]);
+    return done;
+}
+
+// One launch of the block-field sampler: one work item per CTA (the work list's (instance,
+// chain group), or the grid's), TMEM held for the CTA's life.
+template <int MC, int K, bool kHiLo, bool kTrack>
+__global__ void __launch_bounds__(kFThreads, 2)
+    field_sampler_kernel(SampleArgs a, int32_t *status, long long dec_wait_polls, FieldLaunch L) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint32_t tmem_slot;
+    const int j = a.work ? a.work[2 * blockIdx.x] : (int)blockIdx.y;
+    const int grp = a.work ? a.work[2 * blockIdx.x + 1] : (int)blockIdx.x;
+    if (threadIdx.x < 32) {
+        tc::tmem_alloc(&tmem_slot, L.cols);
+        tc::tmem_relinquish();
     }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    field_item<MC, K, kHiLo, kTrack, true>(a, j, grp, smem, tmem, L, status, dec_wait_polls);
+    if (threadIdx.x < 32) tc::tmem_dealloc(tmem, L.cols);
 }
 
 template <int MC, int K, bool H, bool T>
@@ -701,7 +752,7 @@ cudaError_t field_launch(const SampleArgs &a, int32_t *status, long long polls,
                                          (int)L.smem);
     if (e != cudaSuccess) return e;
     const dim3 grid = a.work ? dim3(a.nwork, 1) : dim3((a.chains + kFLanes - 1) / kFLanes, a.count);
-    kern<<<grid, kFThreads, L.smem, s>>>(a, status, polls, L.cols, L.max_n16);
+    kern<<<grid, kFThreads, L.smem, s>>>(a, status, polls, L);
     return cudaGetLastError();
 }
 

@@ -150,20 +150,28 @@ cudaError_t launch_blocked_sampler(const SampleArgs &a, int max_m, int max_npad,
                                    cudaStream_t stream);
 size_t blocked_smem_bytes(int max_npad, int max_words, int block_k, bool stream_w, bool hilo);
 // Block-field sampler: each block's fields from one tcgen05 GEMM over the chain states held in
-// TMEM (W present, m <= 8, 8 ceil(n/16) + K <= 512 TMEM columns).
+// TMEM and, past 512 columns, in shared memory (W present, m <= 8, n <= 1024).
 size_t field_smem_bytes(int max_n16, int max_words, int block_k, bool hilo);
 uint32_t field_tmem_cols(int max_n16, int block_k);
 cudaError_t launch_field_sampler(const SampleArgs &a, int max_m, int max_n16, int max_words,
                                  int block_k, bool hilo, int32_t *status,
                                  long long dec_wait_polls, cudaStream_t stream);
+int field_ring(int max_n16, int max_words, int block_k, bool hilo);
+int field_xs_chunks(int max_n16, int block_k);
+// One persistent launch over a ragged batch's items (instance, chain group, kind): kind 0 / 1
+// block-field sampler on 128 chains (m <= 1 / m <= 8), kind 2 / 3 plain sampler on 256 chains
+// (m <= 8 / m <= 32); `head` is the device work counter (zeroed by the launch); max_n16_w is the
+// largest n16 among the quadratic instances (0 if none).  `stats` receives 4 uint64 per CTA of
+// the launch's ragged_grid(nitems, sms) CTAs: start and end on the global timer (ns), time
+// inside items (ns) and items run.
+constexpr int kRaggedFieldChains = 128, kRaggedPlainItemChains = 256;
+size_t ragged_smem_bytes(int max_n16_w, int max_words, bool hilo, int *ring);
+int ragged_grid(int nitems, int sms);
+cudaError_t launch_ragged(const SampleArgs &a, const int32_t *items, int32_t nitems,
+                          int32_t *head, unsigned long long *stats, int max_n16_w,
+                          int max_words, bool hilo, int32_t *status, long long dec_wait_polls,
+                          int sms, cudaStream_t stream);
 size_t plain_smem_bytes(int max_npad, int max_words, bool any_w, int cpb);
-// Blocked sampler on a CTA pair (thread-block cluster of two) for instances whose items do not
-// fit one SM's TMEM: W present, m <= 8, 128 <= n rounded up to 64 <= 1024.
-bool pair_eligible(int n, int m, bool has_w);
-bool pair_a_tmem(int n);   // the own MMAs' A operand fits in TMEM beside F (n <= 992)
-size_t pair_smem_bytes(int max_n, int max_words, bool hilo);
-cudaError_t launch_pair_sampler(const SampleArgs &a, int max_m, int max_n, int max_words, bool hilo,
-                                int32_t *status, long long dec_wait_polls, cudaStream_t st);
 constexpr size_t kMaxSmemPerBlock = 232448;   // 227 KB opt-in per CTA on sm_103
 cudaError_t launch_post(const PostArgs &a, cudaStream_t stream);
 cudaError_t launch_advance_iter(uint32_t *iter_dev, cudaStream_t stream);

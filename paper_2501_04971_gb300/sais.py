@@ -23,6 +23,7 @@ _f32, _f64, _P = ctypes.c_float, ctypes.c_double, ctypes.c_void_p
 SAIS_OK, SAIS_EINVAL, SAIS_ENOMEM, SAIS_ECUDA, SAIS_EOVERFLOW, SAIS_ETIMEOUT, \
     SAIS_EUNSUPPORTED = range(7)
 SAIS_PLAIN, SAIS_BLOCKED, SAIS_AUTO = 0, 1, 2
+SAIS_AUTO_PERSISTENT, SAIS_AUTO_GROUPS = 0, 1
 _VARIANTS = {"plain": SAIS_PLAIN, "blocked": SAIS_BLOCKED, "auto": SAIS_AUTO}
 
 
@@ -61,14 +62,16 @@ class sais_plan(ctypes.Structure):
 
 
 KERNEL_NAMES = {0: "plain", 1: "rank-k, W resident", 2: "rank-k, W streamed",
-                3: "block fields by GEMM", 4: "CTA pair", 5: "launch groups"}
+                3: "block fields by GEMM", 4: "launch groups", 5: "persistent"}
 
 
 class sais_tuning(ctypes.Structure):
     _fields_ = [("groups", _i32), ("blocked_instances", _i32), ("plain_instances", _i32),
                 ("reserved", _i32), ("group_variant", _i32 * 16), ("group_block_k", _i32 * 16),
                 ("group_chains_per_cta", _i32 * 16), ("group_size", _i32 * 16),
-                ("group_ms", _f64 * 16), ("group_spin_updates", _i64 * 16)]
+                ("group_ms", _f64 * 16), ("group_spin_updates", _i64 * 16),
+                ("persistent_ok", _i32), ("persistent", _i32), ("persistent_ms", _f64),
+                ("groups_ms", _f64)]
 
 
 class sais_solve_result(ctypes.Structure):
@@ -97,6 +100,8 @@ _SIGS = {
     "sais_solve": [_P, ctypes.POINTER(sais_solve_params), ctypes.POINTER(sais_solve_result), _P],
     "sais_synchronize": [_P, _P],
     "sais_sample_plan": [_P, ctypes.POINTER(sais_sample_params), ctypes.POINTER(sais_plan)],
+    "sais_set_auto_mode": [_P, ctypes.c_int32],
+    "sais_persistent_stats": [_P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _P],
     "sais_set_instance_chains": [_P, _P],
     "sais_autotune": [_P, _i32, _i32, ctypes.POINTER(sais_tuning), _P],
     "sais_solve_noalloc": [_P, ctypes.POINTER(sais_solve_params),
@@ -246,6 +251,18 @@ def sais_sample_plan(h, prm) -> sais_plan:
     return out
 
 
+def sais_set_auto_mode(h, mode: int):
+    _check(lib().sais_set_auto_mode(h, mode), "sais_set_auto_mode")
+
+
+def sais_persistent_stats(h, cap: int, stream_ptr) -> np.ndarray:
+    out = np.zeros((cap, 4), np.uint64)
+    n = ctypes.c_int32(0)
+    _check(lib().sais_persistent_stats(h, out.ctypes.data_as(_P), cap, ctypes.byref(n),
+                                       stream_ptr), "sais_persistent_stats")
+    return out[:min(cap, n.value)]
+
+
 _allocator_keep: list = []
 
 
@@ -378,6 +395,20 @@ class Problem:
         return {"kernel": KERNEL_NAMES.get(pl.kernel, str(pl.kernel)), "block_k": pl.block_k,
                 "chains_per_cta": pl.chains_per_cta, "hilo": bool(pl.hilo)}
 
+    def set_auto_mode(self, mode: str):
+        """sais_set_auto_mode: "persistent" (one launch when the batch fits it) or "groups"."""
+        sais_set_auto_mode(self.handle, {"persistent": SAIS_AUTO_PERSISTENT,
+                                         "groups": SAIS_AUTO_GROUPS}[mode])
+
+    def persistent_stats(self, stream=None) -> dict:
+        """sais_persistent_stats of the last persistent launch: per CTA start / end (global timer,
+        ns), busy ns and items, plus the busy fraction of each CTA over the launch's span."""
+        r = sais_persistent_stats(self.handle, 1024, _stream_ptr(stream)).astype(np.int64)
+        span = int(r[:, 1].max() - r[:, 0].min()) if len(r) else 0
+        busy = r[:, 2] / span if span > 0 else np.zeros(len(r))
+        return {"ctas": len(r), "start_ns": r[:, 0], "end_ns": r[:, 1], "busy_ns": r[:, 2],
+                "items": r[:, 3], "span_ns": span, "busy_fraction": busy}
+
     def blocked_kernel(self, block_k: int, chains: int = 128) -> str:
         """Name of the kernel the blocked sampler runs at this block size."""
         return self.plan(chains, "blocked", block_k)["kernel"]
@@ -402,7 +433,9 @@ class Problem:
                 "variant": list(t.group_variant)[:g], "block_k": list(t.group_block_k)[:g],
                 "chains_per_cta": list(t.group_chains_per_cta)[:g],
                 "size": list(t.group_size)[:g], "ms": list(t.group_ms)[:g],
-                "spin_updates": list(t.group_spin_updates)[:g]}
+                "spin_updates": list(t.group_spin_updates)[:g],
+                "persistent_ok": bool(t.persistent_ok), "persistent": bool(t.persistent),
+                "persistent_ms": t.persistent_ms, "groups_ms": t.groups_ms}
 
     @property
     def feature_rows(self) -> int:

@@ -1,11 +1,11 @@
 """Blocked samplers (tcgen05) against the plain sampler and the oracle.
 
-Three kernels: rank-k updates of fields resident in TMEM (N'_pad + K <= 512), block fields from
-a GEMM over the chain states (up to n = 992 items, and K = 32 streamed or hi/lo, K = 64), and a
-CTA pair splitting the fields beyond that.  All are exact (integer products and sums below 2^24
-in FP32), so every blocked sampler must make every decision the plain sampler makes: identical
-states after every sweep, identical costs, constraint values and feasibility, and all identical
-to the CPU oracle.
+Two kernels: rank-k updates of fields resident in TMEM (N'_pad + K <= 512), and block fields
+from a GEMM over the chain states (up to n = 1024 items, the states past 496 TMEM columns in
+shared memory; and K = 32 streamed or hi/lo, K = 64).  Both are exact (integer products and
+sums below 2^24 in FP32), so every blocked sampler must make every decision the plain sampler
+makes: identical states after every sweep, identical costs, constraint values and feasibility,
+and all identical to the CPU oracle.
 """
 import numpy as np
 import pytest
@@ -172,12 +172,12 @@ def test_blocked_streamed_and_hilo(case):
 
 
 @pytest.mark.parametrize("case", ["n500", "n1000_hilo", "mixed_ragged", "n640_trace", "n1020",
-                                  "n990_tail", "n1000_mixed_pair", "n700_default_k"])
+                                  "n990_tail", "n1000_mixed", "n700_default_k"])
 def test_large_instances_equal_plain_and_oracle(case):
-    """Large instances: the block-field kernel (one CTA per SM) up to n = 992 items, whose state
-    columns then fill the SM's TMEM; beyond that the fields split over a CTA pair (cluster of
-    two), flips exchanged through distributed shared memory (n1000_hilo, n1020,
-    n1000_mixed_pair).  All identical to the plain sampler and the oracle."""
+    """Large instances on the block-field kernel (one CTA per SM): up to n = 992 items the state
+    columns fit TMEM beside the fields; beyond, the last 16-spin chunks live in shared memory as
+    the MMA's A operand (n1000_hilo, n1020, n1000_mixed).  All identical to the plain sampler
+    and the oracle."""
     if case == "n500":
         _compare([wl.qkp(500, 0.5, 31)], [[1.0]], C=128, T=60, beta=10.0, seed=13, it=1,
                  block_k=16, oracle_chains=(0, 2))
@@ -197,7 +197,7 @@ def test_large_instances_equal_plain_and_oracle(case):
     elif case == "n990_tail":   # n = 990: 496 state columns and 16 fields, all of TMEM
         _compare([wl.qkp(990, 0.75, 39), wl.qkp(250, 0.5, 40)], [[0.6], [1.0]], C=128, T=12,
                  beta=10.0, seed=18, it=1, block_k=16, oracle_chains=(0, 1))
-    elif case == "n1000_mixed_pair":   # CTA pairs: the largest instance exceeds one SM
+    elif case == "n1000_mixed":   # a batch whose largest instance needs state chunks in SMEM
         _compare([wl.qkp(1000, 0.5, 44), wl.qkp(200, 0.5, 45)], [[1.0], [0.7]], C=128, T=12,
                  beta=10.0, seed=27, it=2, block_k=16, oracle_chains=(0, 1))
     else:                   # the library's block size (K = 32 for the block-field kernel)
@@ -207,7 +207,8 @@ def test_large_instances_equal_plain_and_oracle(case):
 
 @pytest.mark.parametrize("n", [600, 1000])
 def test_large_timeout_path_reports_and_recovers(n):
-    """The timeout path of the block-field kernel (n = 600) and of the CTA pair (n = 1000)."""
+    """The timeout path of the block-field kernel, states in TMEM (n = 600) and partly in
+    shared memory (n = 1000)."""
     inst = wl.qkp(n, 0.5, 37)
     prob = sais.Problem(inst)
     lam = _lam(prob, [[0.5]])
@@ -254,9 +255,9 @@ def test_blocked_constraint_counts(case):
 @pytest.mark.parametrize("n", [520, 1000])
 @pytest.mark.parametrize("case", ["one_chain", "m8", "three_clusters"])
 def test_large_instance_extremes(case, n):
-    """One CTA at n = 520 and the CTA pair at n = 1000, each with a single valid chain, with 8
-    constraints (the pair's follower reads the coefficients past the first two from global
-    memory), and with 300 chains (three CTAs or clusters per instance, the last one ragged)."""
+    """The block-field kernel at n = 520 and n = 1000 (state chunks in shared memory), each with
+    a single valid chain, with 8 constraints, and with 300 chains (three CTAs per instance, the
+    last one ragged)."""
     if case == "one_chain":
         _compare([wl.qkp(n, 0.5, 51)], [[1.0]], C=1, T=20, beta=10.0, seed=22, it=0,
                  block_k=16)
@@ -271,7 +272,7 @@ def test_large_instance_extremes(case, n):
 
 def test_blocked_unsupported_cases():
     cases = ([([wl.mkp(40, 3, 1)], 16), ([wl.qkp(1100, 0.25, 2)], 16),
-              ([wl.qkp(1000, 0.5, 3), wl.qkp(40, 0.5, 4)], 16),
+              ([wl.qkp(1030, 0.5, 3), wl.qkp(40, 0.5, 4)], 16),
               ([_with_constraints(wl.qkp(100, 0.5, 5), 3, 5)], 64),
               ([wl.qkp(1000, 0.5, 6)], 64)])
     for insts, k in cases:

@@ -3,7 +3,7 @@
 * sais_sample_run_best: per chain, the best feasible sweep-end state, its cost, its sweep and
   the number of feasible sweep ends equal the oracle's (or_run_best over the oracle's own
   sweep trace), for the plain sampler, the single-CTA blocked sampler (W resident and
-  streamed hi/lo), the CTA-pair sampler and SAIS_AUTO over a ragged batch;
+  streamed hi/lo), the block-field sampler and SAIS_AUTO over a ragged batch;
 * capacity tightening B' < B (Sec. IV-B): the sampled problem is built from B', feasibility and
   the kept best use B, identical to the oracle; Algorithm 1 with both options matches the
   oracle's solve bit for bit.
@@ -136,15 +136,16 @@ def test_run_best_blocked_hilo_tightened():
     assert _run_best_vs_oracle([inst], [[150.0, 150.0]], 128, 120, 10.0, 5, 0, "blocked") > 20
 
 
-def test_run_best_pair():
-    """CTA-pair sampler (N=500 items beyond one SM's TMEM), 128 chains x 16 sweeps: CTA 1's
-    partial costs cross distributed shared memory at every sweep end."""
-    insts = [wl.qkp(500, 0.5, 11)]
+@pytest.mark.parametrize("n", [500, 1010])
+def test_run_best_large(n):
+    """The block-field kernel (n = 500; n = 1010 with state chunks in shared memory), 128
+    chains x 16 sweeps: the cost follows every flip and each sweep end is checked."""
+    insts = [wl.qkp(n, 0.5, 11)]
     _run_best_vs_oracle(insts, [[1.0]], 128, 16, 10.0, 2, 0, "blocked")
 
 
 def test_run_best_auto_ragged():
-    """SAIS_AUTO over a ragged batch (blocked, CTA-pair and plain groups) equals the plain
+    """SAIS_AUTO over a ragged batch (rank-k, block-field and plain work) equals the plain
     sampler's run-best outputs, and the plain sampler equals the oracle on two members."""
     insts = [wl.qkp(150, 0.5, 1), wl.qkp(520, 0.25, 2), _tighten(wl.mkp(90, 5, 3), 0.85),
              wl.qkp(60, 1.0, 4)]
