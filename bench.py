@@ -86,7 +86,66 @@ def parse():
     ap.add_argument("--no-ksweep", action="store_true")
     ap.add_argument("--ksweep-sweeps", type=int, default=200)
     ap.add_argument("--ragged-tune-sweeps", type=int, default=50)
+    ap.add_argument("--kernel-case", choices=sorted(KERNEL_CASES),
+                    help="run one small sampler launch (after --warmup launches) and exit: the "
+                         "cases the committed ncu summaries were captured on")
     return ap.parse_args()
+
+
+# name: (instances, chains, sweeps, beta_max, variant, block_k); sizes keep an ncu capture short
+# while W stays larger than L2 where the kernel streams it.
+KERNEL_CASES = {
+    "rankk_qkp300": ("152 QKP N=300 d=0.5", 128, 200, 10.0, "blocked", 16),
+    "field_qkp900": ("152 QKP N=900 d=0.5", 128, 30, 10.0, "blocked", 16),
+    "field_qkp1000_hilo": ("152 QKP N=1000 d=0.5, profits <= 1e4", 128, 20, 10.0, "blocked", 16),
+    "field_qkp300_k32": ("304 QKP N=300 d=0.5", 128, 40, 10.0, "blocked", 32),
+    "plain_qkp300": ("152 QKP N=300 d=0.5", 128, 50, 10.0, "plain", 0),
+    "plain_mkp500_m30": ("32 MKP N=500 m=30", 256, 20, 50.0, "plain", 0),
+    "persistent_ragged": ("the ragged batch: 384 QKP N~U[100,1000] (profits <= 1e4) + 128 MKP, "
+                          "chains U[64,256]", 256, 20, 10.0, "auto", 0),
+}
+
+
+def kernel_case(a, sais, torch):
+    """One of KERNEL_CASES: `a.warmup` launches, then one launch timed with CUDA events."""
+    from paper_2501_04971_gb300 import workloads as wl
+    what, C, T, beta, variant, k = KERNEL_CASES[a.kernel_case]
+    name = a.kernel_case
+    counts = None
+    if name == "persistent_ragged":
+        insts = wl.ragged_batch()
+        counts = np.random.default_rng(0x524147).integers(64, 257, len(insts)).astype(np.int32)
+    elif name.startswith("plain_mkp"):
+        insts = [wl.mkp(500, 30, s) for s in range(32)]
+    else:
+        n = int(name.split("qkp")[1].split("_")[0])
+        cnt = 304 if name.endswith("_k32") else 152
+        pm = 10000 if name.endswith("_hilo") else 100
+        insts = [wl.qkp(n, 0.5, s, profit_max=pm) for s in range(cnt)]
+    prob = sais.Problem(insts)
+    if counts is not None:
+        prob.set_instance_chains(counts)
+    lam = torch.full((prob.count * prob.m_stride,), 0.5, device="cuda")
+    out = prob.alloc_outputs(C)
+    kernel = prob.plan(C, variant, k)["kernel"]
+    for _ in range(max(1, a.warmup)):
+        prob.sample(lam, C, T, beta, 1, 0, variant=variant, block_k=k, out=out)
+    prob.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    prob.sample(lam, C, T, beta, 1, 0, variant=variant, block_k=k, out=out)
+    e1.record()
+    prob.synchronize()
+    ms = e0.elapsed_time(e1)
+    per_inst = counts if counts is not None else np.full(prob.count, C)
+    upd = int(sum(s.n_spins * int(c) for s, c in zip(prob.scalars, per_inst))) * T
+    line = {"case": name, "workload": what, "chains": C, "sweeps": T, "kernel": kernel,
+            "ms": ms, "spin_updates": upd, "rate": upd / (ms / 1e3), "unit": UNIT}
+    if kernel == "persistent":
+        st = prob.persistent_stats()
+        line["busy_fraction_mean"] = float(st["busy_fraction"].mean())
+    print(json.dumps(line))
+    prob.close()
 
 
 def workload(per_density: int, rank: int):
@@ -781,6 +840,8 @@ def main():
 
     if a.make_best_known:
         return make_best_known(a, sais, torch)
+    if a.kernel_case:
+        return kernel_case(a, sais, torch)
     insts = workload(a.per_density, rank)
     prob = sais.Problem(insts, device=local)
     nspins = np.array([s.n_spins for s in prob.scalars], dtype=np.int64)

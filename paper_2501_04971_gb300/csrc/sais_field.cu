@@ -11,22 +11,22 @@ cudaError_t launch_field_wide(const SampleArgs &a, int max_m, int block_k, bool 
 
 // TMEM columns: the power of two >= the state columns (8 per 16 item spins) plus K fields, at
 // most 512 (state chunks beyond them live in shared memory).
-uint32_t field_tmem_cols(int max_n16, int block_k) {
+uint32_t field_tmem_cols(int max_n16, int dcols) {
     uint32_t cols = 32;
-    while (cols < 512u && cols < (uint32_t)(max_n16 / 2 + block_k)) cols <<= 1;
+    while (cols < 512u && cols < (uint32_t)(max_n16 / 2 + dcols)) cols <<= 1;
     return cols;
 }
 
-// 16-spin state chunks that do not fit TMEM beside the K field columns.
-int field_xs_chunks(int max_n16, int block_k) {
-    const int in_tmem = (int)(field_tmem_cols(max_n16, block_k) - (uint32_t)block_k) / 8;
+// 16-spin state chunks that do not fit TMEM beside the dcols accumulator columns.
+int field_xs_chunks(int max_n16, int dcols) {
+    const int in_tmem = (int)(field_tmem_cols(max_n16, dcols) - (uint32_t)dcols) / 8;
     return std::max(0, max_n16 / 16 - in_tmem);
 }
 
 size_t field_smem_ring(int max_n16, int max_words, int block_k, bool hilo, int ring) {
     const size_t slot = (size_t)block_k * max_n16 * 2 * (hilo ? 2 : 1) + (size_t)block_k * block_k * 4;
     const size_t xwords = (size_t)((max_words + 1) & ~1);   // as the kernel rounds them
-    return ring * slot + (size_t)field_xs_chunks(max_n16, block_k) * kFXChunkBytes +
+    return ring * slot + (size_t)field_xs_chunks(max_n16, field_dcols(block_k, hilo)) * kFXChunkBytes +
            xwords * kFLanes * 4 + (size_t)2 * block_k * kFLanes * 4 + kFBars * 8 + 32;
 }
 
@@ -47,10 +47,10 @@ cudaError_t launch_field_sampler(const SampleArgs &a, int max_m, int max_n16, in
     // launch; the shared-memory request is raised so that no more than that fit on one SM (a
     // CTA's TMEM allocation would otherwise wait for another CTA's release).
     FieldLaunch L;
-    L.cols = field_tmem_cols(max_n16, block_k);
+    L.cols = field_tmem_cols(max_n16, field_dcols(block_k, hilo));
     L.max_n16 = max_n16;
     L.ring = field_ring(max_n16, max_words, block_k, hilo);
-    L.xs_chunks = field_xs_chunks(max_n16, block_k);
+    L.xs_chunks = field_xs_chunks(max_n16, field_dcols(block_k, hilo));
     const size_t per_sm = 228 * 1024, max_ctas = std::min<size_t>(2, 512 / L.cols);
     L.smem = field_smem_bytes(max_n16, max_words, block_k, hilo);
     const size_t floor_smem = per_sm / (max_ctas + 1) + 1;

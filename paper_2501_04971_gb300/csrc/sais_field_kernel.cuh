@@ -106,10 +106,18 @@ __device__ __forceinline__ bool f_wait_warp(uint64_t *bar, uint32_t parity,
     }
 }
 
-// 32 lanes x K columns of the fields (warp-collective), waited for.
-template <int K>
+// 32 lanes x K columns of the fields (warp-collective), waited for.  With the hi/lo split the
+// accumulator holds the hi products in its first K columns and the lo products in the next K;
+// their sum is exact (integers below 2^24).
+template <int K, bool kHiLo>
 __device__ __forceinline__ void f_load_fields(uint32_t taddr, float (&r)[K]) {
-    if constexpr (K == 16) {
+    if constexpr (K == 16 && kHiLo) {   // both terms in one load
+        float v[32];
+        tc::tmem_ld32(taddr, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) r[i] = v[i] + v[16 + i];
+        return;
+    } else if constexpr (K == 16) {
         tc::tmem_ld16(taddr, r);
     } else {
 #pragma unroll
@@ -120,6 +128,24 @@ __device__ __forceinline__ void f_load_fields(uint32_t taddr, float (&r)[K]) {
             for (int i = 0; i < 32; ++i) r[c + i] = v[i];
         }
     }
+    if constexpr (kHiLo && K != 16) {
+#pragma unroll
+        for (int c = 0; c < K; c += 16) {
+            float v[16];
+            tc::tmem_ld16(taddr + (uint32_t)(K + c), v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) r[c + i] += v[i];
+        }
+    }
+}
+
+// Round and slot of tile u in a ring of 2 or 3 slots (a shift or a multiply-high, not a
+// division by a runtime value).
+__device__ __forceinline__ uint32_t f_round(uint32_t u, uint32_t ring) {
+    return ring == 3u ? u / 3u : u >> 1;
+}
+__device__ __forceinline__ uint32_t f_slot(uint32_t u, uint32_t ring) {
+    return u - f_round(u, ring) * ring;
 }
 
 template <int K>
@@ -128,14 +154,15 @@ __device__ __forceinline__ const float *f_diag_image(const InstDev *ip) {
 }
 
 // One work item: 128 chains (group `grp`) of instance j, on a CTA of 256 threads that holds
-// `tmem` (L.cols columns) and the dynamic shared memory `smem` sized for the launch.  Returns
+// `tmem` (L.cols columns) and dynamic shared memory sized for the launch (declared here, not
+// passed as a pointer, so that every access stays a shared-memory access).  Returns
 // false when a bounded wait gave up (SAIS_ETIMEOUT recorded).  kSplit: the decision / noise
 // warpgroups move to 192 / 64 registers (a CTA launched with 128 per thread; once per CTA).
 template <int MC, int K, bool kHiLo, bool kTrack, bool kSplit>
-__device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp,
-                                           unsigned char *smem, uint32_t tmem,
+__device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp, uint32_t tmem,
                                            const FieldLaunch &L, int32_t *status,
                                            long long dec_wait_polls) {
+    extern __shared__ __align__(1024) unsigned char smem[];
     constexpr int kXW = K >= 32 ? K / 32 : 1;   // state words a block spans
     const uint32_t kFRing = (uint32_t)L.ring;
     const uint32_t tmem_cols = L.cols;
@@ -143,14 +170,18 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp,
     const InstDev *__restrict__ ip = a.inst + j;
     const int m = ip->m, nprime = ip->nprime, words = ip->words, n16 = ip->n16;
     const int kx = n16 / 16;                   // GEMM steps per block
+    // Accumulator columns: K, or 2K with the hi/lo split, whose two W tiles lie one after the
+    // other in shared memory and so form one B operand of N = 2K (an MMA costs the same for any
+    // N up to 128): one GEMM computes both terms.
+    constexpr int KD = kHiLo ? 2 * K : K;
     // State chunks in TMEM (columns 8 kc); the rest in shared memory as SMEM A operands.
-    const int kxt = min(kx, (int)((tmem_cols - (uint32_t)K) / 8u));
+    const int kxt = min(kx, (int)((tmem_cols - (uint32_t)KD) / 8u));
     const int nb = (nprime + K - 1) / K;       // blocks per sweep
     const uint32_t tile_bytes = (uint32_t)K * (uint32_t)n16 * 2u;   // one BF16 term, one block
     const uint32_t diag_off = tile_bytes * (kHiLo ? 2u : 1u);
     const uint32_t slot_stride =
         (uint32_t)K * (uint32_t)max_n16 * 2u * (kHiLo ? 2u : 1u) + (uint32_t)(K * K * 4);
-    const uint32_t dcol = tmem_cols - (uint32_t)K;   // the fields D: last K columns
+    const uint32_t dcol = tmem_cols - (uint32_t)KD;   // the fields D: last KD columns
     const uint32_t total = (uint32_t)a.sweeps * (uint32_t)nb + (uint32_t)nb;   // + readout pass
     const uint32_t ndec = (uint32_t)a.sweeps * (uint32_t)nb;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -198,9 +229,10 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp,
         // W tile of block u (decision or readout) into slot u % kFRing, once that slot's previous
         // block (u - kFRing) is done.
         auto stage = [&](uint32_t u) -> bool {
-            const uint32_t ts = u % kFRing;
+            const uint32_t ts = f_slot(u, kFRing);
             if (u >= kFRing &&
-                !f_wait(&bars[kFBarTileFree + ts], ((u / kFRing) - 1u) & 1u, abort_flag, status, 0))
+                !f_wait(&bars[kFBarTileFree + ts], (f_round(u, kFRing) - 1u) & 1u, abort_flag,
+                        status, 0))
                 return false;
             const uint32_t b = u < ndec ? u % (uint32_t)nb : u - ndec;
             unsigned char *dst = ring + ts * slot_stride;
@@ -271,32 +303,33 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp,
         const float *__restrict__ asum = ip->asum;
         const float4 *__restrict__ spinc = ip->spinc;
         const float *lam = a.lambda + (size_t)j * a.m_stride;
-        const uint32_t idesc = tc::idesc_bf16_f32(128, (uint32_t)K);
+        const uint32_t idesc = tc::idesc_bf16_f32(128, (uint32_t)KD);
 
-        // The GEMM of block u: D = X W[:, blk], kx steps per BF16 term, then one commit.  Issued
-        // by one thread once the tile is in shared memory (bounded wait).
+        // The GEMM of block u: D = X [W_hi | W_lo][:, blk], kx steps, then one commit.  Issued by
+        // one thread once the tile is in shared memory (bounded wait).
         auto issue_gemm = [&](uint32_t u) -> bool {
-            const uint32_t ts = u % kFRing;
-            if (!f_wait(&bars[kFBarTile + ts], (u / kFRing) & 1u, abort_flag, status, 0))
+            const uint32_t ts = f_slot(u, kFRing);
+            if (!f_wait(&bars[kFBarTile + ts], f_round(u, kFRing) & 1u, abort_flag, status, 0))
                 return false;
             const uint32_t base = tc::smem_u32(ring + ts * slot_stride);
+            // 8-row groups of the B operand every 16 n16 bytes: the lo tile (tile_bytes after
+            // the hi one) continues the hi tile's row groups.
             const uint32_t sbo = (uint32_t)n16 * 16u;
-#pragma unroll
-            for (int term = 0; term < (kHiLo ? 2 : 1); ++term) {
-                // descriptor of step kc: the start address advances by 256 bytes (16 in the
-                // descriptor's address field, which stays below 2^14 in shared memory)
-                uint64_t bd = tc::smem_desc(base + (uint32_t)term * tile_bytes, 128u, sbo);
-                for (int kc = 0; kc < kx; ++kc) {
-                    const uint32_t acc = (term | kc) != 0 ? 1u : 0u;
-                    if (kc < kxt) {
-                        tc::mma_bf16_tmem_a(tmem + dcol, tmem + 8u * (uint32_t)kc, bd, idesc, acc);
-                    } else {
-                        const uint64_t ad = tc::smem_desc(
-                            tc::smem_u32(xsm) + (uint32_t)(kc - kxt) * kFXChunkBytes, 128u, 256u);
-                        tc::mma_bf16(tmem + dcol, ad, bd, idesc, acc);
-                    }
-                    bd += 16u;
-                }
+            // descriptor of step kc: the start address advances by 256 bytes (16 in the
+            // descriptor's address field, which stays below 2^14 in shared memory)
+            uint64_t bd = tc::smem_desc(base, 128u, sbo);
+            // A from TMEM for the first kxt chunks, then from shared memory (two loops: no
+            // branch per MMA)
+            for (int kc = 0; kc < kxt; ++kc) {
+                tc::mma_bf16_tmem_a(tmem + dcol, tmem + 8u * (uint32_t)kc, bd, idesc,
+                                    kc != 0 ? 1u : 0u);
+                bd += 16u;
+            }
+            uint64_t ad = tc::smem_desc(tc::smem_u32(xsm), 128u, 256u);
+            for (int kc = kxt; kc < kx; ++kc) {
+                tc::mma_bf16(tmem + dcol, ad, bd, idesc, kc != 0 ? 1u : 0u);
+                ad += kFXChunkBytes >> 4;
+                bd += 16u;
             }
             tc::mma_commit(&bars[kFBarMma]);
             return true;
@@ -369,7 +402,7 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp,
             const uint32_t t = readout ? (uint32_t)a.sweeps : it / (uint32_t)nb;
             const int b = (int)(readout ? it - ndec : it % (uint32_t)nb);
             const int s0 = b * K;
-            const uint32_t ts = it % kFRing;
+            const uint32_t ts = f_slot(it, kFRing);
             const uint32_t slot = it & 1u;
             const float *thb = thbuf + slot * K * kFLanes + r;
             // K = 16: the block's per-spin data, loaded before the wait for the block's GEMM,
@@ -383,7 +416,7 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp,
                 // in-block corrections).
                 if (!f_wait_warp(&bars[kFBarNoise + 2 * warp + slot], (it >> 1) & 1u, abort_flag,
                                  status, dec_wait_polls) ||
-                    !f_wait_warp(&bars[kFBarTile + ts], (it / kFRing) & 1u, abort_flag, status,
+                    !f_wait_warp(&bars[kFBarTile + ts], f_round(it, kFRing) & 1u, abort_flag, status,
                                  dec_wait_polls)) {
                     ok = false;
                     break;
@@ -404,7 +437,7 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp,
                 break;
             }
             tc::tc_fence_after();
-            f_load_fields<K>(lane_addr + dcol, Fr);
+            f_load_fields<K, kHiLo>(lane_addr + dcol, Fr);
 #pragma unroll
             for (int ii = 0; ii < K; ++ii) Fr[ii] += __ldg(hF + s0 + ii);   // exact integers
             const int wi = s0 >> 5, sb = s0 & 31;
@@ -538,12 +571,17 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp,
 #pragma unroll 1
                 for (int ii = 0; ii < K; ++ii) {
                     const int s = s0 + ii;
-                    uint32_t fv;
+                    uint32_t fv, fl_lo = 0u;
                     asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
                                  : "=r"(fv)
                                  : "r"(lane_addr + dcol + (uint32_t)ii));
+                    if (kHiLo)
+                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
+                                     : "=r"(fl_lo)
+                                     : "r"(lane_addr + dcol + (uint32_t)(K + ii)));
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                     float Fi = __uint_as_float(fv) + __ldg(hF + s);
+                    if (kHiLo) Fi += __uint_as_float(fl_lo);
                     uint64_t fl = (bn ^ bo) & ((1ull << ii) - 1ull);
                     while (fl) {
                         const int i2 = __ffsll((long long)fl) - 1;
@@ -729,18 +767,21 @@ template <int MC, int K, bool kHiLo, bool kTrack>
 __global__ void __launch_bounds__(kFThreads, 2)
     field_sampler_kernel(SampleArgs a, int32_t *status, long long dec_wait_polls, FieldLaunch L) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint32_t tmem_slot;
+    // The TMEM address is written to the first word of shared memory and read by every thread
+    // before the item starts to use that memory.
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem);
     const int j = a.work ? a.work[2 * blockIdx.x] : (int)blockIdx.y;
     const int grp = a.work ? a.work[2 * blockIdx.x + 1] : (int)blockIdx.x;
     if (threadIdx.x < 32) {
-        tc::tmem_alloc(&tmem_slot, L.cols);
+        tc::tmem_alloc(tmem_slot, L.cols);
         tc::tmem_relinquish();
     }
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
-    const uint32_t tmem = tmem_slot;
-    field_item<MC, K, kHiLo, kTrack, true>(a, j, grp, smem, tmem, L, status, dec_wait_polls);
+    const uint32_t tmem = *tmem_slot;
+    __syncthreads();
+    field_item<MC, K, kHiLo, kTrack, true>(a, j, grp, tmem, L, status, dec_wait_polls);
     if (threadIdx.x < 32) tc::tmem_dealloc(tmem, L.cols);
 }
 

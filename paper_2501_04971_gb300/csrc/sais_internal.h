@@ -152,12 +152,15 @@ size_t blocked_smem_bytes(int max_npad, int max_words, int block_k, bool stream_
 // Block-field sampler: each block's fields from one tcgen05 GEMM over the chain states held in
 // TMEM and, past 512 columns, in shared memory (W present, m <= 8, n <= 1024).
 size_t field_smem_bytes(int max_n16, int max_words, int block_k, bool hilo);
-uint32_t field_tmem_cols(int max_n16, int block_k);
+// Accumulator columns of the block-field GEMM: K, or 2K with the hi/lo split (both terms in one
+// MMA of N = 2K).
+inline int field_dcols(int block_k, bool hilo) { return hilo ? 2 * block_k : block_k; }
+uint32_t field_tmem_cols(int max_n16, int dcols);
 cudaError_t launch_field_sampler(const SampleArgs &a, int max_m, int max_n16, int max_words,
                                  int block_k, bool hilo, int32_t *status,
                                  long long dec_wait_polls, cudaStream_t stream);
 int field_ring(int max_n16, int max_words, int block_k, bool hilo);
-int field_xs_chunks(int max_n16, int block_k);
+int field_xs_chunks(int max_n16, int dcols);
 // One persistent launch over a ragged batch's items (instance, chain group, kind): kind 0 / 1
 // block-field sampler on 128 chains (m <= 1 / m <= 8), kind 2 / 3 plain sampler on 256 chains
 // (m <= 8 / m <= 32); `head` is the device work counter (zeroed by the launch); max_n16_w is the

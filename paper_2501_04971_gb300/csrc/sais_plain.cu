@@ -8,10 +8,9 @@ namespace {
 
 template <int MC>
 __global__ void __launch_bounds__(128) plain_sampler_kernel(SampleArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int j = a.work ? a.work[2 * blockIdx.x] : (int)blockIdx.y;
     const int grp = a.work ? a.work[2 * blockIdx.x + 1] : (int)blockIdx.x;
-    plain_item<MC>(a, j, grp, (int)blockDim.x, (int)threadIdx.x, smem_raw);
+    plain_item<MC>(a, j, grp, (int)blockDim.x, (int)threadIdx.x);
 }
 
 template <int MC>

@@ -35,10 +35,11 @@ namespace sais {
 namespace {
 
 // One work item: chains grp cpb .. grp cpb + cpb - 1 of instance j, one per thread (thread tid
-// of the item's cpb), shared memory `smem_raw` sized by plain_smem_bytes for cpb chains.
+// of the item's cpb), dynamic shared memory sized by plain_smem_bytes for cpb chains (declared
+// here, not passed as a pointer, so that every access stays a shared-memory access).
 template <int MC>
-__device__ __forceinline__ void plain_item(const SampleArgs &a, int j, int grp, int cpb, int tid,
-                                           unsigned char *smem_raw) {
+__device__ __forceinline__ void plain_item(const SampleArgs &a, int j, int grp, int cpb, int tid) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const InstDev *__restrict__ ip = a.inst + j;
     const int n = ip->n, m = ip->m, nprime = ip->nprime, npad = ip->npad, words = ip->words;
     const int m4 = ip->m4;

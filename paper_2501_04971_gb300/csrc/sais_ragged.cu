@@ -28,7 +28,7 @@ cudaError_t launch_ragged(const SampleArgs &a, const int32_t *items, int32_t nit
     FieldLaunch L;
     L.cols = 512;
     L.max_n16 = std::max(16, max_n16_w);
-    L.xs_chunks = max_n16_w > 0 ? field_xs_chunks(max_n16_w, 16) : 0;
+    L.xs_chunks = max_n16_w > 0 ? field_xs_chunks(max_n16_w, field_dcols(16, hilo)) : 0;
     int ring = 3;
     L.smem = ragged_smem_bytes(max_n16_w, max_words, hilo, &ring);
     L.ring = ring;

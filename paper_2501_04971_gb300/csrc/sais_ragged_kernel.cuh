@@ -37,42 +37,44 @@ __global__ void __launch_bounds__(kRaggedThreads, 1)
                   unsigned long long *stats, FieldLaunch L, int32_t *status,
                   long long dec_wait_polls) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint32_t tmem_slot;
-    __shared__ int32_t item_s;
+    // The TMEM address and each item's index pass through the first two words of shared
+    // memory; every thread reads them before an item uses that memory.
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem);
+    volatile int32_t *item_s = reinterpret_cast<volatile int32_t *>(smem + 4);
     const unsigned long long t_start = global_ns();
     unsigned long long busy = 0, t_item = 0, n_items = 0;
     if (threadIdx.x < 32) {
-        tc::tmem_alloc(&tmem_slot, L.cols);
+        tc::tmem_alloc(tmem_slot, L.cols);
         tc::tmem_relinquish();
     }
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
-    const uint32_t tmem = tmem_slot;
+    const uint32_t tmem = *tmem_slot;
     for (;;) {
         if (threadIdx.x == 0) {
             const unsigned long long now = global_ns();
             if (n_items) busy += now - t_item;
             t_item = now;
-            item_s = atomicAdd(head, 1);
+            *item_s = atomicAdd(head, 1);
         }
         __syncthreads();
-        const int32_t it = item_s;
+        const int32_t it = *item_s;
         __syncthreads();   // every thread has read the index before thread 0 takes the next
         if (it >= nitems) break;
         ++n_items;
         const int j = items[3 * it], grp = items[3 * it + 1], kind = items[3 * it + 2];
         bool ok = true;
         if (kind == 0)
-            ok = field_item<1, 16, kHiLo, kTrack, false>(a, j, grp, smem, tmem, L, status,
+            ok = field_item<1, 16, kHiLo, kTrack, false>(a, j, grp, tmem, L, status,
                                                          dec_wait_polls);
         else if (kind == 1)
-            ok = field_item<8, 16, kHiLo, kTrack, false>(a, j, grp, smem, tmem, L, status,
+            ok = field_item<8, 16, kHiLo, kTrack, false>(a, j, grp, tmem, L, status,
                                                          dec_wait_polls);
         else if (kind == 2)
-            plain_item<8>(a, j, grp, kRaggedPlainChains, (int)threadIdx.x, smem);
+            plain_item<8>(a, j, grp, kRaggedPlainChains, (int)threadIdx.x);
         else
-            plain_item<32>(a, j, grp, kRaggedPlainChains, (int)threadIdx.x, smem);
+            plain_item<32>(a, j, grp, kRaggedPlainChains, (int)threadIdx.x);
         __syncthreads();
         if (!ok) {
             if (threadIdx.x == 0) busy += global_ns() - t_item;

@@ -174,10 +174,10 @@ def test_blocked_streamed_and_hilo(case):
 @pytest.mark.parametrize("case", ["n500", "n1000_hilo", "mixed_ragged", "n640_trace", "n1020",
                                   "n990_tail", "n1000_mixed", "n700_default_k"])
 def test_large_instances_equal_plain_and_oracle(case):
-    """Large instances on the block-field kernel (one CTA per SM): up to n = 992 items the state
-    columns fit TMEM beside the fields; beyond, the last 16-spin chunks live in shared memory as
-    the MMA's A operand (n1000_hilo, n1020, n1000_mixed).  All identical to the plain sampler
-    and the oracle."""
+    """Large instances on the block-field kernel (one CTA per SM): up to n = 992 items (960 with
+    the hi/lo split, whose accumulator takes 2K columns) the state columns fit TMEM beside the
+    fields; beyond, the last 16-spin chunks live in shared memory as the MMA's A operand
+    (n1000_hilo, n1020, n1000_mixed).  All identical to the plain sampler and the oracle."""
     if case == "n500":
         _compare([wl.qkp(500, 0.5, 31)], [[1.0]], C=128, T=60, beta=10.0, seed=13, it=1,
                  block_k=16, oracle_chains=(0, 2))
@@ -191,7 +191,7 @@ def test_large_instances_equal_plain_and_oracle(case):
     elif case == "n640_trace":
         _compare([wl.qkp(640, 0.5, 36)], [[0.8]], C=128, T=20, beta=10.0, seed=16, it=3,
                  block_k=16, trace=True, oracle_chains=(0, 1))
-    elif case == "n1020":   # halves of 512 columns: the own A operand from shared memory
+    elif case == "n1020":   # two state chunks in shared memory
         _compare([wl.qkp(1020, 0.5, 38)], [[1.2]], C=128, T=12, beta=10.0, seed=17, it=0,
                  block_k=16, oracle_chains=(0, 1))
     elif case == "n990_tail":   # n = 990: 496 state columns and 16 fields, all of TMEM
