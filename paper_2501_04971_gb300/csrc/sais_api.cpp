@@ -457,7 +457,8 @@ sais_status ensure_work(sais_problem *p, int chains, cudaStream_t st) {
     if (p->ragged_ok) {
         // Items of the persistent launch, most expensive first by an estimate of SM cycles per
         // sweep: the block-field sampler ~150 per spin plus ~7.5 per spin for each 16-spin
-        // GEMM step (twice with hi/lo); the plain sampler on 256 chains ~(120 + 6 m) per spin.
+        // GEMM step (one MMA per step, hi/lo included); the plain sampler on 256 chains
+        // ~(120 + 6 m) per spin.
         struct Item {
             double cost;
             int32_t j, q, kind;
@@ -469,7 +470,7 @@ sais_status ensure_work(sais_problem *p, int chains, cudaStream_t st) {
             const int per = h.has_w ? kRaggedFieldChains : kRaggedPlainItemChains;
             const int kind = h.has_w ? (h.m <= 1 ? 0 : 1) : (h.m <= 8 ? 2 : 3);
             const double cost =
-                h.has_w ? (double)h.nprime * (150.0 + 7.5 * (n16_of(h.n) / 16) * (p->any_lo ? 2 : 1))
+                h.has_w ? (double)h.nprime * (150.0 + 7.5 * (n16_of(h.n) / 16))
                         : (double)h.nprime * (120.0 + 6.0 * h.m);
             for (int q = 0; q < (cj + per - 1) / per; ++q) items.push_back({cost, j, q, kind});
         }

@@ -59,12 +59,14 @@ constexpr int kFThreads = 256;
 constexpr int kFNoiseWarp0 = 4;
 constexpr uint32_t kFXChunkBytes = 128 * 16 * 2;   // one 16-spin state chunk, 128 chains, BF16
 constexpr long long kFWaitCycles = 8000000000ll;   // about 4 s at 2 GHz
-// bars: 0 never completed (timeout test), 1 the block's field GEMM done (one phase per block),
-// 2..5 drain of decision warp 0..3, 6..13 noise slot written (2 q + slot), 14..21 noise slot
-// consumed, 22..24 W tile slot filled, 25..27 W tile slot free (4 arrivals: every decision warp
-// is done with the block); the ring uses the first f_ring(K) of each
+// bars: 0 never completed (timeout test), 1 and 28 the GEMM of the blocks whose fields go to
+// accumulator slot 0 and 1 done (one phase per block of that slot; 5 arrivals: the four noise
+// warps' parts and the last decision warp's), 2..5 drain of decision warp 0..3, 6..13 noise slot
+// written (2 q + slot), 14..21 noise slot consumed, 22..24 W tile slot filled, 25..27 W tile slot
+// free (4 arrivals: every decision warp is done with the block); the ring uses the first L.ring
+// of each; 29..32 drain of noise warp 0..3
 constexpr int kFBarNever = 0, kFBarMma = 1, kFBarDrain = 2, kFBarNoise = 6, kFBarNoiseFree = 14,
-              kFBarTile = 22, kFBarTileFree = 25, kFBars = 28;
+              kFBarTile = 22, kFBarTileFree = 25, kFBarMma1 = 28, kFBarNDrain = 29, kFBars = 33;
 
 __device__ __forceinline__ bool f_expired(long long n, long long polls, unsigned long long t0) {
     return polls > 0 ? n >= polls : (long long)(clock64() - t0) > kFWaitCycles;
@@ -170,18 +172,20 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp, 
     const InstDev *__restrict__ ip = a.inst + j;
     const int m = ip->m, nprime = ip->nprime, words = ip->words, n16 = ip->n16;
     const int kx = n16 / 16;                   // GEMM steps per block
-    // Accumulator columns: K, or 2K with the hi/lo split, whose two W tiles lie one after the
-    // other in shared memory and so form one B operand of N = 2K (an MMA costs the same for any
-    // N up to 128): one GEMM computes both terms.
+    // Accumulator columns of a block: K, or 2K with the hi/lo split, whose two W tiles lie one
+    // after the other in shared memory and so form one B operand of N = 2K (an MMA costs the
+    // same for any N up to 128): one GEMM computes both terms.  Two slots: block u's fields in
+    // slot u & 1, so that warps done with block u can start the GEMM of block u + 1 while the
+    // others still read block u's fields (the exact re-run reads them again).
     constexpr int KD = kHiLo ? 2 * K : K;
     // State chunks in TMEM (columns 8 kc); the rest in shared memory as SMEM A operands.
-    const int kxt = min(kx, (int)((tmem_cols - (uint32_t)KD) / 8u));
+    const int kxt = min(kx, (int)((tmem_cols - 2u * (uint32_t)KD) / 8u));
     const int nb = (nprime + K - 1) / K;       // blocks per sweep
     const uint32_t tile_bytes = (uint32_t)K * (uint32_t)n16 * 2u;   // one BF16 term, one block
     const uint32_t diag_off = tile_bytes * (kHiLo ? 2u : 1u);
     const uint32_t slot_stride =
         (uint32_t)K * (uint32_t)max_n16 * 2u * (kHiLo ? 2u : 1u) + (uint32_t)(K * K * 4);
-    const uint32_t dcol = tmem_cols - (uint32_t)KD;   // the fields D: last KD columns
+    const uint32_t dcol0 = tmem_cols - 2u * (uint32_t)KD;   // the fields D: last 2 KD columns
     const uint32_t total = (uint32_t)a.sweeps * (uint32_t)nb + (uint32_t)nb;   // + readout pass
     const uint32_t ndec = (uint32_t)a.sweeps * (uint32_t)nb;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -203,7 +207,9 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp, 
     // The barriers start afresh for every item (the previous item's waits are all over).
     if (threadIdx.x == 0) {
         for (int i = 0; i < kFBars; ++i)
-            tc::mbar_init(&bars[i], (i >= kFBarTileFree && i < kFBarTileFree + 3) ? 4u : 1u);
+            tc::mbar_init(&bars[i], (i >= kFBarTileFree && i < kFBarTileFree + 3)
+                                        ? 4u
+                                        : ((i == kFBarMma || i == kFBarMma1) ? 5u : 1u));
         arrivals[0] = arrivals[1] = arrivals[2] = 0u;
         *abort_flag = 0;
         tc::fence_mbar_init();
@@ -211,6 +217,47 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp, 
     }
     __syncthreads();
     const uint32_t iter = a.iter_dev ? *a.iter_dev : a.iter;
+
+    // The GEMM of block v, D(v) = X [W_hi | W_lo][:, blk(v)], one MMA per 16-spin state chunk,
+    // into accumulator slot v & 1, which was zeroed before: every MMA accumulates, so their order
+    // does not matter (sums of exact integers below 2^24).  An MMA holds its issuing warp about as
+    // long as it runs, whatever N <= 128, and warps issue in parallel.  So the GEMM is split: the
+    // chunks block v - 1 leaves unchanged are issued by the four noise warps (chunks kc = q mod 4)
+    // as soon as block v - 2 is done, while block v - 1 is being decided; the last decision warp
+    // to finish block v - 1 adds the chunks it changed.  (v < 2: that warp issues it all.)
+    const uint32_t idesc = tc::idesc_bf16_f32(128, (uint32_t)KD);
+    // Chunks [c0, c1) changed by block u's decisions (none for the readout pass, or past the
+    // items).
+    auto changed = [&](uint32_t u, int &c0, int &c1) {
+        c0 = c1 = 0;
+        if (u >= ndec) return;
+        const int s0u = (int)(u % (uint32_t)nb) * K;
+        if (s0u >= n16) return;
+        c0 = s0u >> 4;
+        c1 = min(kx, c0 + K / 16);
+    };
+    // MMAs over chunks k0, k0 + step, ... < k1 into the slot of block v: A from TMEM for chunks
+    // below kxt, then from shared memory (separate loops: no branch around an MMA).
+    auto mma_chunks = [&](uint32_t v, int k0, int k1, int step) {
+        const uint32_t base = tc::smem_u32(ring + f_slot(v, kFRing) * slot_stride);
+        const uint32_t d = tmem + dcol0 + (v & 1u) * (uint32_t)KD;
+        // B: 8-row groups every 16 n16 bytes (the lo tile, tile_bytes after the hi one, continues
+        // the hi tile's row groups); chunk kc starts 256 kc bytes in (16 kc in the descriptor's
+        // address field, which stays below 2^14 in shared memory).
+        const uint64_t bd0 = tc::smem_desc(base, 128u, (uint32_t)n16 * 16u);
+        const uint64_t ad0 = tc::smem_desc(tc::smem_u32(xsm), 128u, 256u);
+        int kc = k0;
+        for (; kc < min(k1, kxt); kc += step)
+            tc::mma_bf16_tmem_a(d, tmem + 8u * (uint32_t)kc, bd0 + 16u * (uint32_t)kc, idesc, 1u);
+        for (; kc < k1; kc += step)
+            tc::mma_bf16(d, ad0 + (uint32_t)(kc - kxt) * (kFXChunkBytes >> 4),
+                         bd0 + 16u * (uint32_t)kc, idesc, 1u);
+    };
+    auto mma_bar = [&](uint32_t v) { return &bars[(v & 1u) ? kFBarMma1 : kFBarMma]; };
+    auto tile_ready = [&](uint32_t v) -> bool {
+        return f_wait(&bars[kFBarTile + f_slot(v, kFRing)], f_round(v, kFRing) & 1u, abort_flag,
+                      status, 0);
+    };
 
     if (warp >= kFNoiseWarp0) {
         if (kSplit) asm volatile("setmaxnreg.dec.sync.aligned.u32 64;");
@@ -246,6 +293,26 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp, 
             ++tiles_issued;
             return true;
         };
+        // This warp's part of block v's GEMM (v >= 2): its chunks (q mod 4) that block v - 1
+        // leaves unchanged, once block v - 2 is done (its X chunks written and slot v & 1 zeroed:
+        // the tile-free barrier of block v - 2) and block v's tile is in; then its commit.  (v < 2:
+        // the commit alone, which arrives at once.)  Lane 0.
+        auto issue_ahead = [&](uint32_t v) -> bool {
+            if (v >= 2u) {
+                const uint32_t u = v - 2u;
+                if (!f_wait(&bars[kFBarTileFree + f_slot(u, kFRing)], f_round(u, kFRing) & 1u,
+                            abort_flag, status, 0) ||
+                    !tile_ready(v))
+                    return false;
+                tc::tc_fence_after();
+                int c0, c1;
+                changed(v - 1u, c0, c1);
+                mma_chunks(v, q, c0, 4);
+                mma_chunks(v, c1 + (((q - c1) % 4) + 4) % 4, kx, 4);
+            }
+            tc::mma_commit(mma_bar(v));
+            return true;
+        };
         bool ok = true;
         // Tile 0 goes out before any noise (block 0's GEMM needs it at once); tile u + 1 after
         // the noise of block u, a block ahead of its GEMM.  Its slot was freed by block
@@ -273,13 +340,27 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp, 
             }
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&bars[kFBarNoise + 2 * q + slot]);
-            if (stager && it + 1u < total) ok = stage(it + 1u);
+            // Block it's part first: with two tile slots, staging tile it + 1 waits for the end of
+            // block it - 1, and the part should run during that block.
+            if (lane == 0) ok = issue_ahead(it);
+            if (stager && ok && it + 1u < total) ok = stage(it + 1u);
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
         }
-        // Tiles of the readout pass (and of the last decision blocks when the sweeps are few).
-        if (stager && ok && !*abort_flag)
-            for (uint32_t u = tiles_issued; u < total; ++u)
-                if (!stage(u)) break;
+        // The readout pass (no noise): its tiles, and this warp's parts of its GEMMs.
+        for (uint32_t v = ndec; ok && v < total; ++v) {
+            if (stager)   // tile v (when the sweeps are few it may not be out yet)
+                while (ok && tiles_issued <= v) ok = stage(tiles_issued);
+            if (lane == 0 && ok) ok = issue_ahead(v);
+            if (stager)
+                while (ok && tiles_issued < total && tiles_issued <= v + 1u) ok = stage(tiles_issued);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        }
+        // Every MMA this warp issued completes before the outputs and the TMEM release (bounded,
+        // not cut short by an abort).
+        if (lane == 0) {
+            tc::mma_commit(&bars[kFBarNDrain + q]);
+            f_wait(&bars[kFBarNDrain + q], 0, nullptr, status, 0);
+        }
         // The copies complete before shared memory is released.
         if (stager)
             for (uint32_t ts = 0; ts < kFRing && ts < tiles_issued; ++ts) {
@@ -303,53 +384,38 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp, 
         const float *__restrict__ asum = ip->asum;
         const float4 *__restrict__ spinc = ip->spinc;
         const float *lam = a.lambda + (size_t)j * a.m_stride;
-        const uint32_t idesc = tc::idesc_bf16_f32(128, (uint32_t)KD);
 
-        // The GEMM of block u: D = X [W_hi | W_lo][:, blk], kx steps, then one commit.  Issued by
-        // one thread once the tile is in shared memory (bounded wait).
-        auto issue_gemm = [&](uint32_t u) -> bool {
-            const uint32_t ts = f_slot(u, kFRing);
-            if (!f_wait(&bars[kFBarTile + ts], f_round(u, kFRing) & 1u, abort_flag, status, 0))
-                return false;
-            const uint32_t base = tc::smem_u32(ring + ts * slot_stride);
-            // 8-row groups of the B operand every 16 n16 bytes: the lo tile (tile_bytes after
-            // the hi one) continues the hi tile's row groups.
-            const uint32_t sbo = (uint32_t)n16 * 16u;
-            // descriptor of step kc: the start address advances by 256 bytes (16 in the
-            // descriptor's address field, which stays below 2^14 in shared memory)
-            uint64_t bd = tc::smem_desc(base, 128u, sbo);
-            // A from TMEM for the first kxt chunks, then from shared memory (two loops: no
-            // branch per MMA)
-            for (int kc = 0; kc < kxt; ++kc) {
-                tc::mma_bf16_tmem_a(tmem + dcol, tmem + 8u * (uint32_t)kc, bd, idesc,
-                                    kc != 0 ? 1u : 0u);
-                bd += 16u;
-            }
-            uint64_t ad = tc::smem_desc(tc::smem_u32(xsm), 128u, 256u);
-            for (int kc = kxt; kc < kx; ++kc) {
-                tc::mma_bf16(tmem + dcol, ad, bd, idesc, kc != 0 ? 1u : 0u);
-                ad += kFXChunkBytes >> 4;
-                bd += 16u;
-            }
-            tc::mma_commit(&bars[kFBarMma]);
-            return true;
-        };
-        // Arrival of this warp at the end of a block (its TMEM stores waited for and fenced); the
-        // last of the four issues the GEMM of block `next` (if any).
-        auto arrive_and_issue = [&](uint32_t *counter, uint32_t next) -> bool {
+        // End of block v - 1 (v = 0: the start) for this warp: its arrival; the last warp issues
+        // the chunks block v - 1 changed (v < 2: every chunk) and commits.
+        auto arrive_and_issue = [&](uint32_t *counter, uint32_t v, int c0, int c1) -> bool {
             bool ok2 = true;
             tc::tc_fence_before();
             __syncwarp();
             if (lane == 0) {
                 __threadfence_block();
                 const bool last = (atomicAdd(counter, 1u) & 3u) == 3u;
-                if (last && next < total) {
+                if (last && v < total) {
                     __threadfence_block();
                     tc::tc_fence_after();
-                    ok2 = issue_gemm(next);
+                    if (v < 2u) {   // no part was issued ahead: the whole GEMM
+                        c0 = 0;
+                        c1 = kx;
+                    }
+                    if (c1 > c0) {
+                        ok2 = tile_ready(v);
+                        if (ok2) mma_chunks(v, c0, c1, 1);
+                    }
+                    if (ok2) tc::mma_commit(mma_bar(v));
                 }
             }
             return __shfl_sync(0xffffffffu, ok2 ? 1 : 0, 0) != 0;
+        };
+        // This warp's rows of an accumulator slot set to 0 (warp-collective).
+        auto zero_slot = [&](uint32_t slot) {
+            const uint32_t zero8[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int c8 = 0; c8 < KD; c8 += 8)
+                tc::tmem_st8(lane_addr + dcol0 + slot * (uint32_t)KD + (uint32_t)c8, zero8);
         };
 
         // Every run starts from x = 0 (Sec. III-B): X and the bit-packed states cleared.
@@ -364,8 +430,10 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp, 
                 *reinterpret_cast<uint4 *>(row + 128) = make_uint4(0u, 0u, 0u, 0u);
             }
             if (kx > kxt) tc::fence_proxy_async_smem();
+            zero_slot(0u);
+            zero_slot(1u);
         }
-        bool ok = arrive_and_issue(&arrivals[2], 0u);
+        bool ok = arrive_and_issue(&arrivals[2], 0u, 0, kx);
 
         int32_t g[MC];
         float c[MC], cA[MC];
@@ -432,11 +500,12 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp, 
                 }
             }
             // This block's fields: its GEMM is done (issued by the last warp of the block before).
-            if (!f_wait_warp(&bars[kFBarMma], it & 1u, abort_flag, status, dec_wait_polls)) {
+            if (!f_wait_warp(mma_bar(it), (it >> 1) & 1u, abort_flag, status, dec_wait_polls)) {
                 ok = false;
                 break;
             }
             tc::tc_fence_after();
+            const uint32_t dcol = dcol0 + (it & 1u) * (uint32_t)KD;   // this block's slot
             f_load_fields<K, kHiLo>(lane_addr + dcol, Fr);
 #pragma unroll
             for (int ii = 0; ii < K; ++ii) Fr[ii] += __ldg(hF + s0 + ii);   // exact integers
@@ -454,9 +523,11 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp, 
                 }
                 sumF += pf;
                 sumh += ph;
+                zero_slot(it & 1u);   // for the GEMM of block it + 2
+                tc::tc_fence_before();   // the noise warps' MMAs of block it + 2 follow
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&bars[kFBarTileFree + ts]);
-                ok = arrive_and_issue(&arrivals[it & 1u], it + 1u);
+                ok = arrive_and_issue(&arrivals[it & 1u], it + 1u, 0, 0);
                 continue;
             }
             const float beta = beta_of_sweep(a.beta_max, (int)t, a.sweeps);
@@ -667,12 +738,18 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp, 
                     }
                 }
             }
+            zero_slot(it & 1u);   // for the GEMM of block it + 2
+            tc::tc_fence_before();   // the noise warps' MMAs of block it + 2 follow
             __syncwarp();
             if (lane == 0) {
                 if (K != 16) tc::mbar_arrive(&bars[kFBarNoiseFree + 2 * warp + slot]);
                 tc::mbar_arrive(&bars[kFBarTileFree + ts]);
             }
-            ok = arrive_and_issue(&arrivals[it & 1u], it + 1u);
+            {
+                int c0, c1;
+                changed(it, c0, c1);
+                ok = arrive_and_issue(&arrivals[it & 1u], it + 1u, c0, c1);
+            }
             // Sweep end: best feasible sweep-end state of the run, and the trace.
             if (ok && b == nb - 1) {
                 if (kTrack) {

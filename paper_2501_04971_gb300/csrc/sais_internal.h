@@ -152,9 +152,9 @@ size_t blocked_smem_bytes(int max_npad, int max_words, int block_k, bool stream_
 // Block-field sampler: each block's fields from one tcgen05 GEMM over the chain states held in
 // TMEM and, past 512 columns, in shared memory (W present, m <= 8, n <= 1024).
 size_t field_smem_bytes(int max_n16, int max_words, int block_k, bool hilo);
-// Accumulator columns of the block-field GEMM: K, or 2K with the hi/lo split (both terms in one
-// MMA of N = 2K).
-inline int field_dcols(int block_k, bool hilo) { return hilo ? 2 * block_k : block_k; }
+// Accumulator columns of the block-field GEMM: two slots (the GEMM of the next block runs while
+// a block is decided) of K columns, or 2K with the hi/lo split (both terms in one MMA of N = 2K).
+inline int field_dcols(int block_k, bool hilo) { return 2 * (hilo ? 2 * block_k : block_k); }
 uint32_t field_tmem_cols(int max_n16, int dcols);
 cudaError_t launch_field_sampler(const SampleArgs &a, int max_m, int max_n16, int max_words,
                                  int block_k, bool hilo, int32_t *status,

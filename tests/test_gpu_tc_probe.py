@@ -34,7 +34,7 @@ def test_mma_issue_cost_probe(tmp_path):
              re.findall(r"chain A=(\w+) N=(\d+) R=(\d+) cycles=(\d+)", r.stdout)}
     split = {(int(n), int(p)): int(c) for n, p, c in
              re.findall(r"split N=(\d+) R=19 P=(\d+) cycles=(\d+)", r.stdout)}
-    assert len(chain) == 40 and len(split) == 9
+    assert len(chain) == 60 and len(split) == 9
     # 19 narrow MMAs cost far more than one, whatever N: the instruction count dominates
     for n in (16, 32, 64, 128):
         assert chain[("tmem", n, 19)] > 3 * chain[("tmem", n, 1)]
