@@ -24,7 +24,10 @@ int field_xs_chunks(int max_n16, int dcols) {
 }
 
 size_t field_smem_ring(int max_n16, int max_words, int block_k, bool hilo, int ring) {
-    const size_t slot = (size_t)block_k * max_n16 * 2 * (hilo ? 2 : 1) + (size_t)block_k * block_k * 4;
+    // a tile slot: the W tile(s), the FP32 diagonal block, and for K >= 32 the per-spin records
+    // and h
+    const size_t slot = (size_t)block_k * max_n16 * 2 * (hilo ? 2 : 1) +
+                        (size_t)block_k * block_k * 4 + (block_k >= 32 ? (size_t)block_k * 20 : 0);
     const size_t xwords = (size_t)((max_words + 1) & ~1);   // as the kernel rounds them
     return ring * slot + (size_t)field_xs_chunks(max_n16, field_dcols(block_k, hilo)) * kFXChunkBytes +
            xwords * kFLanes * 4 + (size_t)2 * block_k * kFLanes * 4 + kFBars * 8 + 32;

@@ -183,8 +183,14 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp, 
     const int nb = (nprime + K - 1) / K;       // blocks per sweep
     const uint32_t tile_bytes = (uint32_t)K * (uint32_t)n16 * 2u;   // one BF16 term, one block
     const uint32_t diag_off = tile_bytes * (kHiLo ? 2u : 1u);
-    const uint32_t slot_stride =
-        (uint32_t)K * (uint32_t)max_n16 * 2u * (kHiLo ? 2u : 1u) + (uint32_t)(K * K * 4);
+    // K >= 32: after the diagonal, the block's per-spin records {a_0i, D_i, sum_k a_ki, a_1i} and
+    // h (K x 16 and K x 4 bytes), staged with the tile so that no global load waits on the
+    // block's path.  (K = 16 loads them from global memory while it waits for the GEMM: measured
+    // faster there, where the staging warp's extra copies cost more than they save.)
+    constexpr bool kSide = K >= 32;
+    const uint32_t side_off = diag_off + (uint32_t)(K * K * 4);
+    const uint32_t slot_stride = (uint32_t)K * (uint32_t)max_n16 * 2u * (kHiLo ? 2u : 1u) +
+                                 (uint32_t)(K * K * 4) + (kSide ? (uint32_t)(K * 20) : 0u);
     const uint32_t dcol0 = tmem_cols - 2u * (uint32_t)KD;   // the fields D: last 2 KD columns
     const uint32_t total = (uint32_t)a.sweeps * (uint32_t)nb + (uint32_t)nb;   // + readout pass
     const uint32_t ndec = (uint32_t)a.sweeps * (uint32_t)nb;
@@ -284,12 +290,19 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp, 
             const uint32_t b = u < ndec ? u % (uint32_t)nb : u - ndec;
             unsigned char *dst = ring + ts * slot_stride;
             const uint32_t dbytes = (uint32_t)(K * K * 4);
-            tc::mbar_expect_tx(&bars[kFBarTile + ts], diag_off + dbytes);
+            tc::mbar_expect_tx(&bars[kFBarTile + ts],
+                               diag_off + dbytes + (kSide ? (uint32_t)(K * 20) : 0u));
             tc::bulk_g2s(dst, Wg + (size_t)b * tile_bytes, tile_bytes, &bars[kFBarTile + ts]);
             if (kHiLo)
                 tc::bulk_g2s(dst + tile_bytes, Wgl + (size_t)b * tile_bytes, tile_bytes,
                              &bars[kFBarTile + ts]);
             tc::bulk_g2s(dst + diag_off, Wd + (size_t)b * dbytes, dbytes, &bars[kFBarTile + ts]);
+            if (kSide) {   // (N'_pad is a multiple of 64: the block's records are in the arrays)
+                tc::bulk_g2s(dst + side_off, ip->spinc + (size_t)b * K, (uint32_t)(K * 16),
+                             &bars[kFBarTile + ts]);
+                tc::bulk_g2s(dst + side_off + (uint32_t)(K * 16), ip->hF + (size_t)b * K,
+                             (uint32_t)(K * 4), &bars[kFBarTile + ts]);
+            }
             ++tiles_issued;
             return true;
         };
@@ -411,11 +424,11 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp, 
             return __shfl_sync(0xffffffffu, ok2 ? 1 : 0, 0) != 0;
         };
         // This warp's rows of an accumulator slot set to 0 (warp-collective).
+        // Stores issued; the caller waits (tmem_wait_st) before its tile-free arrival.
         auto zero_slot = [&](uint32_t slot) {
-            const uint32_t zero8[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
 #pragma unroll
-            for (int c8 = 0; c8 < KD; c8 += 8)
-                tc::tmem_st8(lane_addr + dcol0 + slot * (uint32_t)KD + (uint32_t)c8, zero8);
+            for (int c16 = 0; c16 < KD; c16 += 16)
+                tc::tmem_zero16_nowait(lane_addr + dcol0 + slot * (uint32_t)KD + (uint32_t)c16);
         };
 
         // Every run starts from x = 0 (Sec. III-B): X and the bit-packed states cleared.
@@ -432,6 +445,7 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp, 
             if (kx > kxt) tc::fence_proxy_async_smem();
             zero_slot(0u);
             zero_slot(1u);
+            tc::tmem_wait_st();
         }
         bool ok = arrive_and_issue(&arrivals[2], 0u, 0, kx);
 
@@ -473,6 +487,13 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp, 
             const uint32_t ts = f_slot(it, kFRing);
             const uint32_t slot = it & 1u;
             const float *thb = thbuf + slot * K * kFLanes + r;
+            // the block's records and h: staged in shared memory (K >= 32) or global
+            const float4 *scs =
+                kSide ? reinterpret_cast<const float4 *>(ring + ts * slot_stride + side_off)
+                      : spinc + s0;
+            const float *hs = kSide ? reinterpret_cast<const float *>(ring + ts * slot_stride +
+                                                                      side_off + (uint32_t)(K * 16))
+                                    : hF + s0;
             // K = 16: the block's per-spin data, loaded before the wait for the block's GEMM,
             // which they overlap: the noise theta and the record {a_0i, D_i, sum_k a_ki, a_1i}.
             // Larger blocks load them spin by spin (registers).
@@ -493,11 +514,15 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp, 
 #pragma unroll
                     for (int ii = 0; ii < kPre; ++ii) {
                         th16[ii] = thb[ii * kFLanes];
-                        sc16[ii] = __ldg(spinc + s0 + ii);
+                        sc16[ii] = scs[ii];
                     }
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(&bars[kFBarNoiseFree + 2 * warp + slot]);
                 }
+            } else if (!f_wait_warp(&bars[kFBarTile + ts], f_round(it, kFRing) & 1u, abort_flag,
+                                    status, dec_wait_polls)) {   // h of the block
+                ok = false;
+                break;
             }
             // This block's fields: its GEMM is done (issued by the last warp of the block before).
             if (!f_wait_warp(mma_bar(it), (it >> 1) & 1u, abort_flag, status, dec_wait_polls)) {
@@ -508,7 +533,7 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp, 
             const uint32_t dcol = dcol0 + (it & 1u) * (uint32_t)KD;   // this block's slot
             f_load_fields<K, kHiLo>(lane_addr + dcol, Fr);
 #pragma unroll
-            for (int ii = 0; ii < K; ++ii) Fr[ii] += __ldg(hF + s0 + ii);   // exact integers
+            for (int ii = 0; ii < K; ++ii) Fr[ii] += hs[ii];   // exact integers
             const int wi = s0 >> 5, sb = s0 & 31;
             if (readout) {
                 // Readout pass: sum_i x_i F_i and h^T x over the block, from the final states.
@@ -518,12 +543,13 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp, 
                     const uint32_t xw = xs[((s0 + ii) >> 5) * kFLanes + r];
                     if ((xw >> ((s0 + ii) & 31)) & 1u) {
                         pf += __float2int_rz(Fr[ii]);
-                        ph += __float2int_rz(__ldg(hF + s0 + ii));
+                        ph += __float2int_rz(hs[ii]);
                     }
                 }
                 sumF += pf;
                 sumh += ph;
                 zero_slot(it & 1u);   // for the GEMM of block it + 2
+                tc::tmem_wait_st();
                 tc::tc_fence_before();   // the noise warps' MMAs of block it + 2 follow
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&bars[kFBarTileFree + ts]);
@@ -556,7 +582,7 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp, 
                 // word and bit of spin s in the block's state words (K = 16: one word, bit sb + ii;
                 // K >= 32: blocks start on a word, so the word index is a constant)
                 const int bw = K == 16 ? 0 : (ii >> 5), bi = K == 16 ? sb + ii : (ii & 31);
-                const float4 sc = K == 16 ? sc16[ii % kPre] : __ldg(spinc + s);
+                const float4 sc = K == 16 ? sc16[ii % kPre] : scs[ii];
                 // Row ii of the block's diagonal of W (FP32, the same address for every lane):
                 // the quads right of spin ii, for the in-block corrections.
                 float4 wq[K / 4];
@@ -651,7 +677,7 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp, 
                                      : "=r"(fl_lo)
                                      : "r"(lane_addr + dcol + (uint32_t)(K + ii)));
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    float Fi = __uint_as_float(fv) + __ldg(hF + s);
+                    float Fi = __uint_as_float(fv) + hs[ii];
                     if (kHiLo) Fi += __uint_as_float(fl_lo);
                     uint64_t fl = (bn ^ bo) & ((1ull << ii) - 1ull);
                     while (fl) {
@@ -726,7 +752,7 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp, 
                         }
                         const int c = (s0 >> 4) + h8;   // the 16-spin chunk
                         if (c < kxt) {
-                            tc::tmem_st8(lane_addr + (uint32_t)(8 * c), v8);
+                            tc::tmem_st8_nowait(lane_addr + (uint32_t)(8 * c), v8);
                         } else {
                             unsigned char *row = xsm + (size_t)(c - kxt) * kFXChunkBytes +
                                                  (r >> 3) * 256 + (r & 7) * 16;
@@ -739,6 +765,7 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp, 
                 }
             }
             zero_slot(it & 1u);   // for the GEMM of block it + 2
+            tc::tmem_wait_st();      // the state chunk and the zeros
             tc::tc_fence_before();   // the noise warps' MMAs of block it + 2 follow
             __syncwarp();
             if (lane == 0) {

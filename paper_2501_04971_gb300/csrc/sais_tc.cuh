@@ -141,6 +141,25 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8])
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
+// The same store without the wait (the caller waits once for several stores).
+__device__ __forceinline__ void tmem_st8_nowait(uint32_t taddr, const uint32_t (&v)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]),
+                 "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+// 32 lanes x 16 columns of zeros, no wait.
+__device__ __forceinline__ void tmem_zero16_nowait(uint32_t taddr) {
+    const uint32_t z = 0u;
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+        "%1,%1};" ::"r"(taddr), "r"(z)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 // ---- tcgen05.mma, kind::f16 (BF16 x BF16 -> FP32 in TMEM), one CTA -----------------------
 // Shared-memory matrix descriptor, no swizzle (core matrices of 8 rows x 16 bytes):
 //   bits 0-13 start address >> 4, 16-29 leading-dimension byte offset >> 4 (between core
