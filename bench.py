@@ -902,9 +902,9 @@ def main():
         npad = ((nspins + 63) // 64) * 64
         flops = float((2 * npad * nspins).sum()) * a.chains * a.sweeps
         # DRAM bytes (read + write) per instance of one launch of this kernel, measured with ncu
-        # on a 640-instance, 10-sweep launch (W is read once per CTA, so traffic scales with
-        # instances, not sweeps)
-        traffic = 218102.0 * prob.count if (a.chains == 128 and a.block_k in (0, 16)) else None
+        # on a 152-instance, 200-sweep launch (bench.py --kernel-case rankk_qkp300): W is read
+        # once per CTA, so the traffic scales with instances, not sweeps
+        traffic = 212512.0 * prob.count if (a.chains == 128 and a.block_k in (0, 16)) else None
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
             if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
         peak = peaks.get("bf16_tflops", 1900.0) * 1e12
@@ -1007,6 +1007,18 @@ def main():
     cpu = None
     if world == 1 and not a.no_cpu:
         cpu = cpu_baseline_line(insts, a.cpu_seconds)
+    clocks = clk.summary()
+    if variant == "blocked":
+        # The sampler is bound by the latency of each chain's sequential decisions, not by a
+        # pipe: SM cycles per spin-step of a 128-chain CTA (live, at the sampled clock), and the
+        # issue and tensor-pipe activity of the same kernel from its ncu capture.
+        mhz = clocks.get("sm_mhz") or SM_MAX_MHZ
+        steps = float(((nspins + 15) // 16 * 16).sum()) * (-(-a.chains // 128)) * a.sweeps
+        roof["latency"] = {
+            "cycles_per_spin_step": kmean * mhz * 1e6 * SM_COUNT / steps,
+            "smsp_issue_active": 0.473, "tensor_pipe_active": 0.056,
+            "source": "ncu of bench.py --kernel-case rankk_qkp300 (profiles/"
+                      "blocked_sampler_qkp300.md): issue slots busy 47 %, tensor pipe 5.6 %"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -1018,7 +1030,7 @@ def main():
                        "l2": "inputs larger than L2 (W int16 + bf16 of 1024 instances, "
                              f"{prob.count * 2 * 2 * 320 * 320 / 1e6:.0f} MB)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": 3 * a.steps, "clocks": clk.summary(),
+            "gpu_launches": 3 * a.steps, "clocks": clocks,
             "updates_per_step": upd_step, "plain": plain_cmp, "blocked_k": ksweep,
             "gap_1pct": gap,
             "ragged": ragged}

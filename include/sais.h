@@ -62,7 +62,11 @@ typedef enum sais_status {
                               |h_i| + sum_j |W_ij| >= 2^24, |W_ij| > 32767, or
                               b_k + sum_i a_ki(ext) >= 2^24                                 */
     SAIS_ETIMEOUT = 5,     /* a bounded device wait gave up (status word set by a kernel)    */
-    SAIS_EUNSUPPORTED = 6  /* device is not sm_103, or sizes exceed what a kernel supports   */
+    SAIS_EUNSUPPORTED = 6, /* device is not sm_103, or sizes exceed what a kernel supports   */
+    SAIS_EBOUNDS = 7       /* debug builds only (compiled with SAIS_DEBUG=1): a device-side
+                              check of an index or size failed; the kernel skipped the access
+                              and its outputs are not valid (sais_last_error names the check's
+                              source line)                                                  */
 } sais_status;
 
 /* One knapsack instance in integer form (Sec. IV, Eq. 12 and 14):
@@ -420,6 +424,13 @@ SAIS_API sais_status sais_persistent_stats(sais_problem *p, uint64_t *out, int32
  * kernel then stopped early and its outputs are not valid).  Resets the device status word.
  * Errors: SAIS_EINVAL, SAIS_ECUDA, SAIS_ETIMEOUT. */
 SAIS_API sais_status sais_synchronize(sais_problem *p, void *stream);
+
+/* Debug builds (SAIS_DEBUG=1): queues on `stream` one kernel whose device-side check fails by
+ * construction, so that the next sais_synchronize reports SAIS_EBOUNDS with that check's line
+ * (a test of the reporting path; the kernel touches no memory but the status words).  Release
+ * builds return SAIS_EUNSUPPORTED and queue nothing.  No counterpart in the paper.
+ * Errors: SAIS_EINVAL, SAIS_ECUDA, SAIS_EUNSUPPORTED. */
+SAIS_API sais_status sais_debug_check_selftest(sais_problem *p, void *stream);
 
 /* ---- Learned multiplier warm start (the paper has no counterpart) -------------------------
  * A 7 -> 128 -> 128 -> 1 ReLU network (BF16 weights, FP32 accumulation, tensor cores) maps the

@@ -19,6 +19,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsais.so")
+# The debug build: device-side index and size checks (SAIS_DEBUG=1) that report SAIS_EBOUNDS.
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(BUILD_DEBUG, "libsais.so")
 
 SOURCES = ["sais_api.cpp", "sais_plain.cu", "sais_post.cu", "sais_blocked.cu",
            "sais_blocked_stream.cu", "sais_field.cu", "sais_field_k.cu", "sais_noalloc.cu",
@@ -42,22 +45,27 @@ def _inputs() -> List[str]:
     return files
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB):
+def stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(f) > t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags: List[str] = ()) -> str:
-    """Compile every source for sm_103a and link libsais.so; returns its path."""
-    if not force and not stale() and not extra_flags:
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags: List[str] = (),
+          debug: bool = False) -> str:
+    """Compile every source for sm_103a and link libsais.so; returns its path.  debug=True
+    builds the library with the device-side checks (SAIS_DEBUG=1) into its own directory."""
+    build_dir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    if not force and not stale(lib) and not extra_flags:
+        return lib
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
+    if debug:
+        extra_flags = [*extra_flags, "-DSAIS_DEBUG=1"]
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+        obj = os.path.join(build_dir, os.path.splitext(src)[0] + ".o")
         cmd = [cc, *ARCH, *FLAGS, *extra_flags, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -68,14 +76,15 @@ def build(force: bool = False, verbose: bool = False, extra_flags: List[str] = (
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [cc, *ARCH, "-shared", "--cudart", "shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link of libsais.so failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force=True, verbose=True))
+    import sys
+    print(build(force=True, verbose=True, debug="--debug" in sys.argv))

@@ -393,7 +393,10 @@ void build_groups(sais_problem *p) {
         g.field = key == 10 || key == 11;
         g.stream_w = key >= 2 && key <= 11;
         g.hilo = key == 3 || key == 11;
-        if (g.field) g.block_k = field_default_k(g.max_m);
+        if (g.field) {   // the default block size where the group's largest member fits it
+            g.block_k = field_default_k(g.max_m);
+            if (!field_fits(g.max_n16, g.words, g.max_m, true, g.block_k, g.hilo)) g.block_k = 16;
+        }
         auto cost = [&](int j) {
             const HostInst &h = p->host[j];
             return (double)h.nprime * (h.has_w ? (double)h.npad : (double)std::max(1, h.m));
@@ -555,6 +558,7 @@ const char *sais_status_string(sais_status s) {
         case SAIS_EOVERFLOW: return "integer bound for exact fields exceeded";
         case SAIS_ETIMEOUT: return "bounded device wait timed out";
         case SAIS_EUNSUPPORTED: return "unsupported device or size";
+        case SAIS_EBOUNDS: return "device-side bounds check failed (debug build)";
     }
     return "unknown status";
 }
@@ -1186,17 +1190,31 @@ sais_status sais_persistent_stats(sais_problem *p, uint64_t *out, int32_t cap, i
     return SAIS_OK;
 }
 
+sais_status sais_debug_check_selftest(sais_problem *p, void *stream) {
+    if (!p) return fail(SAIS_EINVAL, "NULL problem");
+    if (!debug_checks_built())
+        return fail(SAIS_EUNSUPPORTED, "device-side checks are compiled in debug builds only "
+                                       "(SAIS_DEBUG=1)");
+    DeviceGuard dg(p->device);
+    const cudaError_t e = launch_dcheck_selftest(p->d_status, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(SAIS_ECUDA, "check self-test: %s", cudaGetErrorString(e));
+    return SAIS_OK;
+}
+
 sais_status sais_synchronize(sais_problem *p, void *stream) {
     if (!p) return fail(SAIS_EINVAL, "NULL problem");
     DeviceGuard dg(p->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     SAIS_CUDA(cudaStreamSynchronize(st));
-    int32_t v = 0;
-    SAIS_CUDA(cudaMemcpy(&v, p->d_status, 4, cudaMemcpyDeviceToHost));
-    if (v != SAIS_OK) {
-        SAIS_CUDA(cudaMemset(p->d_status, 0, 4));
-        return fail((sais_status)v, "a kernel on this problem reported: %s",
-                    sais_status_string((sais_status)v));
+    int32_t v[2] = {0, 0};   // the status, and the source line of a failed debug check
+    SAIS_CUDA(cudaMemcpy(v, p->d_status, 8, cudaMemcpyDeviceToHost));
+    if (v[0] != SAIS_OK) {
+        SAIS_CUDA(cudaMemset(p->d_status, 0, 8));
+        if (v[0] == SAIS_EBOUNDS)
+            return fail(SAIS_EBOUNDS, "a kernel on this problem reported: %s (check at line %d)",
+                        sais_status_string(SAIS_EBOUNDS), v[1]);
+        return fail((sais_status)v[0], "a kernel on this problem reported: %s",
+                    sais_status_string((sais_status)v[0]));
     }
     return SAIS_OK;
 }

@@ -116,6 +116,8 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
     constexpr uint32_t kRing = 3;
     const int j = a.work ? a.work[2 * blockIdx.x] : (int)blockIdx.y;
     const int grp = a.work ? a.work[2 * blockIdx.x + 1] : (int)blockIdx.x;
+    if (!SAIS_DCHECK(status, j >= 0 && j < a.count && grp >= 0 && grp * kLanes < a.chains))
+        return;
     const InstDev *__restrict__ ip = a.inst + j;
     const int m = ip->m, nprime = ip->nprime, npad = ip->npad, words = ip->words;
     const int nb = (nprime + K - 1) / K;
@@ -138,6 +140,13 @@ __global__ void __launch_bounds__(kThreadsBlocked, 1)
     uint32_t *tmem_slot = arrivals + 2;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
+    // Debug builds: F and the Delta slots within the CTA's TMEM, the layout within its shared
+    // memory (every thread evaluates the same values).
+    if (!SAIS_DCHECK(status, (uint32_t)(npad + K) <= tmem_cols &&
+                                 (uint32_t)(reinterpret_cast<unsigned char *>(
+                                                const_cast<int *>(abort_flag) + 1) -
+                                            smem) <= dynamic_smem_bytes()))
+        return;
     if (threadIdx.x == kIssueThread) {
         for (int i = 0; i < 30; ++i) tc::mbar_init(&bars[i], 1);
         arrivals[0] = arrivals[1] = 0u;

@@ -20,6 +20,27 @@
 
 namespace sais {
 
+// Debug builds (compiled with SAIS_DEBUG=1): device-side checks of indices and sizes that the
+// host's validation makes true by construction.  A failed check records SAIS_EBOUNDS and its
+// source line in the problem's status words (status[0], status[1]; the first failure wins) and
+// the caller skips the access; release builds compile the checks to `true`.
+#if defined(SAIS_DEBUG) && SAIS_DEBUG
+static __device__ __noinline__ void dcheck_fail(int32_t *status, int line) {
+    if (status && atomicCAS(status, 0, (int32_t)SAIS_EBOUNDS) == 0)
+        atomicExch(status + 1, (int32_t)line);
+}
+#define SAIS_DCHECK(status, cond) ((cond) ? true : (::sais::dcheck_fail((status), __LINE__), false))
+#else
+#define SAIS_DCHECK(status, cond) true
+#endif
+
+// Bytes of dynamic shared memory this launch has.
+__device__ __forceinline__ uint32_t dynamic_smem_bytes() {
+    uint32_t v;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+    return v;
+}
+
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32 -> 64-bit
 // products of counter words 0 and 2 with the round multipliers; the high halves are xor-ed
 // with the other counter word and the round key, which advances by the Weyl constants.

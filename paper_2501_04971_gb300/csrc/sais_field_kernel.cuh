@@ -165,6 +165,8 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp, 
                                            const FieldLaunch &L, int32_t *status,
                                            long long dec_wait_polls) {
     extern __shared__ __align__(1024) unsigned char smem[];
+    if (!SAIS_DCHECK(status, j >= 0 && j < a.count && grp >= 0 && grp * kFLanes < a.chains))
+        return false;
     constexpr int kXW = K >= 32 ? K / 32 : 1;   // state words a block spans
     const uint32_t kFRing = (uint32_t)L.ring;
     const uint32_t tmem_cols = L.cols;
@@ -210,6 +212,15 @@ __device__ __forceinline__ bool field_item(const SampleArgs &a, int j, int grp, 
     uint32_t *arrivals = reinterpret_cast<uint32_t *>(bars + kFBars);   // [3]
     volatile int *abort_flag = reinterpret_cast<volatile int *>(arrivals + 4);
 
+    // Debug builds: the launch's shape against this item (the host's sizing makes these hold;
+    // every thread evaluates the same values).
+    if (!SAIS_DCHECK(status, n16 % 16 == 0 && n16 <= max_n16 && nb * K <= ip->npad &&
+                                 8u * (uint32_t)kxt + 2u * (uint32_t)KD <= tmem_cols &&
+                                 kx - kxt <= L.xs_chunks && (kFRing == 2u || kFRing == 3u) &&
+                                 (uint32_t)(reinterpret_cast<unsigned char *>(
+                                                const_cast<int *>(abort_flag) + 1) -
+                                            smem) <= dynamic_smem_bytes()))
+        return false;
     // The barriers start afresh for every item (the previous item's waits are all over).
     if (threadIdx.x == 0) {
         for (int i = 0; i < kFBars; ++i)

@@ -178,6 +178,8 @@ size_t plain_smem_bytes(int max_npad, int max_words, bool any_w, int cpb);
 constexpr size_t kMaxSmemPerBlock = 232448;   // 227 KB opt-in per CTA on sm_103
 cudaError_t launch_post(const PostArgs &a, cudaStream_t stream);
 cudaError_t launch_advance_iter(uint32_t *iter_dev, cudaStream_t stream);
+bool debug_checks_built();   // compiled with SAIS_DEBUG=1
+cudaError_t launch_dcheck_selftest(int32_t *status, cudaStream_t stream);
 
 // Device allocations of the library's own buffers: cudaMalloc / cudaFree, or the caller's pair
 // installed with sais_set_device_allocator.  dev_alloc returns cudaErrorMemoryAllocation when

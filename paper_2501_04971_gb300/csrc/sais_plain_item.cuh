@@ -40,6 +40,8 @@ namespace {
 template <int MC>
 __device__ __forceinline__ void plain_item(const SampleArgs &a, int j, int grp, int cpb, int tid) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (!SAIS_DCHECK(a.status, j >= 0 && j < a.count && grp >= 0 && grp * cpb < a.chains))
+        return;
     const InstDev *__restrict__ ip = a.inst + j;
     const int n = ip->n, m = ip->m, nprime = ip->nprime, npad = ip->npad, words = ip->words;
     const int m4 = ip->m4;
@@ -60,6 +62,10 @@ __device__ __forceinline__ void plain_item(const SampleArgs &a, int j, int grp, 
 
     float *Fs = reinterpret_cast<float *>(smem_raw);
     uint32_t *xs = reinterpret_cast<uint32_t *>(smem_raw + (has_w ? (size_t)npad * cpb * 4 : 0));
+    // Debug builds: this item's shared memory within the launch's (uniform over the CTA).
+    if (!SAIS_DCHECK(a.status, (has_w ? (size_t)npad * cpb * 4 : 0) + (size_t)words * cpb * 4 <=
+                                   dynamic_smem_bytes()))
+        return;
 
     const float *lam = a.lambda + (size_t)j * a.m_stride;
     // Constraint values g_k as FP32 (exact integers: |g| < 2^24, checked at creation) and

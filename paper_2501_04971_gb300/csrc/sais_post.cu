@@ -140,6 +140,12 @@ __global__ void __launch_bounds__(kPostThreads) post_kernel(PostArgs a) {
 
 __global__ void advance_iter_kernel(uint32_t *it) { *it += 1u; }
 
+// A device-side check that fails by construction (debug builds): exercises the reporting path.
+__global__ void dcheck_selftest_kernel(int32_t *status) {
+    const volatile int never = 0;
+    (void)SAIS_DCHECK(status, never != 0);
+}
+
 }  // namespace
 
 cudaError_t launch_post(const PostArgs &a, cudaStream_t stream) {
@@ -149,6 +155,19 @@ cudaError_t launch_post(const PostArgs &a, cudaStream_t stream) {
 
 cudaError_t launch_advance_iter(uint32_t *iter_dev, cudaStream_t stream) {
     advance_iter_kernel<<<1, 1, 0, stream>>>(iter_dev);
+    return cudaGetLastError();
+}
+
+bool debug_checks_built() {
+#if defined(SAIS_DEBUG) && SAIS_DEBUG
+    return true;
+#else
+    return false;
+#endif
+}
+
+cudaError_t launch_dcheck_selftest(int32_t *status, cudaStream_t stream) {
+    dcheck_selftest_kernel<<<1, 1, 0, stream>>>(status);
     return cudaGetLastError();
 }
 

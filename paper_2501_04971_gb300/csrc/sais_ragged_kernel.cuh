@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(kRaggedThreads, 1)
         if (it >= nitems) break;
         ++n_items;
         const int j = items[3 * it], grp = items[3 * it + 1], kind = items[3 * it + 2];
+        if (!SAIS_DCHECK(status, it >= 0 && kind >= 0 && kind <= 3)) break;
         bool ok = true;
         if (kind == 0)
             ok = field_item<1, 16, kHiLo, kTrack, false>(a, j, grp, tmem, L, status,

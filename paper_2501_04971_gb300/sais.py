@@ -15,13 +15,16 @@ from typing import List, Optional, Sequence
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libsais.so")
+# SAIS_DEBUG=1 in the environment loads the build with the device-side checks
+# (paper_2501_04971_gb300.build.build(debug=True)).
+LIB_PATH = os.path.join(HERE, "_build_debug" if os.environ.get("SAIS_DEBUG") == "1" else "_build",
+                        "libsais.so")
 
 _i32, _i64, _u32, _u64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
 _f32, _f64, _P = ctypes.c_float, ctypes.c_double, ctypes.c_void_p
 
 SAIS_OK, SAIS_EINVAL, SAIS_ENOMEM, SAIS_ECUDA, SAIS_EOVERFLOW, SAIS_ETIMEOUT, \
-    SAIS_EUNSUPPORTED = range(7)
+    SAIS_EUNSUPPORTED, SAIS_EBOUNDS = range(8)
 SAIS_PLAIN, SAIS_BLOCKED, SAIS_AUTO = 0, 1, 2
 SAIS_AUTO_PERSISTENT, SAIS_AUTO_GROUPS = 0, 1
 _VARIANTS = {"plain": SAIS_PLAIN, "blocked": SAIS_BLOCKED, "auto": SAIS_AUTO}
@@ -101,6 +104,7 @@ _SIGS = {
     "sais_synchronize": [_P, _P],
     "sais_sample_plan": [_P, ctypes.POINTER(sais_sample_params), ctypes.POINTER(sais_plan)],
     "sais_set_auto_mode": [_P, ctypes.c_int32],
+    "sais_debug_check_selftest": [_P, _P],
     "sais_persistent_stats": [_P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _P],
     "sais_set_instance_chains": [_P, _P],
     "sais_autotune": [_P, _i32, _i32, ctypes.POINTER(sais_tuning), _P],
@@ -452,6 +456,11 @@ class Problem:
     def synchronize(self, stream=None):
         """sais_synchronize: wait for the stream, raise SaisError on a device-side timeout."""
         sais_synchronize(self.handle, _stream_ptr(stream))
+
+    def debug_check_selftest(self, stream=None):
+        """sais_debug_check_selftest: queue a failing device-side check (debug builds)."""
+        _check(lib().sais_debug_check_selftest(self.handle, _stream_ptr(stream)),
+               "sais_debug_check_selftest")
 
     def alloc_outputs(self, chains: int, trace_sweeps: int = 0):
         import torch

@@ -165,6 +165,20 @@ def test_persistent_launch_forced_timeout_reports_and_recovers():
     prob.close()
 
 
+def test_groups_mode_block_size_fits_the_group():
+    """A block-field group whose largest member (n = 1000, hi/lo) does not fit the default K = 32
+    in shared memory runs at K = 16 (it once launched at K = 32 and failed)."""
+    insts = [wl.qkp(100, 0.5, 1), wl.qkp(600, 0.5, 2), wl.qkp(1000, 0.25, 3, profit_max=10000),
+             wl.mkp(60, 12, 4), wl.qkp(300, 0.75, 5)]
+    prob = sais.Problem(insts)
+    prob.set_auto_mode("groups")
+    lam = _lam(prob, insts, 10)
+    g = _sample(prob, lam, 160, 12, 3, 1, "auto")
+    p = _sample(prob, lam, 160, 12, 3, 1, "plain")
+    _assert_same(g, p, "groups vs plain")
+    prob.close()
+
+
 def test_auto_mode_rejects_unknown_mode():
     prob = sais.Problem([wl.qkp(40, 0.5, 1)])
     with pytest.raises(sais.SaisError) as e:
