@@ -523,6 +523,37 @@ def target_measurement(a, sais, torch):
     return out
 
 
+def mkp_measurement(a, sais, torch):
+    """The plain sampler on linear objectives (Eq. 14): MKP N=250 m=5 (32 instances x 1024
+    chains, the shape of config 1) and N=500 m=30 (128 x 256), 100 sweeps at beta_max 50, one
+    timed launch after a warm-up; spin updates/s, and the issue activity of the m = 30 case from
+    its ncu capture."""
+    from paper_2501_04971_gb300 import workloads as wl
+    res = {}
+    for name, (n, m, cnt, C) in (("n250_m5", (250, 5, 32, 1024)), ("n500_m30", (500, 30, 128, 256))):
+        prob = sais.Problem([wl.mkp(n, m, 9000 + s) for s in range(cnt)])
+        lam = torch.full((prob.count * prob.m_stride,), 0.5, device="cuda")
+        out = prob.alloc_outputs(C)
+        T = 100
+        prob.sample(lam, C, T, 50.0, 1, 0, variant="plain", out=out)
+        prob.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        prob.sample(lam, C, T, 50.0, 1, 0, variant="plain", out=out)
+        e1.record()
+        prob.synchronize()
+        ms = e0.elapsed_time(e1)
+        upd = sum(sc.n_spins for sc in prob.scalars) * C * T
+        res[name] = {"value": upd / (ms / 1e3), "unit": UNIT, "ms": ms, "instances": cnt,
+                     "chains": C, "sweeps": T, "kernel": prob.plan(C, "plain")["kernel"],
+                     "chains_per_cta": prob.plan(C, "plain")["chains_per_cta"]}
+        prob.close()
+    res["n500_m30"]["profile"] = ("ncu, 32 instances x 256 chains (bench.py --kernel-case "
+                                  "plain_mkp500_m30; profiles/plain_sampler_mkp500_m30.md): issue "
+                                  "slots busy 31.7 %, 1.7 warps per SM at that size")
+    return res
+
+
 def ksweep_measurement(a, sais, torch, insts, sm_mhz):
     """The blocked sampler at block sizes K = 16, 32, 64 on the bench workload (`ksweep_sweeps`
     sweeps per launch, one timed launch after a warm-up): spin updates/s and SM cycles per
@@ -979,6 +1010,9 @@ def main():
         pval = upd_all / (pms / 1e3)
         plain_cmp = {"value": pval, "unit": UNIT, "sampler_ms_per_step": pms,
                      "blocked_over_plain": value / pval}
+    mkp = None
+    if not a.no_ksweep and world == 1:
+        mkp = mkp_measurement(a, sais, torch)
     ksweep = None
     if not a.no_ksweep and world == 1 and variant == "blocked":
         ksweep = ksweep_measurement(a, sais, torch, insts, clk.summary().get("sm_mhz") or SM_MAX_MHZ)
@@ -1032,6 +1066,7 @@ def main():
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": 3 * a.steps, "clocks": clocks,
             "updates_per_step": upd_step, "plain": plain_cmp, "blocked_k": ksweep,
+            "plain_mkp": mkp,
             "gap_1pct": gap,
             "ragged": ragged}
     if pen is not None:

@@ -53,6 +53,10 @@ def test_our_arm_line_small():
     for k in ("16", "32", "64"):
         assert ks[k]["value"] > 0 and ks[k]["cycles_per_spin_step"] > 0 and ks[k]["kernel"]
     assert ks["plain"]["value"] > 0
+    for case in ("n250_m5", "n500_m30"):
+        assert d["plain_mkp"][case]["value"] > 0 and d["plain_mkp"][case]["kernel"] == "plain"
+    lat = d["roofline"]["latency"]
+    assert lat["cycles_per_spin_step"] > 0 and 0 < lat["smsp_issue_active"] <= 1
 
 
 @pytest.mark.gpu
