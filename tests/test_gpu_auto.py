@@ -179,6 +179,22 @@ def test_groups_mode_block_size_fits_the_group():
     prob.close()
 
 
+@pytest.mark.parametrize("mode", ["persistent", "groups"])
+def test_auto_trace_equals_plain(mode):
+    """sais_sample_trace through SAIS_AUTO: every chain's state at every sweep end equals the
+    plain sampler's, for each item kind of the batch (block fields, rank-k, plain)."""
+    insts = [wl.qkp(120, 0.5, 21), wl.qkp(560, 0.5, 22), wl.mkp(50, 4, 23)]
+    prob = sais.Problem(insts)
+    prob.set_auto_mode(mode)
+    lam = torch.tensor(_lam(prob, insts, 11).reshape(-1), device="cuda:0")
+    a = prob.sample(lam, 128, 9, 10.0, 5, 2, variant="auto", trace=True)
+    p = prob.sample(lam, 128, 9, 10.0, 5, 2, variant="plain", trace=True)
+    prob.synchronize()
+    for k in a:
+        assert torch.equal(a[k], p[k]), k
+    prob.close()
+
+
 def test_auto_mode_rejects_unknown_mode():
     prob = sais.Problem([wl.qkp(40, 0.5, 1)])
     with pytest.raises(sais.SaisError) as e:

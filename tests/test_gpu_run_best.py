@@ -144,13 +144,18 @@ def test_run_best_large(n):
     _run_best_vs_oracle(insts, [[1.0]], 128, 16, 10.0, 2, 0, "blocked")
 
 
-def test_run_best_auto_ragged():
-    """SAIS_AUTO over a ragged batch (rank-k, block-field and plain work) equals the plain
-    sampler's run-best outputs, and the plain sampler equals the oracle on two members."""
+@pytest.mark.parametrize("mode", ["persistent", "groups"])
+def test_run_best_auto_ragged(mode):
+    """SAIS_AUTO over a ragged batch (rank-k, block-field and plain work; one persistent launch
+    or launch groups) equals the plain sampler's run-best outputs, and the plain sampler equals
+    the oracle on two members."""
     insts = [wl.qkp(150, 0.5, 1), wl.qkp(520, 0.25, 2), _tighten(wl.mkp(90, 5, 3), 0.85),
              wl.qkp(60, 1.0, 4)]
     lams = [[0.5], [1.0], [1.0] * 5, [0.3]]
     prob = sais.Problem(insts)
+    prob.set_auto_mode(mode)
+    assert prob.plan(128, "auto")["kernel"] == ("persistent" if mode == "persistent"
+                                                 else "launch groups")
     lam = _lam_dev(lams, prob.m_stride)
     a = prob.sample_run_best(lam, 128, 40, 10.0, 9, 1, variant="auto")
     b = prob.sample_run_best(lam, 128, 40, 10.0, 9, 1, variant="plain")
