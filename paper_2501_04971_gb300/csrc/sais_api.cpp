@@ -58,6 +58,8 @@ struct HostInst {
     float kappa = 0.f;
     bool need_lo = false;                  // lo image allocated (BF16 hi/lo split)
     bool lo_own = false;                   // this instance has |W| > 256
+    bool f16 = false;                      // every |h_i| + sum_j |W_ij| <= 32767: the plain
+                                           // sampler may hold F as int16 (exact)
     std::vector<int32_t> Q, slack_off;     // m, m+1
     std::vector<int32_t> acol;             // nprime x m (spin-major)
     std::vector<float> D, asum;            // npad
@@ -85,7 +87,7 @@ sais_status build_host(const sais_problem_desc *d, HostInst &h) {
     h.W = d->W;
 
     // Integer checks: W symmetric with zero diagonal and int16 range; A >= 0; b >= 1.
-    int64_t maxabs_f = 0, nz = 0, max_w = 0;
+    int64_t maxabs_f = 0, nz = 0, max_w = 0, max_row = 0;
     for (int32_t i = 0; i < n; ++i) {
         int64_t row = std::llabs((int64_t)d->h[i]);
         maxabs_f = std::max(maxabs_f, row);
@@ -109,8 +111,10 @@ sais_status build_host(const sais_problem_desc *d, HostInst &h) {
             return fail(SAIS_EOVERFLOW,
                         "item %d: |h| + sum |W| = %lld >= 2^24 breaks the exact FP32 field", i,
                         (long long)row);
+        max_row = std::max(max_row, row);
     }
     h.need_lo = max_w > 256;
+    h.f16 = h.has_w && max_row <= 32767;   // |F_i| <= max_row for every state
     h.lo_own = h.need_lo;
     // Capacity tightening (Sec. IV-B): the sampled problem uses B' (slack bits, sigma_g, g,
     // penalty rule); feasibility keeps the caller's b through a per-constraint margin.
@@ -278,6 +282,7 @@ struct sais_problem {
     int max_n = 0;
     int max_n16 = 0;              // max over quadratic instances of n rounded up to 16
     bool any_w = false;
+    bool all_f16 = true;          // every quadratic instance has HostInst::f16
     std::vector<HostInst> host;   // host copies (W pointer cleared after creation)
     bool any_lo = false;          // some instance needs the BF16 hi/lo split
     bool all_w = true;            // every instance has a quadratic objective
@@ -298,6 +303,7 @@ struct sais_problem {
         int block_k = 16, cpb = 32;
         int max_m = 0, max_npad = 0, max_npad_w = 0, words = 0, max_n = 0, max_n16 = 0;
         bool any_w = false;
+        bool f16 = true;           // every quadratic member has HostInst::f16 (plain: int16 F)
         bool blocked_ok = false;   // every member fits the blocked sampler
         bool field = false;        // blocked sampler with per-block field GEMMs (one CTA)
         std::vector<int> members;
@@ -387,6 +393,7 @@ void build_groups(sais_problem *p) {
             if (h.has_w) g.max_npad_w = std::max(g.max_npad_w, h.npad);
             g.words = std::max(g.words, h.words);
             g.any_w = g.any_w || h.has_w;
+            if (h.has_w) g.f16 = g.f16 && h.f16;
         }
         g.variant = key >= 100 ? SAIS_PLAIN : SAIS_BLOCKED;
         g.blocked_ok = key < 100;
@@ -542,7 +549,7 @@ cudaError_t launch_group(const sais_problem *p, const sais_problem::Group &g, co
     if (g.variant == SAIS_BLOCKED)
         return launch_blocked_sampler(ga, g.max_m, g.max_npad, g.words, g.block_k, g.stream_w,
                                       g.hilo, p->d_status, polls, st);
-    return launch_plain_sampler(ga, g.max_m, g.max_npad_w, g.words, g.cpb, st);
+    return launch_plain_sampler(ga, g.max_m, g.max_npad_w, g.words, g.cpb, st, g.f16);
 }
 
 }  // namespace
@@ -621,6 +628,7 @@ sais_status sais_create_batch(const sais_problem_desc *descs, int32_t count, int
         }
         p->max_m = std::max(p->max_m, h.m);
         p->any_w = p->any_w || h.has_w;
+        if (h.has_w) p->all_f16 = p->all_f16 && h.f16;
         p->all_w = p->all_w && h.has_w;
         p->any_lo = p->any_lo || h.need_lo;
     }
@@ -918,7 +926,7 @@ sais_status check_sample_params(const sais_problem *p, const sais_sample_params 
 // many chains an SM holds, so small CTAs pack best), or the caller's choice.
 sais_status plain_cpb(const sais_problem *p, int want, int *cpb) {
     const int c = want ? want : 32;
-    const size_t need = plain_smem_bytes(p->max_npad_w, p->words, p->any_w, c);
+    const size_t need = plain_smem_bytes(p->max_npad_w, p->words, p->any_w, c, p->all_f16);
     if (need > (size_t)kMaxPlainSmem)
         return fail(SAIS_EUNSUPPORTED,
                     "plain sampler: N'=%d needs %zu bytes of shared memory at %d chains per CTA",
@@ -966,10 +974,10 @@ sais_status plan_sample(const sais_problem *p, const sais_sample_params *prm, Sa
     if (prm->variant == SAIS_AUTO) {
         for (const auto &g : p->groups)
             if (g.variant == SAIS_PLAIN &&
-                plain_smem_bytes(g.max_npad_w, g.words, g.any_w, g.cpb) > (size_t)kMaxPlainSmem)
+                plain_smem_bytes(g.max_npad_w, g.words, g.any_w, g.cpb, g.f16) > (size_t)kMaxPlainSmem)
                 return fail(SAIS_EUNSUPPORTED,
                             "plain sampler group: padded N'=%d needs %zu bytes of shared memory",
-                            g.max_npad_w, plain_smem_bytes(g.max_npad_w, g.words, g.any_w, g.cpb));
+                            g.max_npad_w, plain_smem_bytes(g.max_npad_w, g.words, g.any_w, g.cpb, g.f16));
         return SAIS_OK;
     }
     if (prm->variant == SAIS_PLAIN) return plain_cpb(p, prm->chains_per_cta, &pl->cpb);
@@ -1090,7 +1098,7 @@ sais_status enqueue_sample(sais_problem *p, const sais_sample_params *prm, const
         e = launch_blocked_sampler(a, p->max_m, p->max_npad, p->words, pl.k, pl.stream_w, pl.hilo,
                                    p->d_status, polls, st);
     else
-        e = launch_plain_sampler(a, p->max_m, p->max_npad_w, p->words, pl.cpb, st);
+        e = launch_plain_sampler(a, p->max_m, p->max_npad_w, p->words, pl.cpb, st, p->all_f16);
     if (e != cudaSuccess) return fail(SAIS_ECUDA, "sampler launch: %s", cudaGetErrorString(e));
     return SAIS_OK;
 }
@@ -1624,7 +1632,7 @@ sais_status sais_autotune(sais_problem *p, int32_t chains, int32_t sweeps, sais_
                 cands.push_back({SAIS_BLOCKED, 32, g.cpb});
         }
         for (int cpb : {32, 64, 128})
-            if (plain_smem_bytes(g.max_npad_w, g.words, g.any_w, cpb) <= (size_t)kMaxPlainSmem)
+            if (plain_smem_bytes(g.max_npad_w, g.words, g.any_w, cpb, g.f16) <= (size_t)kMaxPlainSmem)
                 cands.push_back({SAIS_PLAIN, g.block_k, cpb});
         double best = 1e300;
         Cand pick = cands.front();

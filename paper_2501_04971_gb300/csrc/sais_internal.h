@@ -142,8 +142,10 @@ struct PostArgs {
 };
 
 // Launchers (defined in the .cu files); they only enqueue work on `stream`.
+// f16: F held as int16 in shared memory (every quadratic instance of the launch has
+// |h_i| + sum_j |W_ij| <= 32767, so F is exact in it for every state), else FP32.
 cudaError_t launch_plain_sampler(const SampleArgs &a, int max_m, int max_npad, int max_words,
-                                 int chains_per_cta, cudaStream_t stream);
+                                 int chains_per_cta, cudaStream_t stream, bool f16 = false);
 cudaError_t launch_blocked_sampler(const SampleArgs &a, int max_m, int max_npad,
                                    int max_words, int block_k, bool stream_w, bool hilo,
                                    int32_t *status, long long dec_wait_polls,
@@ -174,7 +176,7 @@ cudaError_t launch_ragged(const SampleArgs &a, const int32_t *items, int32_t nit
                           int32_t *head, unsigned long long *stats, int max_n16_w,
                           int max_words, bool hilo, int32_t *status, long long dec_wait_polls,
                           int sms, cudaStream_t stream);
-size_t plain_smem_bytes(int max_npad, int max_words, bool any_w, int cpb);
+size_t plain_smem_bytes(int max_npad, int max_words, bool any_w, int cpb, bool f16 = false);
 constexpr size_t kMaxSmemPerBlock = 232448;   // 227 KB opt-in per CTA on sm_103
 cudaError_t launch_post(const PostArgs &a, cudaStream_t stream);
 cudaError_t launch_advance_iter(uint32_t *iter_dev, cudaStream_t stream);

@@ -28,6 +28,7 @@
 #pragma once
 
 #include <climits>
+#include <type_traits>
 
 #include "sais_device.cuh"
 
@@ -36,9 +37,13 @@ namespace {
 
 // One work item: chains grp cpb .. grp cpb + cpb - 1 of instance j, one per thread (thread tid
 // of the item's cpb), dynamic shared memory sized by plain_smem_bytes for cpb chains (declared
-// here, not passed as a pointer, so that every access stays a shared-memory access).
-template <int MC>
+// here, not passed as a pointer, so that every access stays a shared-memory access).  kF16: the
+// objective field F is held as int16 (the launch guarantees |F_i| <= |h_i| + sum_j |W_ij| <=
+// 32767 for every state, so every value it takes is exact), half the shared memory of FP32 and
+// so twice the chains per SM; the arithmetic of the field is the same FP32 on the same values.
+template <int MC, bool kF16 = false>
 __device__ __forceinline__ void plain_item(const SampleArgs &a, int j, int grp, int cpb, int tid) {
+    using FT = typename std::conditional<kF16, int16_t, float>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (!SAIS_DCHECK(a.status, j >= 0 && j < a.count && grp >= 0 && grp * cpb < a.chains))
         return;
@@ -60,11 +65,11 @@ __device__ __forceinline__ void plain_item(const SampleArgs &a, int j, int grp, 
     const uint64_t seed = a.seed + (uint64_t)j;
     const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
 
-    float *Fs = reinterpret_cast<float *>(smem_raw);
-    uint32_t *xs = reinterpret_cast<uint32_t *>(smem_raw + (has_w ? (size_t)npad * cpb * 4 : 0));
+    FT *Fs = reinterpret_cast<FT *>(smem_raw);
+    const size_t fbytes = has_w ? (size_t)npad * cpb * sizeof(FT) : 0;
+    uint32_t *xs = reinterpret_cast<uint32_t *>(smem_raw + fbytes);
     // Debug builds: this item's shared memory within the launch's (uniform over the CTA).
-    if (!SAIS_DCHECK(a.status, (has_w ? (size_t)npad * cpb * 4 : 0) + (size_t)words * cpb * 4 <=
-                                   dynamic_smem_bytes()))
+    if (!SAIS_DCHECK(a.status, fbytes + (size_t)words * cpb * 4 <= dynamic_smem_bytes()))
         return;
 
     const float *lam = a.lambda + (size_t)j * a.m_stride;
@@ -86,7 +91,7 @@ __device__ __forceinline__ void plain_item(const SampleArgs &a, int j, int grp, 
         }
     }
     if (has_w)
-        for (int i = 0; i < npad; ++i) Fs[i * cpb + tid] = hF[i];
+        for (int i = 0; i < npad; ++i) Fs[i * cpb + tid] = (FT)hF[i];
     for (int w = 0; w < words; ++w) xs[w * cpb + tid] = 0u;
     const float errk = field_err_factor(m);
     // Best feasible sweep-end state of the run (when a.run_cost is set): the cost of the current
@@ -111,7 +116,7 @@ __device__ __forceinline__ void plain_item(const SampleArgs &a, int j, int grp, 
                 if (i >= n) break;
                 if ((i & 31) == 0) xw = xs[(i >> 5) * cpb + tid];
                 const float theta = theta_of_word(word_of(rw, q));
-                const float Fi = has_w ? Fs[i * cpb + tid] : __ldg(hF + i);
+                const float Fi = has_w ? (float)Fs[i * cpb + tid] : __ldg(hF + i);
                 const int xi = (xw >> (i & 31)) & 1;
                 // Row i of A_ext as FP32, four coefficients per load.
                 float akf[MC];
@@ -183,7 +188,7 @@ __device__ __forceinline__ void plain_item(const SampleArgs &a, int j, int grp, 
                 if (has_w && __any_sync(0xffffffffu, d != 0)) {
                     const float df = (float)d;
                     const int4 *Wi = reinterpret_cast<const int4 *>(W + (size_t)i * npad);
-                    float *Fc = Fs + tid;
+                    FT *Fc = Fs + tid;
                     for (int j8 = 0; j8 < (npad >> 3); ++j8) {
                         const int4 v = __ldg(Wi + j8);
                         const uint32_t u[4] = {(uint32_t)v.x, (uint32_t)v.y, (uint32_t)v.z,
@@ -191,10 +196,17 @@ __device__ __forceinline__ void plain_item(const SampleArgs &a, int j, int grp, 
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             const int r = (j8 * 8 + 2 * e) * cpb;
-                            const float wlo = (float)(int16_t)(u[e] & 0xffffu);
-                            const float whi = (float)(int16_t)(u[e] >> 16);
-                            Fc[r] = fmaf(df, wlo, Fc[r]);
-                            Fc[r + cpb] = fmaf(df, whi, Fc[r + cpb]);
+                            if constexpr (kF16) {   // integer update, exact in int16
+                                const int wlo = (int16_t)(u[e] & 0xffffu);
+                                const int whi = (int16_t)(u[e] >> 16);
+                                Fc[r] = (int16_t)(Fc[r] + d * wlo);
+                                Fc[r + cpb] = (int16_t)(Fc[r + cpb] + d * whi);
+                            } else {
+                                const float wlo = (float)(int16_t)(u[e] & 0xffffu);
+                                const float whi = (float)(int16_t)(u[e] >> 16);
+                                Fc[r] = fmaf(df, wlo, Fc[r]);
+                                Fc[r + cpb] = fmaf(df, whi, Fc[r + cpb]);
+                            }
                         }
                     }
                 }
