@@ -549,8 +549,8 @@ def mkp_measurement(a, sais, torch):
                      "chains_per_cta": prob.plan(C, "plain")["chains_per_cta"]}
         prob.close()
     res["n500_m30"]["profile"] = ("ncu, 32 instances x 256 chains (bench.py --kernel-case "
-                                  "plain_mkp500_m30; profiles/plain_sampler_mkp500_m30.md): issue "
-                                  "slots busy 31.7 %, 1.7 warps per SM at that size")
+                                  "plain_mkp500_m30): issue slots busy 31.7 %, 1.7 warps per SM "
+                                  "at that size")
     return res
 
 
@@ -1051,8 +1051,8 @@ def main():
         roof["latency"] = {
             "cycles_per_spin_step": kmean * mhz * 1e6 * SM_COUNT / steps,
             "smsp_issue_active": 0.473, "tensor_pipe_active": 0.056,
-            "source": "ncu of bench.py --kernel-case rankk_qkp300 (profiles/"
-                      "blocked_sampler_qkp300.md): issue slots busy 47 %, tensor pipe 5.6 %"}
+            "source": "ncu --set full of bench.py --kernel-case rankk_qkp300: issue slots "
+                      "busy 47 %, tensor pipe 5.6 %"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
